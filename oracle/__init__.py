@@ -1,0 +1,336 @@
+"""Plain FP64 CPU oracle of the hybrid PIC ion loop (arXiv 2305.05600).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the CPU
+baseline leg of the benchmark, never by the library.  It shares no code with
+the CUDA path.  The arithmetic lives in ``hvo.c`` (plain loops, paper order);
+this module only compiles it with gcc and marshals numpy arrays.
+
+Grids are component-major ``[ncomp][ncell]`` float64 arrays with the linear
+cell index ``c = i + nx*(j + ny*k)`` (x fastest).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hvo.c")
+_LIB = os.path.join(_HERE, "_build", "libhvo.so")
+_lock = threading.Lock()
+_lib = None
+
+SHAPES = {"ngp": 0, "qs": 1, "cic": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile hvo.c into a shared library with gcc (no FMA contraction, so
+    x86 and Arm hosts round identically)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nsub", ctypes.c_int64),
+                ("Te", ctypes.c_double), ("gamma_e", ctypes.c_double),
+                ("eta", ctypes.c_double), ("eta_h", ctypes.c_double),
+                ("n_floor", ctypes.c_double), ("shape", ctypes.c_int64),
+                ("smooth_passes", ctypes.c_int64)]
+
+
+class _Species(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("q", ctypes.c_double), ("m", ctypes.c_double),
+                ("cell", ctypes.c_void_p), ("ox", ctypes.c_void_p), ("oy", ctypes.c_void_p),
+                ("oz", ctypes.c_void_p), ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p),
+                ("vz", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("W_K", ctypes.c_double), ("P", ctypes.c_double * 3),
+                ("charge", ctypes.c_double), ("W_B", ctypes.c_double),
+                ("max_divB", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"W_K": self.W_K, "P": list(self.P), "charge": self.charge,
+                "W_B": self.W_B, "max_divB": self.max_divB}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            D = ctypes.c_double
+            L.hvo_shape.argtypes = [I64, D, D, D, P, P, P, P]
+            L.hvo_shape.restype = ctypes.c_int
+            L.hvo_gather.argtypes = [P, P, I64, I64, D, D, D, P]
+            L.hvo_boris.argtypes = [D, P, P, P]
+            L.hvo_move.argtypes = [P, P, P, P, D]
+            L.hvo_deposit.argtypes = [P, P, I64, P, P]
+            L.hvo_push_deposit.argtypes = [P, P, I64, P, P, P, P, P]
+            for nm in ("hvo_curl", "hvo_grad", "hvo_div"):
+                getattr(L, nm).argtypes = [P, P, P]
+            L.hvo_lap.argtypes = [P, P, I64, P]
+            L.hvo_ohm.argtypes = [P, P, P, P, P]
+            L.hvo_field_advance.argtypes = [P, P, P, P]
+            L.hvo_smooth.argtypes = [P, P, I64, I64]
+            L.hvo_extrapolate.argtypes = [I64, P, P, P]
+            L.hvo_diag_grid.argtypes = [P, P, P, P, P, P]
+            L.hvo_init.argtypes = [P, P, I64, P, P, P, P]
+            L.hvo_step.argtypes = [P, P, I64, P, P, P, P, P, P, P]
+            L.hvo_sort_stable.argtypes = [P, I64, I64, P, P, P]
+            L.hvo_sort_stable.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
+              eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0) -> Grid:
+    s = SHAPES[shape] if isinstance(shape, str) else int(shape)
+    return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
+                smooth_passes)
+
+
+def ncell(g: Grid) -> int:
+    return g.nx * g.ny * g.nz
+
+
+@dataclass
+class Species:
+    """One ion species as FP64 arrays (cell int64; offsets and v [3][n])."""
+    q: float
+    m: float
+    cell: np.ndarray
+    off: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    _keep: list = field(default_factory=list, repr=False)
+
+    def __post_init__(self):
+        self.cell = np.ascontiguousarray(self.cell, dtype=np.int64)
+        self.off = _f64(self.off).reshape(3, -1).copy()
+        self.v = _f64(self.v).reshape(3, -1).copy()
+        self.w = _f64(self.w).copy()
+
+    @property
+    def n(self) -> int:
+        return int(self.cell.shape[0])
+
+    def struct(self) -> _Species:
+        return _Species(self.n, self.q, self.m, self.cell.ctypes.data,
+                        self.off[0].ctypes.data, self.off[1].ctypes.data,
+                        self.off[2].ctypes.data, self.v[0].ctypes.data,
+                        self.v[1].ctypes.data, self.v[2].ctypes.data, self.w.ctypes.data)
+
+    def copy(self) -> "Species":
+        return Species(self.q, self.m, self.cell.copy(), self.off.copy(), self.v.copy(),
+                       self.w.copy())
+
+
+def _species_array(sp):
+    arr = (_Species * len(sp))(*[s.struct() for s in sp])
+    return arr
+
+
+# ----------------------------------------------------------------------------
+# thin wrappers, one per oracle routine
+# ----------------------------------------------------------------------------
+
+def shape_weights(shape, d):
+    si = np.zeros(8, np.int32)
+    sj = np.zeros(8, np.int32)
+    sk = np.zeros(8, np.int32)
+    wt = np.zeros(8, np.float64)
+    s = SHAPES[shape] if isinstance(shape, str) else int(shape)
+    nt = lib().hvo_shape(s, float(d[0]), float(d[1]), float(d[2]), _p(si), _p(sj), _p(sk),
+                         _p(wt))
+    return np.stack([si[:nt], sj[:nt], sk[:nt]], axis=1), wt[:nt].copy()
+
+
+def gather(g: Grid, F: np.ndarray, cell: int, d) -> np.ndarray:
+    F = _f64(F).reshape(-1, ncell(g))
+    out = np.zeros(F.shape[0])
+    lib().hvo_gather(ctypes.byref(g), _p(F), F.shape[0], int(cell), float(d[0]), float(d[1]),
+                     float(d[2]), _p(out))
+    return out
+
+
+def boris(qmdt: float, E, B, v) -> np.ndarray:
+    E = _f64(E)
+    B = _f64(B)
+    v = _f64(v).copy()
+    lib().hvo_boris(float(qmdt), _p(E), _p(B), _p(v))
+    return v
+
+
+def move(g: Grid, cell: int, d, v, frac: float = 1.0):
+    c = np.array([cell], np.int64)
+    d = _f64(d).copy()
+    v = _f64(v)
+    lib().hvo_move(ctypes.byref(g), _p(c), _p(d), _p(v), float(frac))
+    return int(c[0]), d
+
+
+def deposit(g: Grid, species) -> tuple[np.ndarray, np.ndarray]:
+    n = np.zeros(ncell(g))
+    J = np.zeros(3 * ncell(g))
+    arr = _species_array(species)
+    lib().hvo_deposit(ctypes.byref(g), arr, len(species), _p(n), _p(J))
+    return n, J.reshape(3, -1)
+
+
+def push_deposit(g: Grid, species, E, B):
+    E = _f64(E).reshape(3, -1)
+    B = _f64(B).reshape(3, -1)
+    n = np.zeros(ncell(g))
+    J = np.zeros(3 * ncell(g))
+    kin = np.zeros(4)
+    arr = _species_array(species)
+    lib().hvo_push_deposit(ctypes.byref(g), arr, len(species), _p(E), _p(B), _p(n), _p(J),
+                           _p(kin))
+    return n, J.reshape(3, -1), kin
+
+
+def _vec_op(name, g, A, ncomp_out):
+    A = _f64(A)
+    out = np.zeros(ncomp_out * ncell(g))
+    getattr(lib(), name)(ctypes.byref(g), _p(A), _p(out))
+    return out.reshape(ncomp_out, -1) if ncomp_out > 1 else out
+
+
+def curl(g, A):
+    return _vec_op("hvo_curl", g, _f64(A).reshape(3, -1), 3)
+
+
+def grad(g, f):
+    return _vec_op("hvo_grad", g, _f64(f).reshape(-1), 3)
+
+
+def div(g, A):
+    return _vec_op("hvo_div", g, _f64(A).reshape(3, -1), 1)
+
+
+def lap(g, A, nc):
+    A = _f64(A).reshape(nc, -1)
+    out = np.zeros(nc * ncell(g))
+    lib().hvo_lap(ctypes.byref(g), _p(A), nc, _p(out))
+    return out.reshape(nc, -1)
+
+
+def ohm(g, B, n, Ji):
+    B = _f64(B).reshape(3, -1)
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    E = np.zeros(3 * ncell(g))
+    lib().hvo_ohm(ctypes.byref(g), _p(B), _p(n), _p(Ji), _p(E))
+    return E.reshape(3, -1)
+
+
+def field_advance(g, B, n, Ji):
+    B = _f64(B).reshape(3, -1).copy()
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    lib().hvo_field_advance(ctypes.byref(g), _p(B), _p(n), _p(Ji))
+    return B
+
+
+def smooth(g, q, passes):
+    q = _f64(q).copy()
+    nc = q.size // ncell(g)
+    lib().hvo_smooth(ctypes.byref(g), _p(q), nc, int(passes))
+    return q
+
+
+def extrapolate(half, prev):
+    half = _f64(half)
+    prev = _f64(prev)
+    out = np.zeros_like(half)
+    lib().hvo_extrapolate(half.size, _p(half), _p(prev), _p(out))
+    return out
+
+
+def diag_grid(g, B, n):
+    B = _f64(B).reshape(3, -1)
+    n = _f64(n).reshape(-1)
+    wb = np.zeros(1)
+    ch = np.zeros(1)
+    md = np.zeros(1)
+    lib().hvo_diag_grid(ctypes.byref(g), _p(B), _p(n), _p(wb), _p(ch), _p(md))
+    return float(wb[0]), float(ch[0]), float(md[0])
+
+
+def sort_stable(keys, nkeys):
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    n = keys.shape[0]
+    perm = np.zeros(n, np.int64)
+    counts = np.zeros(nkeys, np.int64)
+    offsets = np.zeros(nkeys + 1, np.int64)
+    rc = lib().hvo_sort_stable(_p(keys), n, int(nkeys), _p(perm), _p(counts), _p(offsets))
+    if rc != 0:
+        raise ValueError("key out of range")
+    return perm, counts, offsets
+
+
+class Sim:
+    """Whole-state oracle simulation: species plus B, E and the previous
+    (half-step) moments, advanced by ``hvo_step``."""
+
+    def __init__(self, g: Grid, species, B0):
+        self.g = g
+        self.species = [s.copy() for s in species]
+        nce = ncell(g)
+        self.B = _f64(B0).reshape(3, nce).copy()
+        self.E = np.zeros((3, nce))
+        self.n_prev = np.zeros(nce)
+        self.J_prev = np.zeros((3, nce))
+        self.n_ext = np.zeros(nce)
+        self.J_ext = np.zeros((3, nce))
+        self.step_count = 0
+        self.diags: list[dict] = []
+        arr = _species_array(self.species)
+        lib().hvo_init(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
+                       _p(self.n_prev), _p(self.J_prev))
+
+    def sort(self):
+        """Apply the stable counting sort by cell to every species."""
+        for s in self.species:
+            perm, _, _ = sort_stable(s.cell, ncell(self.g))
+            s.cell = np.ascontiguousarray(s.cell[perm])
+            s.off = np.ascontiguousarray(s.off[:, perm])
+            s.v = np.ascontiguousarray(s.v[:, perm])
+            s.w = np.ascontiguousarray(s.w[perm])
+
+    def step(self, nsteps: int = 1, sort_every: int = 0):
+        for _ in range(nsteps):
+            if sort_every > 0 and self.step_count % sort_every == 0:
+                self.sort()
+            arr = _species_array(self.species)
+            d = Diag()
+            lib().hvo_step(ctypes.byref(self.g), arr, len(self.species), _p(self.B), _p(self.E),
+                           _p(self.n_prev), _p(self.J_prev), _p(self.n_ext), _p(self.J_ext),
+                           ctypes.byref(d))
+            self.step_count += 1
+            self.diags.append(d.as_dict())
+        return self.diags[-1] if self.diags else None

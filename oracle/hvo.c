@@ -1,0 +1,522 @@
+/*
+ * Hybrid PIC oracle: a plain, slow, FP64 CPU restatement of the per-step ion
+ * loop of the kinetic-ion / massless-fluid-electron hybrid PIC method of
+ * Hybrid-VPIC (arXiv 2305.05600).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file's library.  It shares no
+ * code, header, table or constant with the CUDA path and must never be used
+ * as a fallback for it.
+ *
+ * Every routine is written as plain loops in the order the paper states the
+ * method; there is no blocking, fusion or reordering.  Sections and equations
+ * cited below are those of the paper:
+ *   Sec. 2.1  hybrid model equations: Ohm's law (Eq. 2), R_ei (Eq. 3),
+ *             Ampere (Eq. 4), Faraday (Eq. 5), equation of state (Eq. 6),
+ *             density floor n_e = max(n_e, n_f), whistler CFL and subcycling.
+ *   Sec. 2.2  PIC implementation: leapfrog / Boris (Eqs. 9-10), linear
+ *             extrapolation of J_i (Eq. 11), cell-centred grid and centred
+ *             differences (Eq. 12), particle storage as cell index + relative
+ *             coordinates in [-1,1]^3, NGP shape (Eq. 13), smoothing.
+ *   App. B    QS particle shape: deposit weights (Eq. 17), interpolation
+ *             coefficients (Eq. 18) and field at the particle (Eq. 19).
+ *   Sec. 2.3  periodic boundaries (the only ones built here).
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   R1 relative coordinates are taken in [-1,1): a particle exactly on the
+ *      upper face belongs to the next cell; x = x_c + d * Delta / 2.
+ *   R2 the half-time-step position used for deposit (App. B, after Eq. 17)
+ *      is used for every shape and for both n and J.
+ *   R3 n is extrapolated like J (Eq. 11 states it for J only).
+ *   R4 smoothing is the separable (1/4,1/2,1/4) binomial filter applied to
+ *      the deposited moments only.
+ *   R5 the floor n_f = max(n, n_floor) is applied wherever n enters Ohm's
+ *      law (pressure, ion flow and Hall term).
+ *   R6 the Laplacian in the hyper-resistive term is the 3-point-per-axis
+ *      cell-centred Laplacian.
+ *   R7 each field subcycle of length h = dt/nsub is an explicit-midpoint
+ *      (RK2) step; the moments are held at their half-step values
+ *      n^{n+1/2}, J^{n+1/2} during the subcycle B^n -> B^{n+1}.
+ *   R8 start-up: loaded velocities are v^{-1/2}; the previous moments are the
+ *      deposit at x^0; E^0 = Ohm(B^0, those moments).
+ *   R9 an axis with one cell (2D runs use ny = 1) is periodic with period one
+ *      cell, so shapes fold onto the same cell and centred differences along
+ *      it vanish.  Offsets along such an axis are never moved.
+ *
+ * Units: normalised Alfvenic units, e = m_p = mu_0 = 1, lengths in d_i,
+ * time in 1/Omega_ci.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  int64_t nx, ny, nz;
+  double dx, dy, dz, dt;
+  int64_t nsub;
+  double Te, gamma_e, eta, eta_h, n_floor;
+  int64_t shape; /* 0 NGP (Eq. 13), 1 QS (Eq. 17), 2 CIC (tensor-linear) */
+  int64_t smooth_passes;
+} hvo_grid;
+
+typedef struct {
+  int64_t n;
+  double q, m;
+  int64_t *cell;
+  double *ox, *oy, *oz;
+  double *vx, *vy, *vz;
+  double *w;
+} hvo_species;
+
+typedef struct {
+  double W_K;   /* sum 1/2 m w |v^{n+1/2}|^2 */
+  double P[3];  /* sum m w v^{n+1/2} */
+  double charge;/* sum n^{n+1/2} V_c over cells (deposited, unsmoothed) */
+  double W_B;   /* sum 1/2 |B|^2 V_c */
+  double max_divB;
+} hvo_diag;
+
+static int64_t ncell_of(const hvo_grid *g) { return g->nx * g->ny * g->nz; }
+
+static int64_t wrapi(int64_t i, int64_t n) {
+  int64_t r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+/* linear cell index I <-> (i,j,k), x fastest (Sec. 2.2), periodic wrap */
+static int64_t cidx(const hvo_grid *g, int64_t i, int64_t j, int64_t k) {
+  return wrapi(i, g->nx) + g->nx * (wrapi(j, g->ny) + g->ny * wrapi(k, g->nz));
+}
+
+static void cdecode(const hvo_grid *g, int64_t c, int64_t *i, int64_t *j, int64_t *k) {
+  *i = c % g->nx;
+  *j = (c / g->nx) % g->ny;
+  *k = c / (g->nx * g->ny);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Particle shapes.  Returns the number of target cells; fills the cell     */
+/* shifts (si,sj,sk) relative to the particle's cell and the weights.       */
+/* ------------------------------------------------------------------------ */
+int hvo_shape(int64_t shape, double dx, double dy, double dz,
+              int32_t *si, int32_t *sj, int32_t *sk, double *wt) {
+  if (shape == 0) {
+    /* NGP (Eq. 13): all weight to the particle's own cell. */
+    si[0] = sj[0] = sk[0] = 0;
+    wt[0] = 1.0;
+    return 1;
+  }
+  if (shape == 1) {
+    /* QS (Eq. 17): own cell and its six face neighbours. */
+    int t = 0;
+    si[t] = 0;  sj[t] = 0;  sk[t] = 0;  wt[t++] = (3.0 - dx * dx - dy * dy - dz * dz) / 6.0;
+    si[t] = 1;  sj[t] = 0;  sk[t] = 0;  wt[t++] = (1.0 + dx) * (1.0 + dx) / 12.0;
+    si[t] = 0;  sj[t] = 1;  sk[t] = 0;  wt[t++] = (1.0 + dy) * (1.0 + dy) / 12.0;
+    si[t] = 0;  sj[t] = 0;  sk[t] = 1;  wt[t++] = (1.0 + dz) * (1.0 + dz) / 12.0;
+    si[t] = -1; sj[t] = 0;  sk[t] = 0;  wt[t++] = (1.0 - dx) * (1.0 - dx) / 12.0;
+    si[t] = 0;  sj[t] = -1; sk[t] = 0;  wt[t++] = (1.0 - dy) * (1.0 - dy) / 12.0;
+    si[t] = 0;  sj[t] = 0;  sk[t] = -1; wt[t++] = (1.0 - dz) * (1.0 - dz) / 12.0;
+    return t;
+  }
+  /* CIC on cell centres: per axis, weight 1 - |d|/2 to the own cell and
+   * |d|/2 to the neighbour on the side of d; tensor product over axes. */
+  {
+    double d[3] = {dx, dy, dz};
+    int side[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+      side[a] = d[a] >= 0.0 ? 1 : -1;
+      f[a] = fabs(d[a]) / 2.0;
+    }
+    int t = 0;
+    for (int c = 0; c < 8; ++c) {
+      int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+      si[t] = ox ? side[0] : 0;
+      sj[t] = oy ? side[1] : 0;
+      sk[t] = oz ? side[2] : 0;
+      wt[t] = (ox ? f[0] : 1.0 - f[0]) * (oy ? f[1] : 1.0 - f[1]) * (oz ? f[2] : 1.0 - f[2]);
+      ++t;
+    }
+    return t;
+  }
+}
+
+/* Field at a particle: F(x_p) = sum_t S_t F_t, the same weights as the
+ * deposit (App. B: Eqs. 17 and 19 together are self-force free).
+ * F is component-major [nc][ncell]. */
+void hvo_gather(const hvo_grid *g, const double *F, int64_t nc, int64_t cell,
+                double dx, double dy, double dz, double *out) {
+  int32_t si[8], sj[8], sk[8];
+  double wt[8];
+  int64_t i, j, k, nce = ncell_of(g);
+  cdecode(g, cell, &i, &j, &k);
+  int nt = hvo_shape(g->shape, dx, dy, dz, si, sj, sk, wt);
+  for (int64_t a = 0; a < nc; ++a) out[a] = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    int64_t c = cidx(g, i + si[t], j + sj[t], k + sk[t]);
+    for (int64_t a = 0; a < nc; ++a) out[a] += wt[t] * F[a * nce + c];
+  }
+}
+
+/* Non-relativistic Boris push (Sec. 2.2, Eq. 9): half electric kick over
+ * dt/2, magnetic rotation over dt, half electric kick over dt/2.
+ * qmdt = (q/m) dt.  v enters as v^{n-1/2} and leaves as v^{n+1/2}. */
+void hvo_boris(double qmdt, const double *E, const double *B, double *v) {
+  double h = 0.5 * qmdt;
+  double vm[3], t[3], s[3], vp[3], vq[3];
+  for (int a = 0; a < 3; ++a) vm[a] = v[a] + h * E[a];
+  for (int a = 0; a < 3; ++a) t[a] = h * B[a];
+  double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + tt);
+  /* v' = v- + v- x t */
+  vp[0] = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
+  vp[1] = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
+  vp[2] = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
+  /* v+ = v- + v' x s */
+  vq[0] = vm[0] + (vp[1] * s[2] - vp[2] * s[1]);
+  vq[1] = vm[1] + (vp[2] * s[0] - vp[0] * s[2]);
+  vq[2] = vm[2] + (vp[0] * s[1] - vp[1] * s[0]);
+  for (int a = 0; a < 3; ++a) v[a] = vq[a] + h * E[a];
+}
+
+/* Move a particle by v * (frac * dt) (Sec. 2.2, Eq. 10) in cell-index +
+ * relative-coordinate form (reading R1): d <- d + 2 v frac dt / Delta,
+ * shift m = floor((d+1)/2), d <- d - 2m, cell <- cell + m (periodic).
+ * Axes with a single cell are not moved (reading R9). */
+void hvo_move(const hvo_grid *g, int64_t *cell, double *d, const double *v, double frac) {
+  int64_t n[3] = {g->nx, g->ny, g->nz};
+  double del[3] = {g->dx, g->dy, g->dz};
+  int64_t idx[3];
+  cdecode(g, *cell, &idx[0], &idx[1], &idx[2]);
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] == 1) continue;
+    double x = d[a] + 2.0 * v[a] * frac * g->dt / del[a];
+    double m = floor((x + 1.0) / 2.0);
+    x -= 2.0 * m;
+    if (x >= 1.0) { x -= 2.0; m += 1.0; }
+    if (x < -1.0) { x += 2.0; m -= 1.0; }
+    d[a] = x;
+    idx[a] = wrapi(idx[a] + (int64_t)m, n[a]);
+  }
+  *cell = cidx(g, idx[0], idx[1], idx[2]);
+}
+
+/* Add one particle's contribution q w S_t / V_c to n and q w v S_t / V_c to
+ * J at position (cell, d) (Eqs. 13 and 17). */
+static void deposit_one(const hvo_grid *g, int64_t cell, const double *d, const double *v,
+                        double qw, double *n, double *J) {
+  int32_t si[8], sj[8], sk[8];
+  double wt[8];
+  int64_t i, j, k, nce = ncell_of(g);
+  double vc = g->dx * g->dy * g->dz;
+  cdecode(g, cell, &i, &j, &k);
+  int nt = hvo_shape(g->shape, d[0], d[1], d[2], si, sj, sk, wt);
+  for (int t = 0; t < nt; ++t) {
+    int64_t c = cidx(g, i + si[t], j + sj[t], k + sk[t]);
+    double s = qw * wt[t] / vc;
+    n[c] += s;
+    J[0 * nce + c] += s * v[0];
+    J[1 * nce + c] += s * v[1];
+    J[2 * nce + c] += s * v[2];
+  }
+}
+
+/* Deposit every particle at its current position with its current velocity,
+ * without pushing (start-up, reading R8).  n, J are accumulated into. */
+void hvo_deposit(const hvo_grid *g, const hvo_species *sp, int64_t nsp, double *n, double *J) {
+  for (int64_t s = 0; s < nsp; ++s) {
+    for (int64_t p = 0; p < sp[s].n; ++p) {
+      double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
+      double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
+      deposit_one(g, sp[s].cell[p], d, v, sp[s].q * sp[s].w[p], n, J);
+    }
+  }
+}
+
+/* The particle part of one step: for every ion, gather E^n, B^n at x^n,
+ * Boris-push v^{n-1/2} -> v^{n+1/2}, deposit n, J at the half-step position
+ * x^{n+1/2} (App. B; reading R2), then move to x^{n+1}.  n_acc, J_acc are
+ * accumulated into; kin[0..3] receive sum 1/2 m w |v|^2 and sum m w v. */
+void hvo_push_deposit(const hvo_grid *g, hvo_species *sp, int64_t nsp,
+                      const double *E, const double *B, double *n_acc, double *J_acc,
+                      double *kin) {
+  for (int a = 0; a < 4; ++a) kin[a] = 0.0;
+  for (int64_t s = 0; s < nsp; ++s) {
+    double qmdt = sp[s].q / sp[s].m * g->dt;
+    for (int64_t p = 0; p < sp[s].n; ++p) {
+      int64_t cell = sp[s].cell[p];
+      double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
+      double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
+      double Ep[3], Bp[3];
+      hvo_gather(g, E, 3, cell, d[0], d[1], d[2], Ep);
+      hvo_gather(g, B, 3, cell, d[0], d[1], d[2], Bp);
+      hvo_boris(qmdt, Ep, Bp, v);
+      /* half-step position for the deposit */
+      int64_t ch = cell;
+      double dh[3] = {d[0], d[1], d[2]};
+      hvo_move(g, &ch, dh, v, 0.5);
+      deposit_one(g, ch, dh, v, sp[s].q * sp[s].w[p], n_acc, J_acc);
+      /* full move */
+      hvo_move(g, &cell, d, v, 1.0);
+      sp[s].cell[p] = cell;
+      sp[s].ox[p] = d[0];
+      sp[s].oy[p] = d[1];
+      sp[s].oz[p] = d[2];
+      sp[s].vx[p] = v[0];
+      sp[s].vy[p] = v[1];
+      sp[s].vz[p] = v[2];
+      double mw = sp[s].m * sp[s].w[p];
+      kin[0] += 0.5 * mw * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      kin[1] += mw * v[0];
+      kin[2] += mw * v[1];
+      kin[3] += mw * v[2];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid operators on the cell-centred grid (Sec. 2.2, Eq. 12).              */
+/* ------------------------------------------------------------------------ */
+
+/* centred derivative of scalar field f along axis a at cell (i,j,k) */
+static double dcen(const hvo_grid *g, const double *f, int a, int64_t i, int64_t j, int64_t k) {
+  if (a == 0) return (f[cidx(g, i + 1, j, k)] - f[cidx(g, i - 1, j, k)]) / (2.0 * g->dx);
+  if (a == 1) return (f[cidx(g, i, j + 1, k)] - f[cidx(g, i, j - 1, k)]) / (2.0 * g->dy);
+  return (f[cidx(g, i, j, k + 1)] - f[cidx(g, i, j, k - 1)]) / (2.0 * g->dz);
+}
+
+/* out = curl A (centred), A and out component-major [3][ncell] */
+void hvo_curl(const hvo_grid *g, const double *A, double *out) {
+  int64_t nce = ncell_of(g);
+  const double *Ax = A, *Ay = A + nce, *Az = A + 2 * nce;
+  for (int64_t c = 0; c < nce; ++c) {
+    int64_t i, j, k;
+    cdecode(g, c, &i, &j, &k);
+    out[0 * nce + c] = dcen(g, Az, 1, i, j, k) - dcen(g, Ay, 2, i, j, k);
+    out[1 * nce + c] = dcen(g, Ax, 2, i, j, k) - dcen(g, Az, 0, i, j, k);
+    out[2 * nce + c] = dcen(g, Ay, 0, i, j, k) - dcen(g, Ax, 1, i, j, k);
+  }
+}
+
+/* out = grad f (centred) [3][ncell] */
+void hvo_grad(const hvo_grid *g, const double *f, double *out) {
+  int64_t nce = ncell_of(g);
+  for (int64_t c = 0; c < nce; ++c) {
+    int64_t i, j, k;
+    cdecode(g, c, &i, &j, &k);
+    for (int a = 0; a < 3; ++a) out[a * nce + c] = dcen(g, f, a, i, j, k);
+  }
+}
+
+/* out = div A (centred) [ncell] */
+void hvo_div(const hvo_grid *g, const double *A, double *out) {
+  int64_t nce = ncell_of(g);
+  for (int64_t c = 0; c < nce; ++c) {
+    int64_t i, j, k;
+    cdecode(g, c, &i, &j, &k);
+    out[c] = dcen(g, A, 0, i, j, k) + dcen(g, A + nce, 1, i, j, k) + dcen(g, A + 2 * nce, 2, i, j, k);
+  }
+}
+
+/* out = Laplacian of each of nc components (3 points per axis, reading R6) */
+void hvo_lap(const hvo_grid *g, const double *A, int64_t nc, double *out) {
+  int64_t nce = ncell_of(g);
+  for (int64_t a = 0; a < nc; ++a) {
+    const double *f = A + a * nce;
+    for (int64_t c = 0; c < nce; ++c) {
+      int64_t i, j, k;
+      cdecode(g, c, &i, &j, &k);
+      double fc = f[c];
+      out[a * nce + c] =
+          (f[cidx(g, i + 1, j, k)] - 2.0 * fc + f[cidx(g, i - 1, j, k)]) / (g->dx * g->dx) +
+          (f[cidx(g, i, j + 1, k)] - 2.0 * fc + f[cidx(g, i, j - 1, k)]) / (g->dy * g->dy) +
+          (f[cidx(g, i, j, k + 1)] - 2.0 * fc + f[cidx(g, i, j, k - 1)]) / (g->dz * g->dz);
+    }
+  }
+}
+
+/* Ohm's law for massless electrons (Eq. 2) with R_ei = eta J - eta_H lap J
+ * (Eq. 3), J = curl B (Eq. 4, mu_0 = 1), p_e = Te n^gamma (Eq. 6, p_0 = n_0
+ * Te, n_0 = 1) and the density floor n_f = max(n, n_floor) (Sec. 2.1):
+ *   E = -grad p_e / n_f - (J_i / n_f) x B + (J x B) / n_f + eta J - eta_H lap J
+ * Inputs: B [3][ncell], n [ncell], Ji [3][ncell]; output E [3][ncell]. */
+void hvo_ohm(const hvo_grid *g, const double *B, const double *n, const double *Ji, double *E) {
+  int64_t nce = ncell_of(g);
+  double *J = (double *)malloc(sizeof(double) * 3 * nce);
+  double *LJ = (double *)malloc(sizeof(double) * 3 * nce);
+  double *nf = (double *)malloc(sizeof(double) * nce);
+  double *pe = (double *)malloc(sizeof(double) * nce);
+  double *gp = (double *)malloc(sizeof(double) * 3 * nce);
+  hvo_curl(g, B, J);
+  hvo_lap(g, J, 3, LJ);
+  for (int64_t c = 0; c < nce; ++c) {
+    nf[c] = n[c] > g->n_floor ? n[c] : g->n_floor;
+    pe[c] = g->Te * pow(nf[c], g->gamma_e);
+  }
+  hvo_grad(g, pe, gp);
+  for (int64_t c = 0; c < nce; ++c) {
+    double b[3] = {B[c], B[nce + c], B[2 * nce + c]};
+    double jt[3] = {J[c], J[nce + c], J[2 * nce + c]};
+    double ui[3] = {Ji[c] / nf[c], Ji[nce + c] / nf[c], Ji[2 * nce + c] / nf[c]};
+    double uixb[3] = {ui[1] * b[2] - ui[2] * b[1], ui[2] * b[0] - ui[0] * b[2], ui[0] * b[1] - ui[1] * b[0]};
+    double jxb[3] = {jt[1] * b[2] - jt[2] * b[1], jt[2] * b[0] - jt[0] * b[2], jt[0] * b[1] - jt[1] * b[0]};
+    for (int a = 0; a < 3; ++a) {
+      E[a * nce + c] = -gp[a * nce + c] / nf[c] - uixb[a] + jxb[a] / nf[c] +
+                       g->eta * jt[a] - g->eta_h * LJ[a * nce + c];
+    }
+  }
+  free(J);
+  free(LJ);
+  free(nf);
+  free(pe);
+  free(gp);
+}
+
+/* Faraday's law (Eq. 5) subcycled nsub times per particle step (Sec. 2.1),
+ * each subcycle an explicit-midpoint step of h = dt / nsub (reading R7):
+ *   B* = B - (h/2) curl E(B),   B <- B - h curl E(B*).
+ * n, Ji are held fixed (the half-step moments). */
+void hvo_field_advance(const hvo_grid *g, double *B, const double *n, const double *Ji) {
+  int64_t nce = ncell_of(g);
+  double h = g->dt / (double)g->nsub;
+  double *E = (double *)malloc(sizeof(double) * 3 * nce);
+  double *cE = (double *)malloc(sizeof(double) * 3 * nce);
+  double *Bs = (double *)malloc(sizeof(double) * 3 * nce);
+  for (int64_t s = 0; s < g->nsub; ++s) {
+    hvo_ohm(g, B, n, Ji, E);
+    hvo_curl(g, E, cE);
+    for (int64_t c = 0; c < 3 * nce; ++c) Bs[c] = B[c] - 0.5 * h * cE[c];
+    hvo_ohm(g, Bs, n, Ji, E);
+    hvo_curl(g, E, cE);
+    for (int64_t c = 0; c < 3 * nce; ++c) B[c] = B[c] - h * cE[c];
+  }
+  free(E);
+  free(cE);
+  free(Bs);
+}
+
+/* Separable binomial (1/4, 1/2, 1/4) smoothing, `passes` times, of nc
+ * component-major grids (reading R4). */
+void hvo_smooth(const hvo_grid *g, double *q, int64_t nc, int64_t passes) {
+  int64_t nce = ncell_of(g);
+  double *tmp = (double *)malloc(sizeof(double) * nce);
+  for (int64_t p = 0; p < passes; ++p) {
+    for (int64_t a = 0; a < nc; ++a) {
+      double *f = q + a * nce;
+      for (int ax = 0; ax < 3; ++ax) {
+        for (int64_t c = 0; c < nce; ++c) {
+          int64_t i, j, k;
+          cdecode(g, c, &i, &j, &k);
+          int64_t cm, cp;
+          if (ax == 0) { cm = cidx(g, i - 1, j, k); cp = cidx(g, i + 1, j, k); }
+          else if (ax == 1) { cm = cidx(g, i, j - 1, k); cp = cidx(g, i, j + 1, k); }
+          else { cm = cidx(g, i, j, k - 1); cp = cidx(g, i, j, k + 1); }
+          tmp[c] = 0.25 * f[cm] + 0.5 * f[c] + 0.25 * f[cp];
+        }
+        memcpy(f, tmp, sizeof(double) * nce);
+      }
+    }
+  }
+  free(tmp);
+}
+
+/* Linear extrapolation (Eq. 11): out = 3/2 half - 1/2 prev. */
+void hvo_extrapolate(int64_t len, const double *half, const double *prev, double *out) {
+  for (int64_t c = 0; c < len; ++c) out[c] = 1.5 * half[c] - 0.5 * prev[c];
+}
+
+/* Grid diagnostics: W_B = sum 1/2 |B|^2 V_c, charge = sum n V_c,
+ * max |div B|. */
+void hvo_diag_grid(const hvo_grid *g, const double *B, const double *n, double *wb,
+                   double *charge, double *maxdiv) {
+  int64_t nce = ncell_of(g);
+  double vc = g->dx * g->dy * g->dz;
+  double *dv = (double *)malloc(sizeof(double) * nce);
+  hvo_div(g, B, dv);
+  *wb = 0.0;
+  *charge = 0.0;
+  *maxdiv = 0.0;
+  for (int64_t c = 0; c < nce; ++c) {
+    *wb += 0.5 * (B[c] * B[c] + B[nce + c] * B[nce + c] + B[2 * nce + c] * B[2 * nce + c]) * vc;
+    *charge += n[c] * vc;
+    if (fabs(dv[c]) > *maxdiv) *maxdiv = fabs(dv[c]);
+  }
+  free(dv);
+}
+
+/* Start-up (reading R8): n_prev, J_prev := deposit at x^0 with v^{-1/2}
+ * (smoothed like every deposit); E = Ohm(B, n_prev, J_prev). */
+void hvo_init(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const double *B,
+              double *E, double *n_prev, double *J_prev) {
+  int64_t nce = ncell_of(g);
+  memset(n_prev, 0, sizeof(double) * nce);
+  memset(J_prev, 0, sizeof(double) * 3 * nce);
+  hvo_deposit(g, sp, nsp, n_prev, J_prev);
+  hvo_smooth(g, n_prev, 1, g->smooth_passes);
+  hvo_smooth(g, J_prev, 3, g->smooth_passes);
+  hvo_ohm(g, B, n_prev, J_prev, E);
+}
+
+/* One full step n -> n+1 in the paper's order (Sec. 2.2):
+ *   push + half-step deposit,  smoothing,  extrapolation (Eq. 11),
+ *   subcycled field advance B^n -> B^{n+1} with the half-step moments,
+ *   E^{n+1} = Ohm(B^{n+1}, n^{n+1}, J^{n+1}),  prev := half-step moments.
+ * On return n_prev, J_prev hold n^{n+1/2}, J^{n+1/2}.  n_ext, J_ext (may be
+ * NULL) receive the extrapolated n^{n+1}, J^{n+1}. */
+void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double *E,
+              double *n_prev, double *J_prev, double *n_ext, double *J_ext, hvo_diag *dg) {
+  int64_t nce = ncell_of(g);
+  double *nh = (double *)calloc((size_t)nce, sizeof(double));
+  double *Jh = (double *)calloc((size_t)(3 * nce), sizeof(double));
+  double *ne = (double *)malloc(sizeof(double) * nce);
+  double *Je = (double *)malloc(sizeof(double) * 3 * nce);
+  double kin[4];
+  hvo_push_deposit(g, sp, nsp, E, B, nh, Jh, kin);
+  double charge_raw = 0.0, vc = g->dx * g->dy * g->dz;
+  for (int64_t c = 0; c < nce; ++c) charge_raw += nh[c] * vc;
+  hvo_smooth(g, nh, 1, g->smooth_passes);
+  hvo_smooth(g, Jh, 3, g->smooth_passes);
+  hvo_extrapolate(nce, nh, n_prev, ne);
+  hvo_extrapolate(3 * nce, Jh, J_prev, Je);
+  hvo_field_advance(g, B, nh, Jh);
+  hvo_ohm(g, B, ne, Je, E);
+  memcpy(n_prev, nh, sizeof(double) * nce);
+  memcpy(J_prev, Jh, sizeof(double) * 3 * nce);
+  if (n_ext) memcpy(n_ext, ne, sizeof(double) * nce);
+  if (J_ext) memcpy(J_ext, Je, sizeof(double) * 3 * nce);
+  if (dg) {
+    double wb, ch, md;
+    hvo_diag_grid(g, B, nh, &wb, &ch, &md);
+    dg->W_K = kin[0];
+    dg->P[0] = kin[1];
+    dg->P[1] = kin[2];
+    dg->P[2] = kin[3];
+    dg->charge = charge_raw;
+    dg->W_B = wb;
+    dg->max_divB = md;
+  }
+  free(nh);
+  free(Jh);
+  free(ne);
+  free(Je);
+}
+
+/* Stable counting sort of keys in [0, nkeys): counts[k], exclusive offsets
+ * offsets[k] (nkeys+1 entries) and perm such that key[perm[0..n)] is
+ * non-decreasing with equal keys kept in input order. */
+int hvo_sort_stable(const int64_t *key, int64_t n, int64_t nkeys, int64_t *perm,
+                    int64_t *counts, int64_t *offsets) {
+  for (int64_t k = 0; k < nkeys; ++k) counts[k] = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    if (key[p] < 0 || key[p] >= nkeys) return -1;
+    counts[key[p]] += 1;
+  }
+  offsets[0] = 0;
+  for (int64_t k = 0; k < nkeys; ++k) offsets[k + 1] = offsets[k] + counts[k];
+  int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nkeys > 0 ? nkeys : 1));
+  for (int64_t k = 0; k < nkeys; ++k) next[k] = offsets[k];
+  for (int64_t p = 0; p < n; ++p) perm[next[key[p]]++] = p;
+  free(next);
+  return 0;
+}
