@@ -1,0 +1,428 @@
+"""Benchmark of the hybrid PIC ion loop: ion pushes per second including the
+periodic sort, the deposit and the full subcycled field advance, on the 2D
+Harris-sheet workload (1024x512 cells, dx = 0.25 d_i, 100 ions per cell,
+52,428,800 FP32 ions), plus its HBM roofline fraction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole hot path (sort every 20 steps, gather +
+Boris push + half-step deposit + move, moment post, 10 field subcycles of
+two Ohm/Faraday stages, final Ohm).  Under torchrun each rank runs an
+independent replica (the path is not sharded); rank 0 prints one JSON line.
+The reference arm times the FP64 CPU oracle on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ion pushes/s incl. deposit+field on 1 GB300"
+UNIT = "pushes/s"
+PAPER_PUSHES_PER_CORE = 1.0e7  # Sec. 1: ~10 million pushes/s/processor on CPUs
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="harris2d",
+                    choices=["harris2d", "harris2d_small", "alfven2d", "beam3d_small"])
+    ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, shape, seed_offset=0):
+    from paper_2305_05600_gb300 import inputs as I
+    if name == "harris2d":
+        return I.harris(shape=shape, seed=1000 + seed_offset)
+    if name == "harris2d_small":  # ncu-sized case: 13.1M ions, > L2
+        return I.harris(nx=512, nz=256, shape=shape, seed=1000 + seed_offset)
+    if name == "alfven2d":
+        return I.alfven2d(shape=shape, seed=seed_offset)
+    if name == "beam3d_small":
+        return I.beam3d(nx=64, ny=64, nz=64, shape=shape, seed=2000 + seed_offset)
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int, enabled: bool):
+        self.proc = None
+        self.device = device
+        if enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(device), f"--query-gpu={self.QUERY}",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# roofline bookkeeping
+# ----------------------------------------------------------------------------
+
+def push_bytes_per_launch(wl) -> float:
+    """Algorithmic bytes of one push launch: every ion read once (cell, 2 or
+    3 offsets, v, w) and written once (all but w), plus the gather array
+    (32 B per padded cell) read once and the deposit accumulator (16 B per
+    padded cell) read and written once."""
+    p = wl.params
+    dim2 = p["ny"] == 1
+    per_ion = (4 + 4 * (2 if dim2 else 3) + 12 + 4) + (4 + 4 * (2 if dim2 else 3) + 12)
+    npad = (p["nx"] + 2) * (1 if dim2 else p["ny"] + 2) * (p["nz"] + 2)
+    return float(wl.n_particles * per_ion + npad * (32 + 32))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record(workload: str):
+    """DRAM bytes per push launch from the committed ncu summary, valid only
+    while the push kernel source is unchanged (hash recorded with it)."""
+    src = os.path.join(ROOT, "paper_2305_05600_gb300", "csrc", "hv_push.cu")
+    rec = os.path.join(ROOT, "profiles", "push_traffic.json")
+    try:
+        with open(rec) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        ent = d.get(workload)
+        if ent and ent.get("hv_push_sha") == h:
+            return float(ent["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_strip_rate(wl, rows: int, steps: int):
+    """Time the FP64 oracle on a strip of `rows` z-rows of the workload
+    (all nx columns, every ion in those rows, treated as its own periodic
+    box: per-ion and per-cell costs are those of the full grid).  Returns
+    (pushes/s, ions in strip, seconds, per-step seconds list)."""
+    import oracle as O
+    p = dict(wl.params)
+    nx, nz = p["nx"], p["nz"]
+    k0 = (nz - rows) // 2
+    s = wl.species[0]
+    k = s.cell // (nx * p["ny"])
+    sel = (k >= k0) & (k < k0 + rows)
+    cell = (s.cell[sel] - k0 * nx * p["ny"]).astype(np.int64)
+    sp = O.Species(s.q, s.m, cell, s.off[:, sel], s.v[:, sel], s.w[sel])
+    B = wl.B0[:, k0:k0 + rows].astype(np.float64).reshape(3, -1)
+    g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
+                    p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
+                    p["smooth_passes"])
+    sim = O.Sim(g, [sp], B)
+    times = []
+    for i in range(steps):
+        t0 = time.perf_counter()
+        sim.step(1, sort_every=p["sort_every"])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    return sp.n * steps / total, sp.n, total, times
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, args.shape)
+    p = wl.params
+    n_full = wl.n_particles
+    # bound the whole run to ~2 minutes: rows per step from a two-row probe
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    _, _, t1, _ = oracle_strip_rate(wl, 2, 1)
+    per_row = t1 / 2.0
+    rows = int(max(2, min(p["nz"], budget / max(per_row, 1e-6))))
+    rate, n_strip, total, times = oracle_strip_rate(wl, rows, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    value = n_strip * len(timed) / sum(timed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} ({p['nx']}x{p['ny']}x{p['nz']}, "
+                               f"{n_full} ions, shape {args.shape})",
+                   "sample": f"{rows}-row strip ({n_strip} ions) of the same workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{rows} of {p['nz']} z-rows, all {p['nx']} columns, "
+                                   f"{n_strip} ions, periodic strip; one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "context": {"paper_pushes_per_s_per_core": PAPER_PUSHES_PER_CORE},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2305_05600_gb300 import hv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hv.lib()
+    hv.hv_set_allocator(True)
+    wl = make_workload(args.workload, args.shape, seed_offset=rank)
+    n_ions = wl.n_particles
+    stream = torch.cuda.current_stream(dev)
+    ctx = hv.load_workload(wl, stream=stream)
+
+    # warm-up (the first call also runs the start-up deposit and E^0)
+    for _ in range(args.warmup):
+        hv.hv_step(ctx, 1)
+    torch.cuda.synchronize(dev)
+    hv.hv_profile(ctx, True)
+    clocks = Clocks(local, not args.no_clocks and rank == 0)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    hv.hv_step(ctx, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ck = clocks.stop()
+    ms_local = ev0.elapsed_time(ev1)
+    prof = hv.hv_profile_read(ctx)
+    hv.hv_profile(ctx, False)
+    diag = hv.hv_diag(ctx, check=False)
+    ms = max_over_ranks(ms_local, world)
+    total_ions = sum_over_ranks(float(n_ions), world)
+    value = total_ions * args.steps / (ms * 1e-3)
+    ctx.close()
+    del ctx
+    torch.cuda.synchronize(dev)
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, wl, world, dev, stream)
+
+    peak, peak_kind = measured_peak()
+    push_ms = prof["ms_push"] / max(1, prof["n_push"])
+    bytes_launch = push_bytes_per_launch(wl)
+    achieved = bytes_launch / (push_ms * 1e-3) / 1e9
+    traffic = traffic_record(args.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        p = wl.params
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {p['nx']}x{p['ny']}x{p['nz']} cells, "
+                                   f"dx={p['dx']}, {n_ions} ions/GPU, shape {args.shape}, "
+                                   f"nsub={p['nsub']}, sort every {p['sort_every']}",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (ions %.2f GB/GPU)" % (
+                           n_ions * (28 if p['ny'] == 1 else 32) / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "push_kernel (gather+Boris+deposit+move)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic, "bytes_per_launch": bytes_launch,
+                         "ms_per_launch": push_ms},
+            "phases_ms_per_step": {k: prof["ms_" + k] / max(1, prof["steps"])
+                                   for k in ("sort", "push", "moments", "field", "ohm")},
+            "gpu_launches": int(prof["launches"]),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": ck,
+            "diag": {k: diag[k] for k in ("W_K", "W_B", "charge", "max_divB", "err_word")},
+            "context": {"paper_pushes_per_s_per_core": PAPER_PUSHES_PER_CORE},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, wl, world, dev, stream):
+    """Pushes/s through the public API with ions in pinned host memory: the
+    timed region holds the host->device load, every step with a
+    device->host read of its diagnostics, and the final moments read."""
+    import torch
+
+    from paper_2305_05600_gb300 import hv
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype={np.float32: torch.float32,
+                                        np.int32: torch.int32}[a.dtype.type], pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    hsp = [(s.q, s.m, pinned(s.cell), pinned(s.off), pinned(s.v), pinned(s.w))
+           for s in wl.species]
+    p = wl.params
+    nc = p["nx"] * p["ny"] * p["nz"]
+    n_host = np.zeros((p["nz"], p["ny"], p["nx"]), np.float32)
+    J_host = np.zeros((3, p["nz"], p["ny"], p["nx"]), np.float32)
+    steps = max(1, min(args.steps, 100))
+    ctx = hv.hv_init_grid(p, wl.B0, stream)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i, (q, m, c, o, v, w) in enumerate(hsp):
+        hv.hv_load_ions(ctx, i, q, m, c, o, v, w)
+    for _ in range(steps):
+        hv.hv_step(ctx, 1)
+        hv.hv_diag(ctx)
+    hv.hv_moments(ctx, n_host, J_host, None, None)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    barrier(world)
+    ctx.close()
+    dt = max_over_ranks(dt, world)
+    n_ions = sum_over_ranks(float(wl.n_particles), world)
+    h2d = sum(a.nbytes for s in hsp for a in s[2:]) / steps
+    d2h = 80 + (n_host.nbytes + J_host.nbytes) / steps
+    return {"value": n_ions * steps / dt, "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "note": "load amortised over the steps; one hv_diag read per step"}
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle on the host, one thread, on a strip of the workload
+    sized to ~15 s of CPU work."""
+    nz = wl.params["nz"]
+    _, _, t2, _ = oracle_strip_rate(wl, 2, 1)
+    rows = int(max(2, min(nz, 15.0 / max(t2 / 2.0, 1e-6))))
+    rate, n_strip, total, _ = oracle_strip_rate(wl, rows, 1)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one step of a {rows}-of-{nz}-row strip ({n_strip} ions, all "
+                      f"{wl.params['nx']} columns) of the same workload, periodic, one thread "
+                      f"({total:.1f} s)"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

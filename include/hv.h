@@ -1,0 +1,186 @@
+/*
+ * hv.h - C ABI of libhv, a GB300 (sm_103a) implementation of the per-step ion
+ * loop of the kinetic-ion / massless-fluid-electron hybrid particle-in-cell
+ * method of Hybrid-VPIC (arXiv 2305.05600).
+ *
+ * One step n -> n+1 (Sec. 2.2 of the paper):
+ *   [periodic stable counting sort of the ions by cell]
+ *   gather E^n, B^n at x^n with the particle shape (NGP Eq. 13, QS Eqs. 17-19,
+ *   or CIC on cell centres) -> non-relativistic Boris push (Eq. 9) ->
+ *   deposit n, J_i at the half-step position (App. B) -> move (Eq. 10)
+ *   -> linear extrapolation of the moments (Eq. 11) -> Faraday's law (Eq. 5)
+ *   subcycled nsub times, E from Ohm's law (Eqs. 2-4, 6) with the density
+ *   floor -> E^{n+1} = Ohm(B^{n+1}, n^{n+1}, J^{n+1}).
+ *
+ * Conventions for every entry point:
+ *  - Units are normalised Alfvenic units (e = m_p = mu_0 = n_0 = 1, lengths in
+ *    d_i, time in 1/Omega_ci, velocity in v_A, B in B_0).
+ *  - Cells are cell-centred (Sec. 2.2); the linear cell index is
+ *    c = i + nx*(j + ny*k), x fastest; all boundaries are periodic (Sec. 2.3).
+ *    2D runs are x-z planes with ny = 1; any axis may have one cell.
+ *  - A particle is a cell index plus relative coordinates in [-1, 1) per axis
+ *    (Sec. 2.2), x = x_c + d * Delta / 2; along a single-cell axis the
+ *    coordinate is ignored and reported as 0.
+ *  - Grids exchanged with the caller are float32, component-major
+ *    [ncomp][nz][ny][nx].  Particle arrays are float32 SoA, [3][n] for
+ *    vectors.
+ *  - Pointers are borrowed for the duration of the call only; the library
+ *    copies what it keeps.  `on_device` = 1 means the pointer is CUDA device
+ *    memory, 0 means host memory.
+ *  - No exception or process exit crosses the ABI.  Every call returns an
+ *    hv_status; on failure hv_last_error() returns a thread-local message.
+ *  - Work is enqueued on the stream given to hv_init_grid.  Device-side
+ *    errors (a particle moving more than one cell per step, a non-finite
+ *    particle) are latched in a device error word and reported by the next
+ *    synchronising call (hv_moments, hv_diag, hv_get_ions).
+ *  - A context is not thread-safe; use one context per stream.
+ */
+#ifndef HV_H
+#define HV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hv_ctx hv_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  HV_OK = 0,
+  HV_EINVAL = 1,   /* bad argument (checked on the host before any work) */
+  HV_ENOMEM = 2,   /* device allocation failed */
+  HV_ECUDA = 3,    /* a CUDA runtime call failed */
+  HV_ECFL = 4,     /* a particle moved more than one cell in a step, or the
+                      whistler limit Omega dt/nsub < dx^2/pi (Sec. 2.1) fails */
+  HV_ENAN = 5,     /* a non-finite particle or diagnostic */
+  HV_ETIMEOUT = 6, /* reserved: a bounded device wait gave up */
+  HV_ESTATE = 7    /* call out of order (e.g. loading ions after stepping) */
+} hv_status;
+
+typedef enum { HV_SHAPE_NGP = 0, HV_SHAPE_QS = 1, HV_SHAPE_CIC = 2 } hv_shape;
+
+/* Simulation parameters (Secs. 2.1-2.2).  Layout is fixed (112 bytes). */
+typedef struct {
+  int32_t nx, ny, nz;   /* cells per axis, each >= 1, nx*ny*nz < 2^31 */
+  int32_t nsub;         /* field subcycles per particle step (Sec. 2.1), >= 1 */
+  double dx, dy, dz;    /* cell sizes in d_i (> 0); dy is used as given */
+  double dt;            /* particle time step in 1/Omega_ci (> 0) */
+  double Te;            /* electron temperature: p_e = Te * n^gamma_e (Eq. 6) */
+  double gamma_e;       /* 1 isothermal, 5/3 adiabatic */
+  double eta, eta_h;    /* resistivity and hyper-resistivity (Eq. 3) */
+  double n_floor;       /* density floor n_f in Ohm's law (Sec. 2.1) */
+  int32_t shape;        /* hv_shape */
+  int32_t smooth_passes;/* binomial passes applied to deposited moments */
+  int32_t sort_every;   /* sort ions by cell every this many steps; 0 never */
+  int32_t flags;        /* reserved, must be 0 */
+  uint64_t seed;        /* reserved for stochastic extensions */
+} hv_params;
+
+/* FP64 diagnostics of the last completed step (or of the start-up state). */
+typedef struct {
+  int64_t step;      /* completed steps */
+  double t;          /* step * dt */
+  double W_K;        /* sum over ions of 1/2 m w |v^{n+1/2}|^2 */
+  double P[3];       /* sum over ions of m w v^{n+1/2} */
+  double charge;     /* sum over cells of n^{n+1/2} V_c (= sum q w) */
+  double W_B;        /* sum over cells of 1/2 |B^{n+1}|^2 V_c */
+  double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12) */
+  int32_t err_word;  /* device error bits: 1 CFL, 2 non-finite particle */
+  int32_t pad;
+} hv_diag_t;
+
+/* Accumulated device time per phase while profiling is on (CUDA events on
+ * the context stream), and the number of kernels launched. */
+typedef struct {
+  double ms_sort, ms_push, ms_moments, ms_field, ms_ohm, ms_diag;
+  int64_t n_sort, n_push, n_moments, n_field, n_ohm, n_diag; /* launches */
+  int64_t steps;
+  int64_t launches;  /* all library kernel launches since profiling began */
+} hv_prof_t;
+
+/* Device allocation hook used for every library-owned buffer.  alloc returns
+ * NULL on failure.  `stream` is the context stream (cudaStream_t).  When no
+ * hook is installed the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef void *(*hv_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*hv_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Install (or, with NULLs, remove) the process-wide allocation hook.  Takes
+ * effect for allocations made by later calls. */
+hv_status hv_set_allocator(hv_alloc_fn alloc, hv_free_fn free_fn, void *user);
+
+/* Create a context for the grid and physics in *p on the current CUDA device.
+ * B0_host: initial magnetic field [3][nz][ny][nx] in host memory, or NULL for
+ * the uniform field (1, 0, 0).  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Validates p (HV_EINVAL) and the whistler time-step limit
+ * Omega_ci (dt/nsub) < min(dx,dy,dz)^2 / pi over axes with more than one cell
+ * (Sec. 2.1; HV_ECFL).  On success *out owns the device state. */
+hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stream,
+                       hv_ctx **out);
+
+/* Append ion species number `species` (must equal the number of species
+ * already loaded; up to 8) with charge q and mass m (q_s = Z_s e, m_s; Sec.
+ * 2.1) and n macro-particles: cell[n] int32 in [0, ncell), off3 [3][n]
+ * relative coordinates in [-1, 1) (ignored along single-cell axes),
+ * v3 [3][n] velocities v^{-1/2}, w[n] weights (Sec. 2.2).  Every value is
+ * checked on the host (HV_EINVAL on a bad index, offset or non-finite value);
+ * device inputs are copied to the host for the check.  Only before the first
+ * step (HV_ESTATE afterwards). */
+hv_status hv_load_ions(hv_ctx *ctx, int32_t species, double q, double m, int64_t n,
+                       const int32_t *cell, const float *off3, const float *v3,
+                       const float *w, int on_device);
+
+/* Enqueue nsteps full steps on the context stream and return without
+ * waiting.  The first call also performs the start-up: moments of the
+ * loaded ions at x^0 with v^{-1/2} become n^{-1/2}, J^{-1/2}, and
+ * E^0 = Ohm(B^0, n^{-1/2}, J^{-1/2}).  Returns errors of argument checks and
+ * launches only; device errors appear at the next synchronising call. */
+hv_status hv_step(hv_ctx *ctx, int32_t nsteps);
+
+/* Copy the current grids out (any pointer may be NULL): n_out [nz][ny][nx]
+ * and J_out [3][...] are the last deposited (smoothed) half-step moments
+ * n^{n-1/2}, J^{n-1/2}; E_out, B_out [3][...] are E^n, B^n.  Synchronises
+ * the stream and reports latched device errors. */
+hv_status hv_moments(hv_ctx *ctx, float *n_out, float *J_out, float *E_out, float *B_out,
+                     int on_device);
+
+/* FP64 diagnostics of the state after the last step (Secs. 2.1-2.2).
+ * Synchronises; returns HV_ECFL / HV_ENAN when the error word or a
+ * diagnostic says so (the struct is still filled). */
+hv_status hv_diag(hv_ctx *ctx, hv_diag_t *out);
+
+/* Copy species `species` out in the library's current particle order (the
+ * order changes when ions are sorted): cell [n], off3 [3][n], v3 [3][n]
+ * (v^{n-1/2}), w [n].  Any pointer may be NULL.  n_out (may be NULL)
+ * receives the particle count.  Synchronises. */
+hv_status hv_get_ions(hv_ctx *ctx, int32_t species, int64_t *n_out, int32_t *cell,
+                      float *off3, float *v3, float *w, int on_device);
+
+/* Turn per-phase CUDA-event timing on (1) or off (0); turning it on resets
+ * the counters.  hv_profile_read synchronises and returns the totals. */
+hv_status hv_profile(hv_ctx *ctx, int enable);
+hv_status hv_profile_read(hv_ctx *ctx, hv_prof_t *out);
+
+/* Release every device buffer of the context (NULL is allowed). */
+void hv_destroy(hv_ctx *ctx);
+
+/* Stable counting sort by key, the sort the step applies to ions
+ * (spec device: it only changes FP32 summation order in the method).
+ * keys [n] int32 in [0, nkeys) on the device; perm [n] receives the gather
+ * permutation (keys[perm[i]] non-decreasing, equal keys in input order);
+ * counts [nkeys] (may be NULL) receives the number of each key.  All three
+ * pointers are device memory.  Scratch is allocated through the allocation
+ * hook and released before return.  Runs on cuda_stream and synchronises it.
+ * HV_EINVAL for n < 0, nkeys < 1 or a key out of range (checked on device,
+ * perm is then unspecified). */
+hv_status hv_sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
+                       int32_t *counts, void *cuda_stream);
+
+/* Thread-local description of the last failure (never NULL). */
+const char *hv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HV_H */

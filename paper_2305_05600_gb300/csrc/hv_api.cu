@@ -1,0 +1,615 @@
+// C ABI of libhv: argument checks, device state, and the order of kernels in
+// one step of the hybrid PIC ion loop (Sec. 2.2 of the paper):
+//   [sort] -> push/gather/deposit -> moment post (fold, smoothing, Eq. 11)
+//   -> nsub x 2 Ohm/Faraday stages (Eq. 5, explicit midpoint) -> final Ohm.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hv_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err = "no error";
+hv_alloc_fn g_alloc = nullptr;
+hv_free_fn g_free = nullptr;
+void *g_user = nullptr;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+namespace hv {
+
+hv_status fail(hv_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+hv_status cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? HV_ENOMEM : HV_ECUDA;
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 256;
+  if (g_alloc) return g_alloc(bytes, (void *)s, g_user);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (g_free) {
+    g_free(p, bytes, (void *)s, g_user);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+}  // namespace hv
+
+using namespace hv;
+
+namespace {
+
+void *ctx_alloc(hv_ctx *c, size_t bytes) {
+  if (c->nallocs >= 64) return nullptr;
+  void *p = dev_alloc(bytes, c->stream);
+  if (p) {
+    c->allocs[c->nallocs] = p;
+    c->alloc_bytes[c->nallocs] = bytes;
+    c->nallocs++;
+  }
+  return p;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+hv_status check_params(const hv_params *p) {
+  if (!p) return fail(HV_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(HV_EINVAL, "nx, ny, nz must be >= 1");
+  if ((int64_t)p->nx * p->ny * p->nz >= ((int64_t)1 << 31) ||
+      (int64_t)(p->nx + 2) * (p->ny + 2) * (p->nz + 2) >= ((int64_t)1 << 30))
+    return fail(HV_EINVAL, "grid too large (cell indices are int32)");
+  if (p->nsub < 1) return fail(HV_EINVAL, "nsub must be >= 1");
+  if (!finite_pos(p->dx) || !finite_pos(p->dy) || !finite_pos(p->dz) || !finite_pos(p->dt))
+    return fail(HV_EINVAL, "dx, dy, dz, dt must be finite and > 0");
+  if (!std::isfinite(p->Te) || p->Te < 0) return fail(HV_EINVAL, "Te must be finite and >= 0");
+  if (!finite_pos(p->gamma_e)) return fail(HV_EINVAL, "gamma_e must be > 0");
+  if (!std::isfinite(p->eta) || p->eta < 0 || !std::isfinite(p->eta_h) || p->eta_h < 0)
+    return fail(HV_EINVAL, "eta and eta_h must be finite and >= 0");
+  if (!finite_pos(p->n_floor)) return fail(HV_EINVAL, "n_floor must be > 0 (Ohm's law divides by n)");
+  if (p->shape < 0 || p->shape > 2) return fail(HV_EINVAL, "shape must be 0 (NGP), 1 (QS) or 2 (CIC)");
+  if (p->smooth_passes < 0 || p->smooth_passes > 64) return fail(HV_EINVAL, "smooth_passes in [0, 64]");
+  if (p->sort_every < 0) return fail(HV_EINVAL, "sort_every must be >= 0");
+  if (p->flags != 0) return fail(HV_EINVAL, "flags must be 0");
+  // whistler limit Omega_ci h < Delta^2 / pi (Sec. 2.1) for the field step h
+  double dmin = 1e300;
+  if (p->nx > 1) dmin = std::fmin(dmin, p->dx);
+  if (p->ny > 1) dmin = std::fmin(dmin, p->dy);
+  if (p->nz > 1) dmin = std::fmin(dmin, p->dz);
+  if (dmin < 1e300 && p->dt / p->nsub >= dmin * dmin / M_PI) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "whistler limit violated: dt/nsub = %g >= dx^2/pi = %g",
+             p->dt / p->nsub, dmin * dmin / M_PI);
+    return fail(HV_ECFL, buf);
+  }
+  return HV_OK;
+}
+
+Geom make_geom(const hv_params *p) {
+  Geom g;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.dim2 = p->ny == 1;
+  g.px = p->nx + 2;
+  g.py = g.dim2 ? 1 : p->ny + 2;
+  g.pz = p->nz + 2;
+  g.sx = 1;
+  g.sy = g.px;
+  g.sz = g.px * g.py;
+  g.ncell = p->nx * p->ny * p->nz;
+  g.npad = g.px * g.py * g.pz;
+  g.div_nx = make_fastdiv((uint32_t)p->nx);
+  g.div_ny = make_fastdiv((uint32_t)p->ny);
+  return g;
+}
+
+// component-major [3][ncell] <-> interleaved float4 grids, and the padded
+// gather array's E part
+__global__ void unpack4_kernel(int ncell, const float4 *in, int ncomp, int first, float *out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const float4 v = in[c];
+    const float a[4] = {v.x, v.y, v.z, v.w};
+    for (int m = 0; m < ncomp; ++m) out[(size_t)m * ncell + c] = a[first + m];
+  }
+}
+
+__global__ void unpack_E_kernel(Geom g, const float4 *EB, float *out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    const int i = c % g.nx;
+    const int j = (c / g.nx) % g.ny;
+    const int k = c / (g.nx * g.ny);
+    const int p = (i + 1) + (g.dim2 ? 0 : (j + 1) * g.sy) + (k + 1) * g.sz;
+    const float4 e = EB[2 * p];
+    out[c] = e.x;
+    out[(size_t)g.ncell + c] = e.y;
+    out[(size_t)2 * g.ncell + c] = e.z;
+  }
+}
+
+int eblocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+hv_status latched(hv_ctx *c, int *word) {
+  int e = 0;
+  cudaError_t r = cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "synchronise");
+  if (word) *word = e;
+  if (e & kErrNonFinite) return fail(HV_ENAN, "a particle became non-finite");
+  if (e & kErrCfl) return fail(HV_ECFL, "a particle moved more than one cell in one step");
+  if (e & kErrIndex) return fail(HV_ECUDA, "a corrupt particle cell index was found");
+  return HV_OK;
+}
+
+hv_status startup(hv_ctx *c) {
+  for (int s = 0; s < c->nspecies; ++s) {
+    cudaError_t e = launch_push(c, s, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "start-up deposit");
+  }
+  cudaError_t e = launch_moments(c, 1);
+  if (e != cudaSuccess) return cuda_fail(e, "start-up moments");
+  e = launch_ohm_final(c, c->mext);
+  if (e != cudaSuccess) return cuda_fail(e, "start-up Ohm");
+  c->started = 1;
+  return HV_OK;
+}
+
+struct StepEvents {
+  cudaEvent_t e[6];
+  int64_t launches[5];
+};
+
+}  // namespace
+
+// per-context profiling records (kept outside the POD context)
+namespace {
+struct ProfStore {
+  hv_ctx *owner;
+  std::vector<StepEvents> rec;
+  std::vector<cudaEvent_t> pool;
+};
+std::vector<ProfStore *> g_prof;
+
+ProfStore *prof_store(hv_ctx *c, bool create) {
+  for (auto *p : g_prof)
+    if (p->owner == c) return p;
+  if (!create) return nullptr;
+  ProfStore *p = new ProfStore();
+  p->owner = c;
+  g_prof.push_back(p);
+  return p;
+}
+
+cudaEvent_t prof_event(ProfStore *ps) {
+  if (!ps->pool.empty()) {
+    cudaEvent_t e = ps->pool.back();
+    ps->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_recycle(ProfStore *ps) {
+  for (auto &r : ps->rec)
+    for (int i = 0; i < 6; ++i) ps->pool.push_back(r.e[i]);
+  ps->rec.clear();
+}
+
+void prof_destroy(hv_ctx *c) {
+  for (size_t i = 0; i < g_prof.size(); ++i) {
+    if (g_prof[i]->owner == c) {
+      prof_recycle(g_prof[i]);
+      for (auto e : g_prof[i]->pool) cudaEventDestroy(e);
+      delete g_prof[i];
+      g_prof.erase(g_prof.begin() + i);
+      return;
+    }
+  }
+}
+}  // namespace
+
+extern "C" {
+
+hv_status hv_set_allocator(hv_alloc_fn alloc, hv_free_fn free_fn, void *user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(HV_EINVAL, "alloc and free hooks must be given together");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_user = user;
+  return HV_OK;
+}
+
+const char *hv_last_error(void) { return g_err.c_str(); }
+
+hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stream,
+                       hv_ctx **out) {
+  if (!out) return fail(HV_EINVAL, "out is NULL");
+  *out = nullptr;
+  hv_status st = check_params(p);
+  if (st != HV_OK) return st;
+  hv_ctx *c = new hv_ctx();
+  memset((void *)c, 0, sizeof(hv_ctx));
+  c->p = *p;
+  c->g = make_geom(p);
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&c->device);
+  c->vc = p->dx * p->dy * p->dz;
+  c->push_blocks = push_grid_blocks(c->device);
+  c->grid_blocks = grid_reduce_blocks(c->device);
+  const Geom &g = c->g;
+  const size_t npad = (size_t)g.npad, nc = (size_t)g.ncell;
+  c->EB = (float4 *)ctx_alloc(c, sizeof(float4) * 2 * npad);
+  c->acc = (float4 *)ctx_alloc(c, sizeof(float4) * npad);
+  c->B = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->Bs = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->mhalf = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->mext = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->mprev = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->mtmp = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  c->pushpart = (double *)ctx_alloc(c, sizeof(double) * kMaxSpecies * c->push_blocks * 4);
+  c->gridpart = (double *)ctx_alloc(c, sizeof(double) * c->grid_blocks * 4);
+  c->diag_dev = (double *)ctx_alloc(c, sizeof(double) * 8);
+  c->err = (int *)ctx_alloc(c, sizeof(int));
+  if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
+      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err) {
+    hv_destroy(c);
+    return fail(HV_ENOMEM, "grid allocation failed");
+  }
+  cudaMemsetAsync(c->EB, 0, sizeof(float4) * 2 * npad, c->stream);
+  cudaMemsetAsync(c->acc, 0, sizeof(float4) * npad, c->stream);
+  cudaMemsetAsync(c->mprev, 0, sizeof(float4) * nc, c->stream);
+  cudaMemsetAsync(c->mext, 0, sizeof(float4) * nc, c->stream);
+  cudaMemsetAsync(c->pushpart, 0, sizeof(double) * kMaxSpecies * c->push_blocks * 4, c->stream);
+  cudaMemsetAsync(c->diag_dev, 0, sizeof(double) * 8, c->stream);
+  cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  std::vector<float4> hb(nc);
+  for (size_t i = 0; i < nc; ++i) {
+    if (B0_host) {
+      hb[i] = make_float4(B0_host[i], B0_host[nc + i], B0_host[2 * nc + i], 0.f);
+      if (!std::isfinite(hb[i].x) || !std::isfinite(hb[i].y) || !std::isfinite(hb[i].z)) {
+        hv_destroy(c);
+        return fail(HV_EINVAL, "B0 has a non-finite value");
+      }
+    } else {
+      hb[i] = make_float4(1.f, 0.f, 0.f, 0.f);
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(c->B, hb.data(), sizeof(float4) * nc, cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    hv_destroy(c);
+    return cuda_fail(e, "hv_init_grid upload");
+  }
+  *out = c;
+  return HV_OK;
+}
+
+hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n,
+                       const int32_t *cell, const float *off3, const float *v3, const float *w,
+                       int on_device) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (c->started) return fail(HV_ESTATE, "ions must be loaded before the first step");
+  if (species != c->nspecies || species >= kMaxSpecies)
+    return fail(HV_EINVAL, "species must be the next index (at most 8 species)");
+  if (!std::isfinite(q) || !std::isfinite(m) || m <= 0 || q == 0)
+    return fail(HV_EINVAL, "q must be finite and non-zero, m finite and > 0");
+  if (n < 0 || n >= ((int64_t)1 << 31) - 4) return fail(HV_EINVAL, "n must be in [0, 2^31 - 4)");
+  if (n > 0 && (!cell || !off3 || !v3 || !w)) return fail(HV_EINVAL, "null particle array");
+  const Geom &g = c->g;
+  // host copies for validation (and upload)
+  std::vector<int32_t> hc(n);
+  std::vector<float> ho(3 * n), hv_(3 * n), hw(n);
+  if (n > 0) {
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    cudaError_t e = cudaMemcpy(hc.data(), cell, sizeof(int32_t) * n, k);
+    if (e == cudaSuccess) e = cudaMemcpy(ho.data(), off3, sizeof(float) * 3 * n, k);
+    if (e == cudaSuccess) e = cudaMemcpy(hv_.data(), v3, sizeof(float) * 3 * n, k);
+    if (e == cudaSuccess) e = cudaMemcpy(hw.data(), w, sizeof(float) * n, k);
+    if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions copy");
+  }
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  for (int64_t i = 0; i < n; ++i) {
+    if (hc[i] < 0 || hc[i] >= g.ncell) return fail(HV_EINVAL, "cell index out of range");
+    for (int a = 0; a < 3; ++a) {
+      float &o = ho[a * n + i];
+      if (dims[a] == 1 || (a == 1 && g.dim2)) {
+        o = 0.f;  // single-cell axis: coordinate is irrelevant
+      } else if (!(o >= -1.f && o < 1.f)) {
+        return fail(HV_EINVAL, "relative coordinate outside [-1, 1) or non-finite");
+      }
+      if (!std::isfinite(hv_[a * n + i])) return fail(HV_EINVAL, "non-finite velocity");
+    }
+    if (!std::isfinite(hw[i])) return fail(HV_EINVAL, "non-finite weight");
+  }
+  Species &sp = c->sp[species];
+  sp.q = q;
+  sp.m = m;
+  sp.n = n;
+  sp.cap = ((n + 3) / 4) * 4;
+  if (sp.cap == 0) sp.cap = 4;
+  const size_t arr = align256(sizeof(float) * sp.cap);
+  const int narr = g.dim2 ? 7 : 8;
+  std::vector<float> zeros;
+  for (int b = 0; b < 2; ++b) {
+    sp.bytes[b] = arr * narr;
+    sp.base[b] = dev_alloc(sp.bytes[b], c->stream);
+    if (!sp.base[b]) return fail(HV_ENOMEM, "particle allocation failed");
+    cudaMemsetAsync(sp.base[b], 0, sp.bytes[b], c->stream);
+    char *p = (char *)sp.base[b];
+    Soa &s = sp.buf[b];
+    int slot = 0;
+    s.cell = (int32_t *)(p + arr * slot++);
+    s.ox = (float *)(p + arr * slot++);
+    s.oy = g.dim2 ? nullptr : (float *)(p + arr * slot++);
+    s.oz = (float *)(p + arr * slot++);
+    s.vx = (float *)(p + arr * slot++);
+    s.vy = (float *)(p + arr * slot++);
+    s.vz = (float *)(p + arr * slot++);
+    s.w = (float *)(p + arr * slot++);
+  }
+  c->nspecies++;
+  sp.cur = 0;
+  if (n > 0) {
+    Soa &s = sp.buf[0];
+    cudaError_t e = cudaMemcpyAsync(s.cell, hc.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.ox, ho.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && s.oy)
+      e = cudaMemcpyAsync(s.oy, ho.data() + n, 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.oz, ho.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.vx, hv_.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.vy, hv_.data() + n, 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.vz, hv_.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.w, hw.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions upload");
+  }
+  return HV_OK;
+}
+
+hv_status hv_step(hv_ctx *c, int32_t nsteps) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(HV_EINVAL, "nsteps must be >= 0");
+  if (!c->started) {
+    hv_status st = startup(c);
+    if (st != HV_OK) return st;
+  }
+  ProfStore *ps = c->prof_on ? prof_store(c, true) : nullptr;
+  const float h = (float)(c->p.dt / c->p.nsub);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    StepEvents ev;
+    int64_t l0 = c->launches;
+    if (ps) {
+      for (int i = 0; i < 6; ++i) ev.e[i] = prof_event(ps);
+      cudaEventRecord(ev.e[0], c->stream);
+    }
+    if (c->p.sort_every > 0 && c->step % c->p.sort_every == 0) {
+      for (int sp = 0; sp < c->nspecies; ++sp) {
+        hv_status st = sort_species(c, sp);
+        if (st != HV_OK) return st;
+      }
+    }
+    if (ps) {
+      cudaEventRecord(ev.e[1], c->stream);
+      ev.launches[0] = c->launches - l0;
+      l0 = c->launches;
+    }
+    for (int sp = 0; sp < c->nspecies; ++sp) {
+      cudaError_t e = launch_push(c, sp, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "push");
+    }
+    if (ps) {
+      cudaEventRecord(ev.e[2], c->stream);
+      ev.launches[1] = c->launches - l0;
+      l0 = c->launches;
+    }
+    cudaError_t e = launch_moments(c, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "moments");
+    if (ps) {
+      cudaEventRecord(ev.e[3], c->stream);
+      ev.launches[2] = c->launches - l0;
+      l0 = c->launches;
+    }
+    for (int k = 0; k < c->p.nsub; ++k) {
+      e = launch_field_stage(c, c->B, c->B, c->Bs, 0.5f * h);
+      if (e == cudaSuccess) e = launch_field_stage(c, c->Bs, c->B, c->B, h);
+      if (e != cudaSuccess) return cuda_fail(e, "field stage");
+    }
+    if (ps) {
+      cudaEventRecord(ev.e[4], c->stream);
+      ev.launches[3] = c->launches - l0;
+      l0 = c->launches;
+    }
+    e = launch_ohm_final(c, c->mext);
+    if (e != cudaSuccess) return cuda_fail(e, "final Ohm");
+    if (ps) {
+      cudaEventRecord(ev.e[5], c->stream);
+      ev.launches[4] = c->launches - l0;
+      ps->rec.push_back(ev);
+    }
+    c->step++;
+  }
+  return HV_OK;
+}
+
+hv_status hv_moments(hv_ctx *c, float *n_out, float *J_out, float *E_out, float *B_out,
+                     int on_device) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (!c->started) {
+    hv_status st = startup(c);
+    if (st != HV_OK) return st;
+  }
+  const Geom &g = c->g;
+  const size_t nc = (size_t)g.ncell;
+  float *tmp = (float *)dev_alloc(sizeof(float) * 4 * nc, c->stream);
+  if (!tmp) return fail(HV_ENOMEM, "hv_moments scratch");
+  cudaError_t e = cudaSuccess;
+  struct Job {
+    float *dst;
+    int kind;
+  } jobs[4] = {{n_out, 0}, {J_out, 1}, {E_out, 2}, {B_out, 3}};
+  for (auto &jb : jobs) {
+    if (!jb.dst || e != cudaSuccess) continue;
+    int ncomp = jb.kind == 0 ? 1 : 3;
+    if (jb.kind == 0) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->mprev, 1, 0, tmp);
+    if (jb.kind == 1) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->mprev, 3, 1, tmp);
+    if (jb.kind == 2) unpack_E_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g, c->EB, tmp);
+    if (jb.kind == 3) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->B, 3, 0, tmp);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(jb.dst, tmp, sizeof(float) * ncomp * nc,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  }
+  dev_free(tmp, sizeof(float) * 4 * nc, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_moments");
+  return latched(c, nullptr);
+}
+
+hv_status hv_diag(hv_ctx *c, hv_diag_t *out) {
+  if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
+  if (!c->started) {
+    hv_status st = startup(c);
+    if (st != HV_OK) return st;
+  }
+  cudaError_t e = launch_diag(c);
+  double d[8] = {0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d, c->diag_dev, sizeof(double) * 7, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_diag");
+  int word = 0;
+  hv_status st = latched(c, &word);
+  memset(out, 0, sizeof(*out));
+  out->step = c->step;
+  out->t = c->step * c->p.dt;
+  out->W_K = d[0];
+  out->P[0] = d[1];
+  out->P[1] = d[2];
+  out->P[2] = d[3];
+  out->charge = d[4];
+  out->W_B = d[5];
+  out->max_divB = d[6];
+  out->err_word = word;
+  if (st != HV_OK) return st;
+  for (int i = 0; i < 7; ++i)
+    if (!std::isfinite(d[i])) return fail(HV_ENAN, "non-finite diagnostic");
+  return HV_OK;
+}
+
+hv_status hv_get_ions(hv_ctx *c, int32_t species, int64_t *n_out, int32_t *cell, float *off3,
+                      float *v3, float *w, int on_device) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (species < 0 || species >= c->nspecies) return fail(HV_EINVAL, "no such species");
+  Species &sp = c->sp[species];
+  if (n_out) *n_out = sp.n;
+  const int64_t n = sp.n;
+  const Soa &s = sp.buf[sp.cur];
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void *dst, const void *src) {
+    if (dst && e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dst, src, 4 * n, k, c->stream);
+  };
+  cp(cell, s.cell);
+  if (off3) {
+    cp(off3, s.ox);
+    if (s.oy) {
+      cp(off3 + n, s.oy);
+    } else if (n > 0 && e == cudaSuccess) {
+      e = on_device ? cudaMemsetAsync(off3 + n, 0, 4 * n, c->stream)
+                    : (memset(off3 + n, 0, 4 * n), cudaSuccess);
+    }
+    cp(off3 + 2 * n, s.oz);
+  }
+  if (v3) {
+    cp(v3, s.vx);
+    cp(v3 + n, s.vy);
+    cp(v3 + 2 * n, s.vz);
+  }
+  cp(w, s.w);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_get_ions");
+  return latched(c, nullptr);
+}
+
+hv_status hv_profile(hv_ctx *c, int enable) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  ProfStore *ps = prof_store(c, true);
+  cudaStreamSynchronize(c->stream);
+  prof_recycle(ps);
+  memset(&c->prof, 0, sizeof(c->prof));
+  c->prof_on = enable ? 1 : 0;
+  c->prof.launches = 0;
+  c->launches = 0;
+  return HV_OK;
+}
+
+hv_status hv_profile_read(hv_ctx *c, hv_prof_t *out) {
+  if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
+  ProfStore *ps = prof_store(c, true);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_profile_read");
+  for (auto &r : ps->rec) {
+    float ms[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], r.e[i], r.e[i + 1]);
+    c->prof.ms_sort += ms[0];
+    c->prof.ms_push += ms[1];
+    c->prof.ms_moments += ms[2];
+    c->prof.ms_field += ms[3];
+    c->prof.ms_ohm += ms[4];
+    c->prof.n_sort += r.launches[0];
+    c->prof.n_push += r.launches[1];
+    c->prof.n_moments += r.launches[2];
+    c->prof.n_field += r.launches[3];
+    c->prof.n_ohm += r.launches[4];
+    c->prof.steps += 1;
+  }
+  prof_recycle(ps);
+  c->prof.launches = c->launches;
+  *out = c->prof;
+  return HV_OK;
+}
+
+void hv_destroy(hv_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  prof_destroy(c);
+  for (int s = 0; s < c->nspecies; ++s)
+    for (int b = 0; b < 2; ++b) dev_free(c->sp[s].base[b], c->sp[s].bytes[b], c->stream);
+  sort_release(c);
+  for (int i = 0; i < c->nallocs; ++i) dev_free(c->allocs[i], c->alloc_bytes[i], c->stream);
+  cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+hv_status hv_sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
+                       int32_t *counts, void *cuda_stream) {
+  return sort_keys(keys, n, nkeys, perm, counts, (cudaStream_t)cuda_stream, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,523 @@
+// Grid kernels of the hybrid PIC step on the cell-centred grid (Sec. 2.2):
+//  * moment post: fold the ghost layer of the deposit accumulator back onto
+//    the periodic interior, optional binomial smoothing, linear
+//    extrapolation (Eq. 11);
+//  * field stage: one fused explicit-midpoint stage of the subcycled
+//    Faraday update (Eq. 5) with E from Ohm's law (Eqs. 2-4, 6) and the
+//    density floor, computed tile by tile in shared memory (halo 3: J = curl B
+//    needs B at +-1, the hyper-resistive Laplacian needs J at +-1, and curl E
+//    needs E at +-1);
+//  * final Ohm: E^{n+1} written with B^{n+1} into the ghost-padded gather
+//    array;
+//  * diagnostics: FP64 block partials of sum |B|^2/2 V_c, sum n V_c and
+//    max |div B|, reduced in a fixed order with the particle partials.
+#include "hv_internal.cuh"
+
+namespace hv {
+namespace {
+
+__device__ __forceinline__ int wrapn(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ void decode(const Geom &g, int c, int &i, int &j, int &k) {
+  const int q = (int)fdiv((uint32_t)c, g.div_nx);
+  i = c - q * g.nx;
+  k = (int)fdiv((uint32_t)q, g.div_ny);
+  j = q - k * g.ny;
+}
+
+// Padded coordinates that represent interior coordinate i on an axis of n
+// cells: itself, plus the low ghost if i is the last cell and the high ghost
+// if i is the first.  Returns the count (1..3).
+__device__ __forceinline__ int images(int i, int n, int *out) {
+  int c = 0;
+  out[c++] = i + 1;
+  if (i == n - 1) out[c++] = 0;
+  if (i == 0) out[c++] = n + 1;
+  return c;
+}
+
+struct MomArgs {
+  Geom g;
+  float4 *acc;
+  const float4 *prev_in;  // n^{n-1/2}, J^{n-1/2}
+  float4 *raw_out;        // folded deposit (when smoothing follows)
+  float4 *prev_out;       // n^{n+1/2}, J^{n+1/2}
+  float4 *ext_out;        // extrapolated n^{n+1}, J^{n+1}
+  int fuse;               // 1: fold + extrapolate in one pass
+  int init;               // 1: start-up (prev := ext := deposit)
+};
+
+// Fold the padded accumulator onto the interior, zero it for the next step,
+// and (fused) extrapolate: ext = 3/2 half - 1/2 prev (Eq. 11).
+__global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
+  const Geom &g = a.g;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, c, i, j, k);
+    int xs[3], ys[3], zs[3];
+    const int nxs = images(i, g.nx, xs);
+    const int nys = g.dim2 ? 1 : images(j, g.ny, ys);
+    if (g.dim2) ys[0] = 0;
+    const int nzs = images(k, g.nz, zs);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int a3 = 0; a3 < nzs; ++a3)
+      for (int a2 = 0; a2 < nys; ++a2)
+        for (int a1 = 0; a1 < nxs; ++a1) {
+          const int p = xs[a1] + (g.dim2 ? 0 : ys[a2] * g.sy) + zs[a3] * g.sz;
+          const float4 v = a.acc[p];
+          m.x += v.x;
+          m.y += v.y;
+          m.z += v.z;
+          m.w += v.w;
+          a.acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    if (!a.fuse) {
+      a.raw_out[c] = m;
+      continue;
+    }
+    if (a.init) {
+      a.prev_out[c] = m;
+      a.ext_out[c] = m;
+      continue;
+    }
+    const float4 pv = a.prev_in[c];
+    a.ext_out[c] = make_float4(1.5f * m.x - 0.5f * pv.x, 1.5f * m.y - 0.5f * pv.y,
+                               1.5f * m.z - 0.5f * pv.z, 1.5f * m.w - 0.5f * pv.w);
+    a.prev_out[c] = m;
+  }
+}
+
+// One pass of the separable (1/4, 1/2, 1/4) binomial filter along every
+// axis with more than one cell (tensor-product stencil), periodic.
+__global__ void __launch_bounds__(256) smooth_kernel(Geom g, const float4 *in, float4 *out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, c, i, j, k);
+    const float wts[3] = {0.25f, 0.5f, 0.25f};
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int kk = wrapn(k + dz, g.nz);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int jj = wrapn(j + dy, g.ny);
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ii = wrapn(i + dx, g.nx);
+          const float w = wts[dx + 1] * wts[dy + 1] * wts[dz + 1];
+          const float4 v = in[ii + g.nx * (jj + g.ny * kk)];
+          s.x = fmaf(w, v.x, s.x);
+          s.y = fmaf(w, v.y, s.y);
+          s.z = fmaf(w, v.z, s.z);
+          s.w = fmaf(w, v.w, s.w);
+        }
+      }
+    }
+    out[c] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) extrap_kernel(int ncell, const float4 *half,
+                                                     const float4 *prev_in, float4 *prev_out,
+                                                     float4 *ext_out, int init) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const float4 m = half[c];
+    if (init) {
+      prev_out[c] = m;
+      ext_out[c] = m;
+      continue;
+    }
+    const float4 pv = prev_in[c];
+    ext_out[c] = make_float4(1.5f * m.x - 0.5f * pv.x, 1.5f * m.y - 0.5f * pv.y,
+                             1.5f * m.z - 0.5f * pv.z, 1.5f * m.w - 0.5f * pv.w);
+    prev_out[c] = m;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Ohm's law + Faraday stage, tiled in shared memory
+// ----------------------------------------------------------------------------
+
+struct FieldConsts {
+  float idx2, idy2, idz2;       // 1 / (2 Delta) per axis (0 on single-cell axes)
+  float ilx, ily, ilz;          // 1 / Delta^2 per axis (0 on single-cell axes)
+  float Te, gamma_e, eta, eta_h, n_floor;
+  int isothermal;
+};
+
+struct StageArgs {
+  Geom g;
+  FieldConsts k;
+  const float4 *Bin;
+  const float4 *Bbase;
+  float4 *Bout;
+  const float4 *mom;  // {n, Jix, Jiy, Jiz}
+  float coef;         // B_out = B_base - coef * curl E
+  float4 *EB;         // final variant: padded gather array
+};
+
+// Output tile and halos.  FINAL = 0: stage (E on halo 1, B on halo 3);
+// FINAL = 1: E on the tile itself (B on halo 2).  DIM = 2: x-z plane.
+template <int DIM, int FINAL>
+struct Tile {
+  static constexpr int OX = DIM == 2 ? 32 : 8;
+  static constexpr int OY = DIM == 2 ? 1 : 8;
+  static constexpr int OZ = DIM == 2 ? 8 : 4;
+  static constexpr int HE = FINAL ? 0 : 1;  // E halo
+  static constexpr int HJ = HE + 1;         // J, n halo
+  static constexpr int HB = HE + 2;         // B halo
+  static constexpr int HY = DIM == 2 ? 0 : 1;  // y halos scale by this
+  template <int H>
+  struct R {
+    static constexpr int X = OX + 2 * H, Y = OY + 2 * H * HY, Z = OZ + 2 * H;
+    static constexpr int N = X * Y * Z;
+  };
+  static constexpr int NB = R<HB>::N, NJ = R<HJ>::N, NE = R<HE>::N;
+  static constexpr size_t smem_floats = 3 * NB + 3 * NJ + 2 * NJ + 3 * NE;
+};
+
+template <int DIM, int FINAL>
+__global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
+  using T = Tile<DIM, FINAL>;
+  using RB = typename T::template R<T::HB>;
+  using RJ = typename T::template R<T::HJ>;
+  using RE = typename T::template R<T::HE>;
+  extern __shared__ float sm[];
+  float *Bx = sm, *By = Bx + RB::N, *Bz = By + RB::N;
+  float *Jx = Bz + RB::N, *Jy = Jx + RJ::N, *Jz = Jy + RJ::N;
+  float *nf = Jz + RJ::N, *pe = nf + RJ::N;
+  float *Ex = pe + RJ::N, *Ey = Ex + RE::N, *Ez = Ey + RE::N;
+  const Geom &g = a.g;
+  const FieldConsts &k = a.k;
+
+  const int ntx = (g.nx + T::OX - 1) / T::OX;
+  const int nty = DIM == 2 ? 1 : (g.ny + T::OY - 1) / T::OY;
+  const int bid = blockIdx.x;
+  const int tx = bid % ntx;
+  const int ty = (bid / ntx) % nty;
+  const int tz = bid / (ntx * nty);
+  const int x0 = tx * T::OX, y0 = ty * T::OY, z0 = tz * T::OZ;
+
+  // global interior index of a tile-relative coordinate (periodic)
+  auto gidx = [&](int lx, int ly, int lz) {
+    const int ii = wrapn(x0 + lx, g.nx);
+    const int jj = DIM == 2 ? 0 : wrapn(y0 + ly, g.ny);
+    const int kk = wrapn(z0 + lz, g.nz);
+    return ii + g.nx * (jj + g.ny * kk);
+  };
+
+  // B on the B region
+  for (int r = threadIdx.x; r < RB::N; r += blockDim.x) {
+    const int lx = r % RB::X - T::HB;
+    const int ly = (r / RB::X) % RB::Y - T::HB * T::HY;
+    const int lz = r / (RB::X * RB::Y) - T::HB;
+    const float4 b = a.Bin[gidx(lx, ly, lz)];
+    Bx[r] = b.x;
+    By[r] = b.y;
+    Bz[r] = b.z;
+  }
+  // floored density and electron pressure on the J region
+  for (int r = threadIdx.x; r < RJ::N; r += blockDim.x) {
+    const int lx = r % RJ::X - T::HJ;
+    const int ly = (r / RJ::X) % RJ::Y - T::HJ * T::HY;
+    const int lz = r / (RJ::X * RJ::Y) - T::HJ;
+    const float n = a.mom[gidx(lx, ly, lz)].x;
+    const float f = fmaxf(n, k.n_floor);
+    nf[r] = f;
+    pe[r] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
+  }
+  __syncthreads();
+
+  // J = curl B (centred, Eq. 12) on the J region
+  constexpr int sBy = RB::X, sBz = RB::X * RB::Y;
+  for (int r = threadIdx.x; r < RJ::N; r += blockDim.x) {
+    const int lx = r % RJ::X - T::HJ;
+    const int ly = (r / RJ::X) % RJ::Y - T::HJ * T::HY;
+    const int lz = r / (RJ::X * RJ::Y) - T::HJ;
+    const int b = (lx + T::HB) + (ly + T::HB * T::HY) * sBy + (lz + T::HB) * sBz;
+    const float dBz_dy = DIM == 2 ? 0.f : (Bz[b + sBy] - Bz[b - sBy]) * k.idy2;
+    const float dBx_dy = DIM == 2 ? 0.f : (Bx[b + sBy] - Bx[b - sBy]) * k.idy2;
+    const float dBy_dz = (By[b + sBz] - By[b - sBz]) * k.idz2;
+    const float dBx_dz = (Bx[b + sBz] - Bx[b - sBz]) * k.idz2;
+    const float dBz_dx = (Bz[b + 1] - Bz[b - 1]) * k.idx2;
+    const float dBy_dx = (By[b + 1] - By[b - 1]) * k.idx2;
+    Jx[r] = dBz_dy - dBy_dz;
+    Jy[r] = dBx_dz - dBz_dx;
+    Jz[r] = dBy_dx - dBx_dy;
+  }
+  __syncthreads();
+
+  // E = [-grad p_e + (J - J_i) x B] / n_f + eta J - eta_H lap J (Eqs. 2-4, 6)
+  constexpr int sJy = RJ::X, sJz = RJ::X * RJ::Y;
+  for (int r = threadIdx.x; r < RE::N; r += blockDim.x) {
+    const int lx = r % RE::X - T::HE;
+    const int ly = (r / RE::X) % RE::Y - T::HE * T::HY;
+    const int lz = r / (RE::X * RE::Y) - T::HE;
+    const int jc = (lx + T::HJ) + (ly + T::HJ * T::HY) * sJy + (lz + T::HJ) * sJz;
+    const int b = (lx + T::HB) + (ly + T::HB * T::HY) * sBy + (lz + T::HB) * sBz;
+    const float4 mi = a.mom[gidx(lx, ly, lz)];
+    const float inv = 1.f / nf[jc];
+    const float bx = Bx[b], by = By[b], bz = Bz[b];
+    const float jx = Jx[jc], jy = Jy[jc], jz = Jz[jc];
+    const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
+    const float gpx = (pe[jc + 1] - pe[jc - 1]) * k.idx2;
+    const float gpy = DIM == 2 ? 0.f : (pe[jc + sJy] - pe[jc - sJy]) * k.idy2;
+    const float gpz = (pe[jc + sJz] - pe[jc - sJz]) * k.idz2;
+    float lx_ = (Jx[jc + 1] + Jx[jc - 1] - 2.f * jx) * k.ilx +
+                (Jx[jc + sJz] + Jx[jc - sJz] - 2.f * jx) * k.ilz;
+    float ly_ = (Jy[jc + 1] + Jy[jc - 1] - 2.f * jy) * k.ilx +
+                (Jy[jc + sJz] + Jy[jc - sJz] - 2.f * jy) * k.ilz;
+    float lz_ = (Jz[jc + 1] + Jz[jc - 1] - 2.f * jz) * k.ilx +
+                (Jz[jc + sJz] + Jz[jc - sJz] - 2.f * jz) * k.ilz;
+    if (DIM == 3) {
+      lx_ += (Jx[jc + sJy] + Jx[jc - sJy] - 2.f * jx) * k.ily;
+      ly_ += (Jy[jc + sJy] + Jy[jc - sJy] - 2.f * jy) * k.ily;
+      lz_ += (Jz[jc + sJy] + Jz[jc - sJy] - 2.f * jz) * k.ily;
+    }
+    const float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
+    const float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
+    const float ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz_;
+    if (FINAL) {
+      // interior cell of the tile: write E, B into the padded gather array
+      // at the cell and at each of its ghost images
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      if (gx < g.nx && (DIM == 2 || gy < g.ny) && gz < g.nz) {
+        int xs[3], ys[3], zs[3];
+        const int nxs = images(gx, g.nx, xs);
+        const int nys = DIM == 2 ? 1 : images(gy, g.ny, ys);
+        if (DIM == 2) ys[0] = 0;
+        const int nzs = images(gz, g.nz, zs);
+        const float4 e0 = make_float4(ex, ey, ez, bx);
+        const float4 e1 = make_float4(by, bz, 0.f, 0.f);
+        for (int a3 = 0; a3 < nzs; ++a3)
+          for (int a2 = 0; a2 < nys; ++a2)
+            for (int a1 = 0; a1 < nxs; ++a1) {
+              const int p = xs[a1] + (DIM == 2 ? 0 : ys[a2] * g.sy) + zs[a3] * g.sz;
+              a.EB[2 * p] = e0;
+              a.EB[2 * p + 1] = e1;
+            }
+      }
+    } else {
+      Ex[r] = ex;
+      Ey[r] = ey;
+      Ez[r] = ez;
+    }
+  }
+  if (FINAL) return;
+  __syncthreads();
+
+  // B_out = B_base - coef * curl E on the tile (Eq. 5)
+  constexpr int sEy = RE::X, sEz = RE::X * RE::Y;
+  for (int r = threadIdx.x; r < T::OX * T::OY * T::OZ; r += blockDim.x) {
+    const int lx = r % T::OX;
+    const int ly = (r / T::OX) % T::OY;
+    const int lz = r / (T::OX * T::OY);
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    if (gx >= g.nx || (DIM == 3 && gy >= g.ny) || gz >= g.nz) continue;
+    const int e = (lx + T::HE) + (ly + T::HE * T::HY) * sEy + (lz + T::HE) * sEz;
+    const float dEz_dy = DIM == 2 ? 0.f : (Ez[e + sEy] - Ez[e - sEy]) * k.idy2;
+    const float dEx_dy = DIM == 2 ? 0.f : (Ex[e + sEy] - Ex[e - sEy]) * k.idy2;
+    const float dEy_dz = (Ey[e + sEz] - Ey[e - sEz]) * k.idz2;
+    const float dEx_dz = (Ex[e + sEz] - Ex[e - sEz]) * k.idz2;
+    const float dEz_dx = (Ez[e + 1] - Ez[e - 1]) * k.idx2;
+    const float dEy_dx = (Ey[e + 1] - Ey[e - 1]) * k.idx2;
+    const int c = gx + g.nx * ((DIM == 2 ? 0 : gy) + g.ny * gz);
+    const float4 bb = a.Bbase[c];
+    a.Bout[c] = make_float4(bb.x - a.coef * (dEz_dy - dEy_dz), bb.y - a.coef * (dEx_dz - dEz_dx),
+                            bb.z - a.coef * (dEy_dx - dEx_dy), 0.f);
+  }
+}
+
+FieldConsts field_consts(const hv_ctx *c) {
+  FieldConsts k;
+  const hv_params &p = c->p;
+  k.idx2 = p.nx > 1 ? (float)(1.0 / (2.0 * p.dx)) : 0.f;
+  k.idy2 = p.ny > 1 ? (float)(1.0 / (2.0 * p.dy)) : 0.f;
+  k.idz2 = p.nz > 1 ? (float)(1.0 / (2.0 * p.dz)) : 0.f;
+  k.ilx = p.nx > 1 ? (float)(1.0 / (p.dx * p.dx)) : 0.f;
+  k.ily = p.ny > 1 ? (float)(1.0 / (p.dy * p.dy)) : 0.f;
+  k.ilz = p.nz > 1 ? (float)(1.0 / (p.dz * p.dz)) : 0.f;
+  k.Te = (float)p.Te;
+  k.gamma_e = (float)p.gamma_e;
+  k.eta = (float)p.eta;
+  k.eta_h = (float)p.eta_h;
+  k.n_floor = (float)p.n_floor;
+  k.isothermal = p.gamma_e == 1.0;
+  return k;
+}
+
+template <int DIM, int FINAL>
+cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
+  using T = Tile<DIM, FINAL>;
+  const size_t smem = T::smem_floats * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<DIM, FINAL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int ntx = (c->g.nx + T::OX - 1) / T::OX;
+  const int nty = DIM == 2 ? 1 : (c->g.ny + T::OY - 1) / T::OY;
+  const int ntz = (c->g.nz + T::OZ - 1) / T::OZ;
+  stage_kernel<DIM, FINAL><<<ntx * nty * ntz, 256, smem, c->stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// diagnostics
+// ----------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, float vc,
+                                                        const float4 *B, const float4 *mom,
+                                                        double *part) {
+  double wb = 0.0, ch = 0.0, md = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, kk;
+    decode(g, c, i, j, kk);
+    const float4 b = B[c];
+    wb += 0.5 * ((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) * vc;
+    ch += (double)mom[c].x * vc;
+    const int xp = wrapn(i + 1, g.nx) + g.nx * (j + g.ny * kk);
+    const int xm = wrapn(i - 1, g.nx) + g.nx * (j + g.ny * kk);
+    const int yp = i + g.nx * (wrapn(j + 1, g.ny) + g.ny * kk);
+    const int ym = i + g.nx * (wrapn(j - 1, g.ny) + g.ny * kk);
+    const int zp = i + g.nx * (j + g.ny * wrapn(kk + 1, g.nz));
+    const int zm = i + g.nx * (j + g.ny * wrapn(kk - 1, g.nz));
+    const double dv = ((double)B[xp].x - B[xm].x) * k.idx2 + ((double)B[yp].y - B[ym].y) * k.idy2 +
+                      ((double)B[zp].z - B[zm].z) * k.idz2;
+    md = fmax(md, fabs(dv));
+  }
+  __shared__ double s[3][256];
+  s[0][threadIdx.x] = wb;
+  s[1][threadIdx.x] = ch;
+  s[2][threadIdx.x] = md;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + o];
+      s[1][threadIdx.x] += s[1][threadIdx.x + o];
+      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * 4 + 0] = s[0][0];
+    part[blockIdx.x * 4 + 1] = s[1][0];
+    part[blockIdx.x * 4 + 2] = s[2][0];
+    part[blockIdx.x * 4 + 3] = 0.0;
+  }
+}
+
+// One block: fixed-order sums of the grid and particle partials.
+// out: W_K, Px, Py, Pz, charge, W_B, max_divB
+__global__ void diag_final_kernel(const double *gpart, int ngb, const double *ppart, int npb,
+                                  int nspecies, double *out) {
+  __shared__ double s[7][256];
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < ngb; b += blockDim.x) {
+    v[5] += gpart[b * 4 + 0];
+    v[4] += gpart[b * 4 + 1];
+    v[6] = fmax(v[6], gpart[b * 4 + 2]);
+  }
+  for (int b = threadIdx.x; b < npb * nspecies; b += blockDim.x) {
+    for (int m = 0; m < 4; ++m) v[m] += ppart[(size_t)b * 4 + m];
+  }
+  for (int m = 0; m < 7; ++m) s[m][threadIdx.x] = v[m];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      for (int m = 0; m < 6; ++m) s[m][threadIdx.x] += s[m][threadIdx.x + o];
+      s[6][threadIdx.x] = fmax(s[6][threadIdx.x], s[6][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 7) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+}  // namespace
+
+int grid_reduce_blocks(int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return sms > 0 ? 2 * sms : 2;
+}
+
+static int elem_blocks(int n) {
+  int b = (n + 255) / 256;
+  return b < 1 ? 1 : (b > 4096 ? 4096 : b);
+}
+
+cudaError_t launch_moments(hv_ctx *c, int init) {
+  MomArgs a;
+  a.g = c->g;
+  a.acc = c->acc;
+  a.prev_in = c->mprev;
+  a.prev_out = c->mprev;
+  a.ext_out = c->mext;
+  a.raw_out = c->mtmp;
+  a.init = init;
+  const int passes = c->p.smooth_passes;
+  a.fuse = passes == 0;
+  const int nb = elem_blocks(c->g.ncell);
+  c->launches++;
+  fold_kernel<<<nb, 256, 0, c->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || passes == 0) return e;
+  float4 *src = c->mtmp, *dst = c->mhalf;
+  for (int p = 0; p < passes; ++p) {
+    c->launches++;
+    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, src, dst);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    float4 *t = src;
+    src = dst;
+    dst = t;
+  }
+  c->launches++;
+  extrap_kernel<<<nb, 256, 0, c->stream>>>(c->g.ncell, src, c->mprev, c->mprev, c->mext, init);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
+                               float coef) {
+  StageArgs a;
+  a.g = c->g;
+  a.k = field_consts(c);
+  a.Bin = Bin;
+  a.Bbase = Bbase;
+  a.Bout = Bout;
+  a.mom = c->mprev;
+  a.coef = coef;
+  a.EB = nullptr;
+  c->launches++;
+  return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
+}
+
+cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
+  StageArgs a;
+  a.g = c->g;
+  a.k = field_consts(c);
+  a.Bin = c->B;
+  a.Bbase = c->B;
+  a.Bout = nullptr;
+  a.mom = mom;
+  a.coef = 0.f;
+  a.EB = c->EB;
+  c->launches++;
+  return c->g.dim2 ? launch_stage_t<2, 1>(c, a) : launch_stage_t<3, 1>(c, a);
+}
+
+cudaError_t launch_diag(hv_ctx *c) {
+  FieldConsts k = field_consts(c);
+  c->launches += 2;
+  grid_diag_kernel<<<c->grid_blocks, 256, 0, c->stream>>>(c->g, k, (float)c->vc, c->B, c->mprev,
+                                                          c->gridpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 256, 0, c->stream>>>(c->gridpart, c->grid_blocks, c->pushpart,
+                                              c->push_blocks, c->nspecies, c->diag_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace hv

@@ -1,0 +1,386 @@
+// Stable sort of ions by cell (a device of the GPU layout: it keeps a
+// warp's particles in one or two cells so that gathers hit cache and
+// deposits aggregate; the method's result changes only through FP32
+// summation order).
+//
+// Least-significant-digit radix sort on (key, index) pairs with 8-bit
+// digits, ceil(log2(nkeys)/8) passes.  Each pass is reduce-then-scan, so no
+// kernel waits on another block:
+//   upsweep   per 4096-key tile digit counts -> table[digit][tile]
+//   scan      exclusive scan of the table in digit-major order
+//   downsweep stable per-tile ranks (warp match + per-warp counters) and
+//             scatter to table offset + rank.
+// A final gather applies the permutation to the particle arrays.
+#include <algorithm>
+
+#include "hv_internal.cuh"
+
+namespace hv {
+
+struct SortScratch {
+  int32_t *k[2], *v[2];
+  int32_t *table, *bsum;
+  int64_t cap_n, cap_table, cap_bsum;
+  void *base;
+  size_t bytes;
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kScanChunk = 4096;
+
+// Items of a tile are split into one contiguous run of 512 per warp; round r
+// of warp w covers tile items w*512 + r*32 + lane, so lane order within a
+// round and round order within a warp follow input order.
+__device__ __forceinline__ int64_t item_index(int64_t tile0, int warp, int r, int lane) {
+  return tile0 + warp * (32 * kItems) + r * 32 + lane;
+}
+
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const int32_t *keys, int64_t n,
+                                                            int shift, int64_t ntiles,
+                                                            int32_t *table) {
+  __shared__ int hist[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t idx = item_index(tile0, warp, r, lane);
+    const bool valid = idx < n;
+    const unsigned act = __ballot_sync(kFull, valid);
+    if (!valid) continue;
+    const int d = (int)(((uint32_t)keys[idx] >> shift) & 255u);
+    const unsigned peers = __match_any_sync(act, d);
+    if (lane == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
+  }
+  __syncthreads();
+  table[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Exclusive scan of a large int32 array in three steps: chunk sums, scan of
+// the sums in one block, chunk-local scans plus the chunk offset.
+__global__ void __launch_bounds__(kThreads) chunk_sum_kernel(const int32_t *a, int64_t len,
+                                                              int32_t *bsum) {
+  __shared__ int s[kThreads];
+  const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
+  int t = 0;
+  for (int i = threadIdx.x; i < kScanChunk; i += kThreads) {
+    const int64_t idx = c0 + i;
+    if (idx < len) t += a[idx];
+  }
+  s[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+}
+
+// block-wide exclusive scan of one value per thread; returns the total
+__device__ int block_exclusive_scan(int x, int *s_warp, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kWarps ? s_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kWarps) s_warp[lane] = wi - w;
+    if (lane == kWarps - 1) s_warp[kWarps] = wi;
+  }
+  __syncthreads();
+  total = s_warp[kWarps];
+  const int r = s_warp[warp] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads) scan_bsum_kernel(int32_t *bsum, int64_t nb) {
+  __shared__ int s_warp[kWarps + 1];
+  int carry = 0;
+  for (int64_t base = 0; base < nb; base += kThreads) {
+    const int64_t idx = base + threadIdx.x;
+    const int x = idx < nb ? bsum[idx] : 0;
+    int total;
+    const int ex = block_exclusive_scan(x, s_warp, total);
+    if (idx < nb) bsum[idx] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) chunk_scan_kernel(int32_t *a, int64_t len,
+                                                               const int32_t *bsum) {
+  __shared__ int s_warp[kWarps + 1];
+  const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
+  int carry = bsum[blockIdx.x];
+  constexpr int per = kScanChunk / kThreads;  // 16 consecutive values per thread
+  int v[per];
+  int t = 0;
+  for (int i = 0; i < per; ++i) {
+    const int64_t idx = c0 + (int64_t)threadIdx.x * per + i;
+    v[i] = idx < len ? a[idx] : 0;
+    t += v[i];
+  }
+  int total;
+  int ex = block_exclusive_scan(t, s_warp, total) + carry;
+  for (int i = 0; i < per; ++i) {
+    const int64_t idx = c0 + (int64_t)threadIdx.x * per + i;
+    if (idx < len) a[idx] = ex;
+    ex += v[i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys_in,
+                                                              const int32_t *vals_in, int64_t n,
+                                                              int shift, int64_t ntiles,
+                                                              const int32_t *table,
+                                                              int32_t *keys_out,
+                                                              int32_t *vals_out) {
+  __shared__ int wcount[kWarps][256];
+  __shared__ int gbase[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < kWarps; ++w) wcount[w][threadIdx.x] = 0;
+  gbase[threadIdx.x] = table[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  int key[kItems], val[kItems], rank[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t idx = item_index(tile0, warp, r, lane);
+    const bool valid = idx < n;
+    key[r] = valid ? keys_in[idx] : 0;
+    val[r] = valid ? (vals_in ? vals_in[idx] : (int)idx) : 0;
+    rank[r] = -1;
+    const unsigned act = __ballot_sync(kFull, valid);
+    if (valid) {
+      const int d = (int)(((uint32_t)key[r] >> shift) & 255u);
+      const unsigned peers = __match_any_sync(act, d);
+      const int before = wcount[warp][d];
+      rank[r] = before + __popc(peers & ((1u << lane) - 1u));
+      __syncwarp(act);
+      if (lane == __ffs(peers) - 1) wcount[warp][d] = before + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive scan over warps for each digit
+  {
+    int run = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      const int t = wcount[w][threadIdx.x];
+      wcount[w][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    if (rank[r] < 0) continue;
+    const int d = (int)(((uint32_t)key[r] >> shift) & 255u);
+    const int64_t dst = (int64_t)gbase[d] + wcount[warp][d] + rank[r];
+    keys_out[dst] = key[r];
+    vals_out[dst] = val[r];
+  }
+}
+
+// Apply the permutation to every particle array: out[i] = in[perm[i]].
+__global__ void __launch_bounds__(256) gather_kernel(Soa in, Soa out, const int32_t *perm,
+                                                     int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int src = perm[i];
+    out.cell[i] = in.cell[src];
+    out.ox[i] = in.ox[src];
+    if (in.oy) out.oy[i] = in.oy[src];
+    out.oz[i] = in.oz[src];
+    out.vx[i] = in.vx[src];
+    out.vy[i] = in.vy[src];
+    out.vz[i] = in.vz[src];
+    out.w[i] = in.w[src];
+  }
+}
+
+// Count keys (warp-aggregated atomics) and flag out-of-range keys.  The loop
+// advances whole warps together so that every lane of a warp takes part in
+// the ballot and match of each round.
+__global__ void count_kernel(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *counts,
+                             int *bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+       base += stride) {
+    const int64_t i = base + lane;
+    const int k = i < n ? keys[i] : 0;
+    const bool inrange = i < n && k >= 0 && k < nkeys;
+    if (i < n && !inrange) atomicOr(bad, 1);
+    const unsigned act = __ballot_sync(kFull, inrange);
+    if (!inrange || !counts) continue;
+    const unsigned peers = __match_any_sync(act, k);
+    if (lane == __ffs(peers) - 1) atomicAdd(&counts[k], __popc(peers));
+  }
+}
+
+int key_bits(int64_t nkeys) {
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < nkeys) ++b;
+  return b;
+}
+
+int64_t table_len(int64_t n) { return 256 * ((n + kTile - 1) / kTile); }
+
+int64_t bsum_len(int64_t len) { return (len + kScanChunk - 1) / kScanChunk; }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Size (or resize) the scratch for n keys.  Returns false on allocation
+// failure.
+bool scratch_reserve(SortScratch *&s, int64_t n, cudaStream_t st) {
+  const int64_t tl = table_len(std::max<int64_t>(n, 1));
+  const int64_t bl = bsum_len(tl);
+  if (s && s->cap_n >= n && s->cap_table >= tl && s->cap_bsum >= bl) return true;
+  if (s) {
+    dev_free(s->base, s->bytes, st);
+  } else {
+    s = new SortScratch();
+  }
+  const int64_t nn = std::max<int64_t>(n, 1);
+  const size_t kv = align256(sizeof(int32_t) * nn);
+  const size_t bytes = 4 * kv + align256(sizeof(int32_t) * tl) + align256(sizeof(int32_t) * bl);
+  char *p = (char *)dev_alloc(bytes, st);
+  if (!p) {
+    delete s;
+    s = nullptr;
+    return false;
+  }
+  s->base = p;
+  s->bytes = bytes;
+  s->k[0] = (int32_t *)p;
+  s->k[1] = (int32_t *)(p + kv);
+  s->v[0] = (int32_t *)(p + 2 * kv);
+  s->v[1] = (int32_t *)(p + 3 * kv);
+  s->table = (int32_t *)(p + 4 * kv);
+  s->bsum = (int32_t *)(p + 4 * kv + align256(sizeof(int32_t) * tl));
+  s->cap_n = nn;
+  s->cap_table = tl;
+  s->cap_bsum = bl;
+  return true;
+}
+
+// Radix passes over keys[n]; returns the buffer holding the permutation.
+cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratch *s,
+                       cudaStream_t st, int32_t **perm_out, int64_t *launches) {
+  const int bits = key_bits(nkeys);
+  const int passes = (bits + 7) / 8;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t tl = 256 * ntiles;
+  const int64_t nb = bsum_len(tl);
+  const int32_t *kin = keys;
+  const int32_t *vin = nullptr;
+  int out = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    upsweep_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, n, shift, ntiles, s->table);
+    chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, st>>>(s->table, tl, s->bsum);
+    scan_bsum_kernel<<<1, kThreads, 0, st>>>(s->bsum, nb);
+    chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(s->table, tl, s->bsum);
+    downsweep_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, vin, n, shift, ntiles, s->table,
+                                                             s->k[out], s->v[out]);
+    *launches += 5;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kin = s->k[out];
+    vin = s->v[out];
+    out ^= 1;
+  }
+  *perm_out = const_cast<int32_t *>(vin);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+hv_status sort_species(hv_ctx *c, int sidx) {
+  Species &sp = c->sp[sidx];
+  if (sp.n <= 1) return HV_OK;
+  if (!scratch_reserve(c->sort, sp.n, c->stream))
+    return fail(HV_ENOMEM, "sort scratch allocation failed");
+  int32_t *perm = nullptr;
+  Soa &in = sp.buf[sp.cur];
+  cudaError_t e = radix_perm(in.cell, sp.n, c->g.ncell, c->sort, c->stream, &perm, &c->launches);
+  if (e != cudaSuccess) return cuda_fail(e, "sort passes");
+  Soa &out = sp.buf[sp.cur ^ 1];
+  int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 1024);
+  gather_kernel<<<blocks, 256, 0, c->stream>>>(in, out, perm, sp.n);
+  c->launches++;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sort gather");
+  sp.cur ^= 1;
+  return HV_OK;
+}
+
+void sort_release(hv_ctx *c) {
+  if (c->sort) {
+    dev_free(c->sort->base, c->sort->bytes, c->stream);
+    delete c->sort;
+    c->sort = nullptr;
+  }
+}
+
+hv_status sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm, int32_t *counts,
+                    cudaStream_t st, int64_t *launches) {
+  if (n < 0 || nkeys < 1) return fail(HV_EINVAL, "hv_sort_keys: n < 0 or nkeys < 1");
+  if (n > 0 && (!keys || !perm)) return fail(HV_EINVAL, "hv_sort_keys: null pointer");
+  if (n >= ((int64_t)1 << 31)) return fail(HV_EINVAL, "hv_sort_keys: n must be < 2^31");
+  int64_t dummy = 0;
+  if (!launches) launches = &dummy;
+  int *bad = (int *)dev_alloc(sizeof(int), st);
+  if (!bad) return fail(HV_ENOMEM, "hv_sort_keys: allocation failed");
+  cudaMemsetAsync(bad, 0, sizeof(int), st);
+  hv_status rc = HV_OK;
+  SortScratch *s = nullptr;
+  if (counts) cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)nkeys, st);
+  if (n > 0) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * 1024);
+    count_kernel<<<blocks, 256, 0, st>>>(keys, n, nkeys, counts, bad);
+    ++*launches;
+  }
+  if (n > 0) {
+    if (!scratch_reserve(s, n, st)) {
+      rc = fail(HV_ENOMEM, "hv_sort_keys: scratch allocation failed");
+    } else {
+      int32_t *p = nullptr;
+      cudaError_t e = radix_perm(keys, n, nkeys, s, st, &p, launches);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(perm, p, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "hv_sort_keys");
+    }
+  }
+  int hbad = 0;
+  cudaError_t e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess && rc == HV_OK) rc = cuda_fail(e, "hv_sort_keys sync");
+  if (s) {
+    dev_free(s->base, s->bytes, st);
+    delete s;
+  }
+  dev_free(bad, sizeof(int), st);
+  if (rc == HV_OK && hbad) rc = fail(HV_EINVAL, "hv_sort_keys: key out of range");
+  return rc;
+}
+
+}  // namespace hv

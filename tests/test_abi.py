@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/hv.h declares, its structs have the declared layout,
+and host-side argument checks reject bad input before touching a GPU."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2305_05600_gb300 import hv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(hv_[a-z_]+)\s*\(", src)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_library_exports_every_declared_function():
+    L = hv.lib()
+    names = declared_functions()
+    assert "hv_step" in names and "hv_init_grid" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(hv.EXPORTS)
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(hv.Params) == 112
+    assert ctypes.sizeof(hv.Diag) == 8 * 9 + 8
+    assert ctypes.sizeof(hv.Prof) == 8 * 14
+
+
+def _params(**kw):
+    d = dict(nx=16, ny=1, nz=8, dx=0.5, dy=1.0, dz=0.5, dt=0.01, nsub=10, Te=0.1,
+             n_floor=0.05, shape="qs")
+    d.update(kw)
+    return hv.params_from(d)
+
+
+def _init_status(p):
+    out = ctypes.c_void_p()
+    rc = hv.lib().hv_init_grid(ctypes.byref(p), None, None, ctypes.byref(out))
+    return rc, out.value
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(nsub=0), dict(dx=-1.0), dict(dt=math.nan),
+                                 dict(shape=5), dict(n_floor=0.0), dict(smooth_passes=-1),
+                                 dict(Te=-1.0), dict(eta=-1e-3)])
+def test_init_rejects_bad_parameters_on_host(bad):
+    rc, h = _init_status(_params(**bad))
+    assert rc == hv.HV_EINVAL and not h
+    assert len(hv.hv_last_error()) > 0
+
+
+def test_init_rejects_whistler_limit_violation():
+    # dt/nsub = 0.1 >= dx^2/pi = 0.0796 (Sec. 2.1)
+    rc, h = _init_status(_params(dt=1.0, nsub=10))
+    assert rc == hv.HV_ECFL and not h
+    assert "whistler" in hv.hv_last_error()
+
+
+def test_sort_keys_rejects_bad_sizes_on_host():
+    L = hv.lib()
+    assert L.hv_sort_keys(None, -1, 4, None, None, None) == hv.HV_EINVAL
+    assert L.hv_sort_keys(None, 4, 0, None, None, None) == hv.HV_EINVAL
+
+
+def test_allocator_hooks_must_come_in_pairs():
+    L = hv.lib()
+    a = hv.ALLOC_FN(lambda n, s, u: None)
+    assert L.hv_set_allocator(a, hv.FREE_FN(0), None) == hv.HV_EINVAL
+    assert L.hv_set_allocator(hv.ALLOC_FN(0), hv.FREE_FN(0), None) == hv.HV_OK

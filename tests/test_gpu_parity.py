@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 push/deposit/stencils against FP64):
+  * sort permutation and cell counts: bit-exact;
+  * one-step particle states: |dv| <= 1e-5 (|v| + v_scale) and physical
+    position within 1e-5 cell widths (cells compared through positions, so a
+    particle on a face may sit on either side);
+  * deposited moments n, J: relative L2 error <= 1e-5;
+  * fields after one step: B and its one-step change, E, relative L2 (the
+    tolerance of each is stated at its assertion);
+  * energy histories: relative error <= 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_05600_gb300 import inputs as I
+from tests.helpers import oracle_sim, periodic_delta, phys_pos
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hvmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_05600_gb300 import hv
+    hv.lib()
+    hv.hv_set_allocator(True)
+    return hv
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ----------------------------------------------------------------------------
+# sort
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,nkeys,kind", [(1, 1, "rand"), (4097, 300, "rand"),
+                                           (100003, 4096, "near"), (250001, 524288, "rand"),
+                                           (65536, 3, "dup"), (0, 5, "rand")])
+def test_sort_bit_exact(hvmod, n, nkeys, kind):
+    import torch
+    rng = np.random.default_rng(n + nkeys)
+    if kind == "near":
+        keys = np.sort(rng.integers(0, nkeys, n))
+        swap = rng.random(n) < 0.05
+        keys[swap] = np.clip(keys[swap] + rng.integers(-2, 3, swap.sum()), 0, nkeys - 1)
+    else:
+        keys = rng.integers(0, nkeys, n)
+    keys = keys.astype(np.int32)
+    perm, counts = hvmod.hv_sort_keys(torch.from_numpy(keys).cuda(), nkeys)
+    operm, ocounts, _ = O.sort_stable(keys.astype(np.int64), nkeys)
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), operm)
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), ocounts)
+
+
+def test_sort_rejects_out_of_range_key(hvmod):
+    import torch
+    keys = torch.tensor([0, 1, 7, 2], dtype=torch.int32, device="cuda")
+    with pytest.raises(hvmod.HVError):
+        hvmod.hv_sort_keys(keys, 5)
+
+
+# ----------------------------------------------------------------------------
+# one step, small 2D and 3D workloads, every shape
+# ----------------------------------------------------------------------------
+
+def small_workload(dim, shape):
+    if dim == 2:
+        # 40 x 24 cells (several field tiles, ragged in x), ragged particle count
+        wl = I.harris(nx=40, nz=24, ppc=24, dx=0.25, seed=11, shape=shape, sort_every=1)
+    else:
+        wl = I.beam3d(nx=12, ny=10, nz=9, n_core=6, n_beam=3, dx=0.5, seed=12, shape=shape,
+                      sort_every=1)
+    s = wl.species[0]
+    keep = s.n - 3  # ragged tail: not a multiple of 4 or of a warp's 128
+    wl.species[0] = I.SpeciesInput(s.q, s.m, s.cell[:keep].copy(), s.off[:, :keep].copy(),
+                                   s.v[:, :keep].copy(), s.w[:keep].copy())
+    return wl
+
+
+def compare_particles(p, gpu, sp, vscale):
+    po = phys_pos(p, sp.cell, sp.off)
+    pg = phys_pos(p, gpu["cell"], gpu["off"].astype(np.float64))
+    d = periodic_delta(p, pg, po)
+    dl = np.array([p["dx"], p["dy"], p["dz"]])[:, None]
+    assert np.abs(d / dl).max() < 1e-5
+    dv = np.abs(gpu["v"].astype(np.float64) - sp.v)
+    vmag = np.linalg.norm(sp.v, axis=0)
+    assert (dv.max(axis=0) <= 1e-5 * (vmag + vscale)).all(), dv.max()
+    assert np.array_equal(gpu["w"].astype(np.float64), sp.w)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("shape", ["qs", "cic", "ngp"])
+def test_one_step_parity(hvmod, dim, shape):
+    wl = small_workload(dim, shape)
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    # start-up state: moments at x^0 and E^0
+    m0 = hvmod.hv_moments(ctx)
+    assert rel_l2(m0["n"].reshape(-1), sim.n_prev) < 1e-5
+    assert rel_l2(m0["E"].reshape(3, -1), sim.E) < 1e-4
+    hvmod.hv_step(ctx, 1)
+    sim.step(1, sort_every=1)
+    g = hvmod.hv_get_ions(ctx, 0)
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    compare_particles(p, g, sim.species[0], vscale)
+    m1 = hvmod.hv_moments(ctx)
+    # deposited half-step moments (spec bound 1e-5 relative L2)
+    assert rel_l2(m1["n"].reshape(-1), sim.n_prev) < 1e-5
+    for a in range(3):
+        assert rel_l2(m1["J"][a].reshape(-1), sim.J_prev[a]) < 1e-5
+    # B after 2*nsub stages: the one-step change to 1e-4, the field to 1e-6
+    B0 = wl.B0.astype(np.float64).reshape(3, -1)
+    Bg = m1["B"].reshape(3, -1)
+    assert rel_l2(Bg, sim.B) < 1e-6
+    assert rel_l2(Bg - B0, sim.B - B0) < 1e-4
+    # E = Ohm(B^1, extrapolated moments): divides by n and differences noisy
+    # moments, so FP32 rounding is amplified; bound 1e-4 relative L2
+    assert rel_l2(m1["E"].reshape(3, -1), sim.E) < 1e-4
+    d = hvmod.hv_diag(ctx)
+    od = sim.diags[-1]
+    assert abs(d["charge"] - od["charge"]) < 1e-6 * od["charge"]
+    assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+    assert abs(d["W_B"] - od["W_B"]) < 1e-6 * od["W_B"]
+    ctx.close()
+
+
+def test_smoothing_parity(hvmod):
+    wl = I.harris(nx=32, nz=16, ppc=16, dx=0.25, seed=21, smooth_passes=2, sort_every=1)
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    hvmod.hv_step(ctx, 2)
+    sim.step(2, sort_every=1)
+    m = hvmod.hv_moments(ctx)
+    assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+    assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+    ctx.close()
+
+
+def test_quasi_1d_and_multispecies(hvmod):
+    """nz = 1 (one-cell z axis) and two species with different q/m."""
+    wl = I.whistler1d(nx=64, ppc=32, steps=1)
+    s = wl.species[0]
+    half = s.n // 2
+    a = I.SpeciesInput(1.0, 1.0, s.cell[:half], s.off[:, :half], s.v[:, :half], s.w[:half])
+    b = I.SpeciesInput(2.0, 4.0, s.cell[half:], s.off[:, half:], s.v[:, half:],
+                       (s.w[half:] * 0.5).astype(np.float32))
+    wl.species = [a, b]
+    wl.params["sort_every"] = 1
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    hvmod.hv_step(ctx, 3)
+    sim.step(3, sort_every=1)
+    m = hvmod.hv_moments(ctx)
+    assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+    assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# energy histories
+# ----------------------------------------------------------------------------
+
+def test_energy_history_1000_steps(hvmod):
+    """W_K and W_B histories over 1000 steps of the uniform Alfven-wave
+    plasma (32x32 cells, 16 ppc), GPU (FP32) against the oracle (FP64),
+    within 1e-3 relative."""
+    wl = I.alfven2d(nx=32, nz=32, ppc=16, dx=0.5, seed=5, sort_every=20)
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    worst = {"W_K": 0.0, "W_B": 0.0}
+    for chunk in range(10):
+        hvmod.hv_step(ctx, 100)
+        sim.step(100, sort_every=20)
+        d = hvmod.hv_diag(ctx)
+        od = sim.diags[-1]
+        for key in worst:
+            worst[key] = max(worst[key], abs(d[key] - od[key]) / abs(od[key]))
+    assert worst["W_K"] < 1e-3 and worst["W_B"] < 1e-3, worst
+    ctx.close()
+
+
+def test_alfven_config_200_steps(hvmod):
+    """The full 64x64, 64-ppc Alfven-wave workload for its 200 steps:
+    charge, div B and energies against the oracle."""
+    wl = I.alfven2d()
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    hvmod.hv_step(ctx, 200)
+    sim.step(200, sort_every=wl.params["sort_every"])
+    d = hvmod.hv_diag(ctx)
+    od = sim.diags[-1]
+    for key in ("W_K", "W_B", "charge"):
+        assert abs(d[key] - od[key]) < 1e-3 * abs(od[key]), (key, d[key], od[key])
+    assert d["max_divB"] < 1e-3
+    ctx.close()
