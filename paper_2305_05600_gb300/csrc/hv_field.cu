@@ -21,6 +21,13 @@ __device__ __forceinline__ int wrapn(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// Periodic wrap of a coordinate at most `h` cells outside [0, n): two
+// compares instead of a division when n >= h.
+__device__ __forceinline__ int wrap_near(int i, int n, int h) {
+  if (n >= h) return i < 0 ? i + n : (i >= n ? i - n : i);
+  return wrapn(i, n);
+}
+
 __device__ __forceinline__ void decode(const Geom &g, int c, int &i, int &j, int &k) {
   const int q = (int)fdiv((uint32_t)c, g.div_nx);
   i = c - q * g.nx;
@@ -162,7 +169,7 @@ template <int DIM, int FINAL>
 struct Tile {
   static constexpr int OX = DIM == 2 ? 32 : 8;
   static constexpr int OY = DIM == 2 ? 1 : 8;
-  static constexpr int OZ = DIM == 2 ? 8 : 4;
+  static constexpr int OZ = DIM == 2 ? 16 : 4;
   static constexpr int HE = FINAL ? 0 : 1;  // E halo
   static constexpr int HJ = HE + 1;         // J, n halo
   static constexpr int HB = HE + 2;         // B halo
@@ -198,11 +205,12 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   const int tz = bid / (ntx * nty);
   const int x0 = tx * T::OX, y0 = ty * T::OY, z0 = tz * T::OZ;
 
-  // global interior index of a tile-relative coordinate (periodic)
+  // global interior index of a tile-relative coordinate (periodic; tiles
+  // may overhang the grid by up to one tile minus a cell, halos by HB)
   auto gidx = [&](int lx, int ly, int lz) {
-    const int ii = wrapn(x0 + lx, g.nx);
-    const int jj = DIM == 2 ? 0 : wrapn(y0 + ly, g.ny);
-    const int kk = wrapn(z0 + lz, g.nz);
+    const int ii = wrap_near(x0 + lx, g.nx, T::OX + T::HB);
+    const int jj = DIM == 2 ? 0 : wrap_near(y0 + ly, g.ny, T::OY + T::HB);
+    const int kk = wrap_near(z0 + lz, g.nz, T::OZ + T::HB);
     return ii + g.nx * (jj + g.ny * kk);
   };
 

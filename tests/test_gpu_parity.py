@@ -152,9 +152,12 @@ def test_quasi_1d_and_multispecies(hvmod):
     wl = I.whistler1d(nx=64, ppc=32, steps=1)
     s = wl.species[0]
     half = s.n // 2
-    a = I.SpeciesInput(1.0, 1.0, s.cell[:half], s.off[:, :half], s.v[:, :half], s.w[:half])
-    b = I.SpeciesInput(2.0, 4.0, s.cell[half:], s.off[:, half:], s.v[:, half:],
-                       (s.w[half:] * 0.5).astype(np.float32))
+    cut = lambda a, sl: np.ascontiguousarray(a[..., sl])  # noqa: E731
+    a = I.SpeciesInput(1.0, 1.0, cut(s.cell, slice(0, half)), cut(s.off, slice(0, half)),
+                       cut(s.v, slice(0, half)), cut(s.w, slice(0, half)))
+    b = I.SpeciesInput(2.0, 4.0, cut(s.cell, slice(half, None)), cut(s.off, slice(half, None)),
+                       cut(s.v, slice(half, None)),
+                       (cut(s.w, slice(half, None)) * 0.5).astype(np.float32))
     wl.species = [a, b]
     wl.params["sort_every"] = 1
     ctx = hvmod.load_workload(wl)
