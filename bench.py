@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default="harris2d",
                     choices=["harris2d", "harris2d_small", "alfven2d", "beam3d_small"])
     ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
+    ap.add_argument("--sort-every", type=int, default=None,
+                    help="override the workload's sort interval")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -165,14 +167,13 @@ class Clocks:
 
 def push_bytes_per_launch(wl) -> float:
     """Algorithmic bytes of one push launch: every ion read once (cell, 2 or
-    3 offsets, v, w) and written once (all but w), plus the gather array
-    (32 B per padded cell) read once and the deposit accumulator (16 B per
-    padded cell) read and written once."""
+    3 offsets, v, w) and written once (all but w), plus, per interior cell,
+    E and B read once (24 B) and n, J written once (16 B)."""
     p = wl.params
     dim2 = p["ny"] == 1
     per_ion = (4 + 4 * (2 if dim2 else 3) + 12 + 4) + (4 + 4 * (2 if dim2 else 3) + 12)
-    npad = (p["nx"] + 2) * (1 if dim2 else p["ny"] + 2) * (p["nz"] + 2)
-    return float(wl.n_particles * per_ion + npad * (32 + 32))
+    ncell = p["nx"] * p["ny"] * p["nz"]
+    return float(wl.n_particles * per_ion + ncell * (24 + 16))
 
 
 def measured_peak():
@@ -279,6 +280,8 @@ def run_ours(args, world, rank, local):
     hv.lib()
     hv.hv_set_allocator(True)
     wl = make_workload(args.workload, args.shape, seed_offset=rank)
+    if args.sort_every is not None:
+        wl.params["sort_every"] = args.sort_every
     n_ions = wl.n_particles
     stream = torch.cuda.current_stream(dev)
     ctx = hv.load_workload(wl, stream=stream)

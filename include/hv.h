@@ -100,6 +100,17 @@ typedef struct {
   int64_t launches;  /* all library kernel launches since profiling began */
 } hv_prof_t;
 
+/* Layout facts of a context. */
+typedef struct {
+  int64_t ncell;      /* nx * ny * nz */
+  int32_t tile[3];    /* supercell tile extents (x, y, z) of the ion order */
+  int32_t ntiles;
+  int32_t nspecies;
+  int32_t pad;
+  int64_t n[8];       /* ions per species */
+  int64_t step;       /* completed steps */
+} hv_info_t;
+
 /* Device allocation hook used for every library-owned buffer.  alloc returns
  * NULL on failure.  `stream` is the context stream (cudaStream_t).  When no
  * hook is installed the library uses cudaMallocAsync / cudaFreeAsync. */
@@ -151,11 +162,16 @@ hv_status hv_moments(hv_ctx *ctx, float *n_out, float *J_out, float *E_out, floa
 hv_status hv_diag(hv_ctx *ctx, hv_diag_t *out);
 
 /* Copy species `species` out in the library's current particle order (the
- * order changes when ions are sorted): cell [n], off3 [3][n], v3 [3][n]
+ * order changes when ions are sorted; see hv_query): cell [n], off3 [3][n], v3 [3][n]
  * (v^{n-1/2}), w [n].  Any pointer may be NULL.  n_out (may be NULL)
  * receives the particle count.  Synchronises. */
 hv_status hv_get_ions(hv_ctx *ctx, int32_t species, int64_t *n_out, int32_t *cell,
                       float *off3, float *v3, float *w, int on_device);
+
+/* Fill *out with the context's layout: the library keeps ions sorted
+ * tile-major (supercell tile index, then the linear cell inside the tile,
+ * both x fastest) whenever it sorts them, with tile extents as reported. */
+hv_status hv_query(const hv_ctx *ctx, hv_info_t *out);
 
 /* Turn per-phase CUDA-event timing on (1) or off (0); turning it on resets
  * the counters.  hv_profile_read synchronises and returns the totals. */
@@ -165,8 +181,9 @@ hv_status hv_profile_read(hv_ctx *ctx, hv_prof_t *out);
 /* Release every device buffer of the context (NULL is allowed). */
 void hv_destroy(hv_ctx *ctx);
 
-/* Stable counting sort by key, the sort the step applies to ions
- * (spec device: it only changes FP32 summation order in the method).
+/* Stable sort by key, the sort the step applies to ions (keyed by the
+ * supercell order of their cells); it is a device of the GPU layout and
+ * changes results only through FP32 summation order.
  * keys [n] int32 in [0, nkeys) on the device; perm [n] receives the gather
  * permutation (keys[perm[i]] non-decreasing, equal keys in input order);
  * counts [nkeys] (may be NULL) receives the number of each key.  All three

@@ -313,19 +313,22 @@ class Sim:
         lib().hvo_init(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
                        _p(self.n_prev), _p(self.J_prev))
 
-    def sort(self):
-        """Apply the stable counting sort by cell to every species."""
+    def sort(self, key_fn=None):
+        """Apply the stable counting sort to every species, by cell or by
+        key_fn(cell) (integer keys >= 0)."""
         for s in self.species:
-            perm, _, _ = sort_stable(s.cell, ncell(self.g))
+            keys = s.cell if key_fn is None else np.asarray(key_fn(s.cell), dtype=np.int64)
+            nk = int(keys.max()) + 1 if keys.size else 1
+            perm, _, _ = sort_stable(keys, max(nk, ncell(self.g)))
             s.cell = np.ascontiguousarray(s.cell[perm])
             s.off = np.ascontiguousarray(s.off[:, perm])
             s.v = np.ascontiguousarray(s.v[:, perm])
             s.w = np.ascontiguousarray(s.w[perm])
 
-    def step(self, nsteps: int = 1, sort_every: int = 0):
+    def step(self, nsteps: int = 1, sort_every: int = 0, key_fn=None):
         for _ in range(nsteps):
             if sort_every > 0 and self.step_count % sort_every == 0:
-                self.sort()
+                self.sort(key_fn)
             arr = _species_array(self.species)
             d = Diag()
             lib().hvo_step(ctypes.byref(self.g), arr, len(self.species), _p(self.B), _p(self.E),

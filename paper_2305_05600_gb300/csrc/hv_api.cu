@@ -2,6 +2,7 @@
 // one step of the hybrid PIC ion loop (Sec. 2.2 of the paper):
 //   [sort] -> push/gather/deposit -> moment post (fold, smoothing, Eq. 11)
 //   -> nsub x 2 Ohm/Faraday stages (Eq. 5, explicit midpoint) -> final Ohm.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +81,13 @@ hv_status check_params(const hv_params *p) {
       (int64_t)(p->nx + 2) * (p->ny + 2) * (p->nz + 2) >= ((int64_t)1 << 30))
     return fail(HV_EINVAL, "grid too large (cell indices are int32)");
   if (p->nsub < 1) return fail(HV_EINVAL, "nsub must be >= 1");
+  {
+    const int64_t tx = p->ny == 1 ? kTile2X : kTile3, ty = p->ny == 1 ? 1 : kTile3;
+    const int64_t tz = p->ny == 1 ? kTile2Z : kTile3;
+    const int64_t nt = ((p->nx + tx - 1) / tx) * ((p->ny + ty - 1) / ty) * ((p->nz + tz - 1) / tz);
+    if (nt * tx * ty * tz >= ((int64_t)1 << 31))
+      return fail(HV_EINVAL, "grid too large for int32 supercell keys");
+  }
   if (!finite_pos(p->dx) || !finite_pos(p->dy) || !finite_pos(p->dz) || !finite_pos(p->dt))
     return fail(HV_EINVAL, "dx, dy, dz, dt must be finite and > 0");
   if (!std::isfinite(p->Te) || p->Te < 0) return fail(HV_EINVAL, "Te must be finite and >= 0");
@@ -111,17 +119,63 @@ Geom make_geom(const hv_params *p) {
   g.ny = p->ny;
   g.nz = p->nz;
   g.dim2 = p->ny == 1;
-  g.px = p->nx + 2;
-  g.py = g.dim2 ? 1 : p->ny + 2;
-  g.pz = p->nz + 2;
-  g.sx = 1;
+  g.px = p->nx + 2 * kGhost;
+  g.py = g.dim2 ? 1 : p->ny + 2 * kGhost;
+  g.pz = p->nz + 2 * kGhost;
   g.sy = g.px;
   g.sz = g.px * g.py;
   g.ncell = p->nx * p->ny * p->nz;
   g.npad = g.px * g.py * g.pz;
+  g.vlo = 2 * (1 + (g.dim2 ? 0 : g.sy) + g.sz);
+  g.vhi = g.npad - g.vlo;
   g.div_nx = make_fastdiv((uint32_t)p->nx);
   g.div_ny = make_fastdiv((uint32_t)p->ny);
+  g.div_px = make_fastdiv((uint32_t)g.px);
+  g.div_py = make_fastdiv((uint32_t)g.py);
+  g.tx = g.dim2 ? kTile2X : kTile3;
+  g.ty = g.dim2 ? 1 : kTile3;
+  g.tz = g.dim2 ? kTile2Z : kTile3;
+  g.ntx = (p->nx + g.tx - 1) / g.tx;
+  g.nty = (p->ny + g.ty - 1) / g.ty;
+  g.ntz = (p->nz + g.tz - 1) / g.tz;
+  g.ntiles = g.ntx * g.nty * g.ntz;
+  g.tlog = 0;
+  while ((1 << g.tlog) < g.tx * g.ty * g.tz) ++g.tlog;
   return g;
+}
+
+int linear_to_voxel(const Geom &g, int c) {
+  const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+  return voxel_of(g, i, j, k);
+}
+
+__host__ __device__ int voxel_to_linear(const Geom &g, int v) {
+  const int k = v / g.sz - kGhost;
+  const int r = v % g.sz;
+  const int j = g.dim2 ? 0 : r / g.sy - kGhost;
+  const int i = (g.dim2 ? r : r % g.sy) - kGhost;
+  return i + g.nx * (j + g.ny * k);
+}
+
+__global__ void vox_to_linear_kernel(Geom g, const int *in, int *out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = voxel_to_linear(g, in[t]);
+}
+
+// wrap table: voxel of the interior image of every padded voxel
+std::vector<int> wrap_table(const Geom &g) {
+  std::vector<int> w((size_t)g.npad);
+  const int ny_pad = g.dim2 ? 1 : g.py;
+  for (int Pz = 0; Pz < g.pz; ++Pz)
+    for (int Py = 0; Py < ny_pad; ++Py)
+      for (int Px = 0; Px < g.px; ++Px) {
+        const int i = ((Px - kGhost) % g.nx + g.nx) % g.nx;
+        const int j = g.dim2 ? 0 : ((Py - kGhost) % g.ny + g.ny) % g.ny;
+        const int k = ((Pz - kGhost) % g.nz + g.nz) % g.nz;
+        w[(size_t)Px + (size_t)Py * g.sy + (size_t)Pz * g.sz] = voxel_of(g, i, j, k);
+      }
+  return w;
 }
 
 // component-major [3][ncell] <-> interleaved float4 grids, and the padded
@@ -139,8 +193,7 @@ __global__ void unpack_E_kernel(Geom g, const float4 *EB, float *out) {
     const int i = c % g.nx;
     const int j = (c / g.nx) % g.ny;
     const int k = c / (g.nx * g.ny);
-    const int p = (i + 1) + (g.dim2 ? 0 : (j + 1) * g.sy) + (k + 1) * g.sz;
-    const float4 e = EB[2 * p];
+    const float4 e = EB[2 * voxel_of(g, i, j, k)];
     out[c] = e.x;
     out[(size_t)g.ncell + c] = e.y;
     out[(size_t)2 * g.ncell + c] = e.z;
@@ -161,6 +214,7 @@ hv_status latched(hv_ctx *c, int *word) {
   if (e & kErrNonFinite) return fail(HV_ENAN, "a particle became non-finite");
   if (e & kErrCfl) return fail(HV_ECFL, "a particle moved more than one cell in one step");
   if (e & kErrIndex) return fail(HV_ECUDA, "a corrupt particle cell index was found");
+  if (e & kErrTimeout) return fail(HV_ETIMEOUT, "a bounded device wait gave up");
   return HV_OK;
 }
 
@@ -259,7 +313,7 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&c->device);
   c->vc = p->dx * p->dy * p->dz;
-  c->push_blocks = push_grid_blocks(c->device);
+  c->push_blocks = c->g.ntiles;  // the push runs one block per supercell tile
   c->grid_blocks = grid_reduce_blocks(c->device);
   const Geom &g = c->g;
   const size_t npad = (size_t)g.npad, nc = (size_t)g.ncell;
@@ -275,8 +329,13 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->gridpart = (double *)ctx_alloc(c, sizeof(double) * c->grid_blocks * 4);
   c->diag_dev = (double *)ctx_alloc(c, sizeof(double) * 8);
   c->err = (int *)ctx_alloc(c, sizeof(int));
+  c->wrapvox = (int *)ctx_alloc(c, sizeof(int) * npad);
+  const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
+  for (int b = 0; b < 2; ++b)
+    c->accm[b] = rec ? (float *)ctx_alloc(c, sizeof(float) * kMono * npad) : nullptr;
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
-      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err) {
+      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err || !c->wrapvox ||
+      (rec && (!c->accm[0] || !c->accm[1]))) {
     hv_destroy(c);
     return fail(HV_ENOMEM, "grid allocation failed");
   }
@@ -287,6 +346,10 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   cudaMemsetAsync(c->pushpart, 0, sizeof(double) * kMaxSpecies * c->push_blocks * 4, c->stream);
   cudaMemsetAsync(c->diag_dev, 0, sizeof(double) * 8, c->stream);
   cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  for (int b = 0; b < 2; ++b)
+    if (c->accm[b]) cudaMemsetAsync(c->accm[b], 0, sizeof(float) * kMono * npad, c->stream);
+  const std::vector<int> wt = wrap_table(c->g);
+  cudaMemcpyAsync(c->wrapvox, wt.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, c->stream);
   std::vector<float4> hb(nc);
   for (size_t i = 0; i < nc; ++i) {
     if (B0_host) {
@@ -336,6 +399,7 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
   const int dims[3] = {g.nx, g.ny, g.nz};
   for (int64_t i = 0; i < n; ++i) {
     if (hc[i] < 0 || hc[i] >= g.ncell) return fail(HV_EINVAL, "cell index out of range");
+    hc[i] = linear_to_voxel(g, hc[i]);
     for (int a = 0; a < 3; ++a) {
       float &o = ho[a * n + i];
       if (dims[a] == 1 || (a == 1 && g.dim2)) {
@@ -373,8 +437,14 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
     s.vz = (float *)(p + arr * slot++);
     s.w = (float *)(p + arr * slot++);
   }
+  sp.tile_off = (int *)dev_alloc(sizeof(int) * (g.ntiles + 1), c->stream);
+  if (!sp.tile_off) return fail(HV_ENOMEM, "tile range allocation failed");
   c->nspecies++;
   sp.cur = 0;
+  {
+    cudaError_t e = tile_ranges_even(c, species);
+    if (e != cudaSuccess) return cuda_fail(e, "tile ranges");
+  }
   if (n > 0) {
     Soa &s = sp.buf[0];
     cudaError_t e = cudaMemcpyAsync(s.cell, hc.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
@@ -536,7 +606,17 @@ hv_status hv_get_ions(hv_ctx *c, int32_t species, int64_t *n_out, int32_t *cell,
   auto cp = [&](void *dst, const void *src) {
     if (dst && e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dst, src, 4 * n, k, c->stream);
   };
-  cp(cell, s.cell);
+  if (cell && n > 0 && e == cudaSuccess) {
+    if (on_device) {
+      const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+      vox_to_linear_kernel<<<blocks, 256, 0, c->stream>>>(c->g, s.cell, cell, n);
+      e = cudaGetLastError();
+    } else {
+      e = cudaMemcpyAsync(cell, s.cell, 4 * n, k, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      for (int64_t t = 0; t < n && e == cudaSuccess; ++t) cell[t] = voxel_to_linear(c->g, cell[t]);
+    }
+  }
   if (off3) {
     cp(off3, s.ox);
     if (s.oy) {
@@ -555,6 +635,20 @@ hv_status hv_get_ions(hv_ctx *c, int32_t species, int64_t *n_out, int32_t *cell,
   cp(w, s.w);
   if (e != cudaSuccess) return cuda_fail(e, "hv_get_ions");
   return latched(c, nullptr);
+}
+
+hv_status hv_query(const hv_ctx *c, hv_info_t *out) {
+  if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
+  memset(out, 0, sizeof(*out));
+  out->ncell = c->g.ncell;
+  out->tile[0] = c->g.tx;
+  out->tile[1] = c->g.ty;
+  out->tile[2] = c->g.tz;
+  out->ntiles = c->g.ntiles;
+  out->nspecies = c->nspecies;
+  for (int s = 0; s < c->nspecies; ++s) out->n[s] = c->sp[s].n;
+  out->step = c->step;
+  return HV_OK;
 }
 
 hv_status hv_profile(hv_ctx *c, int enable) {
@@ -599,8 +693,10 @@ void hv_destroy(hv_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   prof_destroy(c);
-  for (int s = 0; s < c->nspecies; ++s)
+  for (int s = 0; s < c->nspecies; ++s) {
     for (int b = 0; b < 2; ++b) dev_free(c->sp[s].base[b], c->sp[s].bytes[b], c->stream);
+    dev_free(c->sp[s].tile_off, sizeof(int) * (c->g.ntiles + 1), c->stream);
+  }
   sort_release(c);
   for (int i = 0; i < c->nallocs; ++i) dev_free(c->allocs[i], c->alloc_bytes[i], c->stream);
   cudaStreamSynchronize(c->stream);

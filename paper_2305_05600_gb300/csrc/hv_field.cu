@@ -35,20 +35,11 @@ __device__ __forceinline__ void decode(const Geom &g, int c, int &i, int &j, int
   j = q - k * g.ny;
 }
 
-// Padded coordinates that represent interior coordinate i on an axis of n
-// cells: itself, plus the low ghost if i is the last cell and the high ghost
-// if i is the first.  Returns the count (1..3).
-__device__ __forceinline__ int images(int i, int n, int *out) {
-  int c = 0;
-  out[c++] = i + 1;
-  if (i == n - 1) out[c++] = 0;
-  if (i == 0) out[c++] = n + 1;
-  return c;
-}
-
 struct MomArgs {
   Geom g;
-  float4 *acc;
+  float4 *acc;            // per-target accumulator (read and zeroed)
+  const float *rec;       // moment records of this step (read)
+  float *rec_clear;       // moment records of the next step (zeroed)
   const float4 *prev_in;  // n^{n-1/2}, J^{n-1/2}
   float4 *raw_out;        // folded deposit (when smoothing follows)
   float4 *prev_out;       // n^{n+1/2}, J^{n+1/2}
@@ -57,23 +48,40 @@ struct MomArgs {
   int init;               // 1: start-up (prev := ext := deposit)
 };
 
-// Fold the padded accumulator onto the interior, zero it for the next step,
-// and (fused) extrapolate: ext = 3/2 half - 1/2 prev (Eq. 11).
+__device__ __forceinline__ void finish_moment(const MomArgs &a, int c, float4 m) {
+  if (!a.fuse) {
+    a.raw_out[c] = m;
+    return;
+  }
+  if (a.init) {
+    a.prev_out[c] = m;
+    a.ext_out[c] = m;
+    return;
+  }
+  const float4 pv = a.prev_in[c];
+  a.ext_out[c] = make_float4(1.5f * m.x - 0.5f * pv.x, 1.5f * m.y - 0.5f * pv.y,
+                             1.5f * m.z - 0.5f * pv.z, 1.5f * m.w - 0.5f * pv.w);
+  a.prev_out[c] = m;
+}
+
+// Fold the per-target accumulator onto the periodic interior: every padded
+// voxel that stands for the cell (the cell and its ghost images) is summed
+// and zeroed for the next step; then (fused) extrapolate with Eq. 11.
 __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
   const Geom &g = a.g;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, k;
     decode(g, c, i, j, k);
-    int xs[3], ys[3], zs[3];
-    const int nxs = images(i, g.nx, xs);
-    const int nys = g.dim2 ? 1 : images(j, g.ny, ys);
+    int xs[5], ys[5], zs[5];
+    const int nxs = axis_images(i, g.nx, xs);
+    const int nys = g.dim2 ? 1 : axis_images(j, g.ny, ys);
     if (g.dim2) ys[0] = 0;
-    const int nzs = images(k, g.nz, zs);
+    const int nzs = axis_images(k, g.nz, zs);
     float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int a3 = 0; a3 < nzs; ++a3)
       for (int a2 = 0; a2 < nys; ++a2)
         for (int a1 = 0; a1 < nxs; ++a1) {
-          const int p = xs[a1] + (g.dim2 ? 0 : ys[a2] * g.sy) + zs[a3] * g.sz;
+          const int p = xs[a1] + ys[a2] * g.sy + zs[a3] * g.sz;
           const float4 v = a.acc[p];
           m.x += v.x;
           m.y += v.y;
@@ -81,19 +89,60 @@ __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
           m.w += v.w;
           a.acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-    if (!a.fuse) {
-      a.raw_out[c] = m;
-      continue;
-    }
-    if (a.init) {
-      a.prev_out[c] = m;
-      a.ext_out[c] = m;
-      continue;
-    }
-    const float4 pv = a.prev_in[c];
-    a.ext_out[c] = make_float4(1.5f * m.x - 0.5f * pv.x, 1.5f * m.y - 0.5f * pv.y,
-                               1.5f * m.z - 0.5f * pv.z, 1.5f * m.w - 0.5f * pv.w);
-    a.prev_out[c] = m;
+    finish_moment(a, c, m);
+  }
+}
+
+// Fold of the QS moment records (x-z layout): a record holds, per channel,
+// the sums S0, Sx, Sxx, Sz, Szz of s, s dx, s dx^2, s dz, s dz^2 over the ions
+// whose half-step cell is that voxel.  Eq. 17 gives the voxel itself
+// (4 S0 - Sxx - Szz)/6 (the two y neighbours of the single y cell folded in),
+// its x+-1 neighbours (S0 +- 2 Sx + Sxx)/12 and its z+-1 neighbours
+// (S0 +- 2 Sz + Szz)/12.  A cell collects from every source voxel whose
+// stencil reaches one of its images.  The other record buffer (read by the
+// previous fold) is zeroed for the next deposit.
+__global__ void __launch_bounds__(256) fold_records_kernel(MomArgs a) {
+  const Geom &g = a.g;
+  const float c6 = 1.f / 6.f, c12 = 1.f / 12.f;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, c, i, j, k);
+    int xs[5], zs[5];
+    const int nxs = axis_images(i, g.nx, xs);
+    const int nzs = axis_images(k, g.nz, zs);
+    float m[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int a3 = 0; a3 < nzs; ++a3)
+      for (int a1 = 0; a1 < nxs; ++a1) {
+        const int Px = xs[a1], Pz = zs[a3];
+        const int T = Px + Pz * g.sz;
+        // (dx, dz) of the target relative to the source: 0, +x, -x, +z, -z
+        for (int t = 0; t < 5; ++t) {
+          const int sx = t == 1 ? -1 : (t == 2 ? 1 : 0);
+          const int sz = t == 3 ? -1 : (t == 4 ? 1 : 0);
+          const int Qx = Px + sx, Qz = Pz + sz;
+          if (Qx < 0 || Qx >= g.px || Qz < 0 || Qz >= g.pz) continue;
+          const float4 *r4 = reinterpret_cast<const float4 *>(a.rec + (size_t)(Qx + Qz * g.sz) * kMono);
+          const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4];
+          const float r[kMono] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y,
+                                  q2.z, q2.w, q3.x, q3.y, q3.z, q3.w, q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            const float S0 = r[5 * ch], Sx = r[5 * ch + 1], Sxx = r[5 * ch + 2],
+                        Sz = r[5 * ch + 3], Szz = r[5 * ch + 4];
+            float w;
+            if (t == 0) w = (4.f * S0 - Sxx - Szz) * c6;
+            else if (t == 1) w = (S0 + 2.f * Sx + Sxx) * c12;
+            else if (t == 2) w = (S0 - 2.f * Sx + Sxx) * c12;
+            else if (t == 3) w = (S0 + 2.f * Sz + Szz) * c12;
+            else w = (S0 - 2.f * Sz + Szz) * c12;
+            m[ch] += w;
+          }
+        }
+        float4 *z4 = reinterpret_cast<float4 *>(a.rec_clear + (size_t)T * kMono);
+#pragma unroll
+        for (int q = 0; q < kMono / 4; ++q) z4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    finish_moment(a, c, make_float4(m[0], m[1], m[2], m[3]));
   }
 }
 
@@ -290,11 +339,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       // at the cell and at each of its ghost images
       const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
       if (gx < g.nx && (DIM == 2 || gy < g.ny) && gz < g.nz) {
-        int xs[3], ys[3], zs[3];
-        const int nxs = images(gx, g.nx, xs);
-        const int nys = DIM == 2 ? 1 : images(gy, g.ny, ys);
+        int xs[5], ys[5], zs[5];
+        const int nxs = axis_images(gx, g.nx, xs);
+        const int nys = DIM == 2 ? 1 : axis_images(gy, g.ny, ys);
         if (DIM == 2) ys[0] = 0;
-        const int nzs = images(gz, g.nz, zs);
+        const int nzs = axis_images(gz, g.nz, zs);
         const float4 e0 = make_float4(ex, ey, ez, bx);
         const float4 e1 = make_float4(by, bz, 0.f, 0.f);
         for (int a3 = 0; a3 < nzs; ++a3)
@@ -460,6 +509,8 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
   MomArgs a;
   a.g = c->g;
   a.acc = c->acc;
+  a.rec = c->accm[c->accpar];
+  a.rec_clear = c->accm[c->accpar ^ 1];
   a.prev_in = c->mprev;
   a.prev_out = c->mprev;
   a.ext_out = c->mext;
@@ -469,7 +520,12 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
   a.fuse = passes == 0;
   const int nb = elem_blocks(c->g.ncell);
   c->launches++;
-  fold_kernel<<<nb, 256, 0, c->stream>>>(a);
+  if (uses_records(c)) {
+    fold_records_kernel<<<nb, 256, 0, c->stream>>>(a);
+    c->accpar ^= 1;
+  } else {
+    fold_kernel<<<nb, 256, 0, c->stream>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || passes == 0) return e;
   float4 *src = c->mtmp, *dst = c->mhalf;

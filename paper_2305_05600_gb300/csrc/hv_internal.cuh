@@ -12,10 +12,17 @@ namespace hv {
 
 constexpr int kMaxSpecies = 8;
 
+// QS deposit in the x-z layout accumulates, per cell and channel
+// (n, Jx, Jy, Jz), the sums of s, s dx, s dx^2, s dz, s dz^2 (s = q w / V_c,
+// times v for J); the stencil of Eq. 17 is applied to these records when
+// the moments are folded onto the grid.
+constexpr int kMono = 20;
+
 // Device error bits latched by kernels (atomicOr into the error word).
 constexpr int kErrCfl = 1;     // a particle moved more than one cell in a step
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIndex = 4;    // a corrupt cell index was skipped
+constexpr int kErrTimeout = 8;  // a bounded device wait gave up
 
 // Exact unsigned division of 32-bit values by an invariant divisor:
 // q = floor(M * n / 2^64) with M = ceil(2^64 / d) (Lemire, Kaser and Kurz,
@@ -36,18 +43,60 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
   return f.d <= 1 ? n : (uint32_t)__umul64hi(f.M, (unsigned long long)n);
 }
 
-// Geometry of the ghost-padded gather/deposit grids: one ghost layer on each
-// side of every axis; padded index p = (i+1) + PX*((j+1) + PY*(k+1)).
-// In the 2D (x-z) layout the y axis is not padded: p = (i+1) + PX*(k+1).
+// Geometry of the ghost-padded gather/deposit grids.  Every axis carries
+// kGhost = 2 ghost layers on each side, so a particle's voxel index
+// (the padded linear index of its cell, as VPIC stores it) can move by one
+// cell at the half step and still address its whole deposit stencil without
+// any wrap: p = (i+2) + SY*(j+2) + SZ*(k+2).  In the 2D (x-z) layout the y
+// axis is not padded: p = (i+2) + SZ*(k+2).  A ghost voxel stands for the
+// interior cell ((P-2) mod n) on each axis.
+constexpr int kGhost = 2;
+
 struct Geom {
   int nx, ny, nz;
   int px, py, pz;       // padded extents (2D: py = 1)
-  int sx, sy, sz;       // padded strides (x: 1)
+  int sy, sz;           // padded strides (x stride is 1)
   int ncell;            // interior cells
   int npad;             // padded cells
   int dim2;             // 1: x-z plane layout (ny == 1)
+  int vlo, vhi;         // voxel indices in [vlo, vhi) address their whole
+                        // gather/deposit neighbourhood inside the grid
   FastDiv div_nx, div_ny;
+  FastDiv div_px, div_py;  // voxel -> padded coordinates
+  // supercell tiles: ions are kept sorted tile-major (tile index, then the
+  // cell inside the tile), and one block of the push works on one tile
+  int tx, ty, tz;       // tile extents in cells (2D: ty = 1)
+  int ntx, nty, ntz;    // tiles per axis
+  int ntiles;
+  int tlog;             // log2(cells per tile)
 };
+
+// Tile extents of the supercell order: 16x16 cells in the x-z layout,
+// 8x8x8 cells in 3D (cells per tile a power of two).
+constexpr int kTile2X = 16, kTile2Z = 16, kTile3 = 8;
+
+// Supercell sort key of interior cell (i, j, k): tile index, then the cell
+// inside the tile, both x fastest.
+__host__ __device__ __forceinline__ int supercell_key(const Geom &g, int i, int j, int k) {
+  const int ti = i / g.tx, tj = j / g.ty, tk = k / g.tz;
+  const int li = i - ti * g.tx, lj = j - tj * g.ty, lk = k - tk * g.tz;
+  const int tile = ti + g.ntx * (tj + g.nty * tk);
+  return (tile << g.tlog) + li + g.tx * (lj + g.ty * lk);
+}
+
+__host__ __device__ __forceinline__ int voxel_of(const Geom &g, int i, int j, int k) {
+  return (i + kGhost) + (g.dim2 ? 0 : (j + kGhost) * g.sy) + (k + kGhost) * g.sz;
+}
+
+// Padded coordinates standing for interior coordinate i on an axis of n
+// cells: P in [0, n + 2*kGhost) with (P - kGhost) mod n == i.  At most 5.
+__host__ __device__ __forceinline__ int axis_images(int i, int n, int *out) {
+  int c = 0;
+  const int hi = n + 2 * kGhost;
+  for (int P = (i + kGhost) % n; P < hi; P += n)
+    if (P >= 0) out[c++] = P;
+  return c;
+}
 
 // Particle SoA for one species, one buffer set.  Arrays are 256-byte aligned
 // and have capacity rounded up to a multiple of 4 elements.
@@ -61,6 +110,8 @@ struct Soa {
 struct Species {
   double q, m;
   int64_t n, cap;
+  int *tile_off;        // [ntiles + 1] first ion of each tile in the live
+                        // buffer (valid ranges even before the first sort)
   Soa buf[2];
   int cur;              // index of the live buffer set
   void *base[2];        // allocation bases
@@ -86,7 +137,11 @@ struct hv_ctx {
   double vc;
   // grids (device)
   float4 *EB;           // padded [npad][2]: {Ex,Ey,Ez,Bx},{By,Bz,0,0}
-  float4 *acc;          // padded [npad] deposit accumulator {n,Jx,Jy,Jz}
+  float4 *acc;          // padded [npad] per-cell deposit {n,Jx,Jy,Jz}
+  float *accm[2];       // padded [npad][kMono] per-cell moment records
+                        // (QS in the x-z layout), used alternately
+  int accpar;           // record buffer the next deposit writes
+  int *wrapvox;         // padded [npad]: voxel of the interior image
   float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}
   float4 *mhalf, *mext, *mprev, *mtmp;  // interior moments {n,Jx,Jy,Jz}
   double *pushpart;     // [kMaxSpecies][push_blocks][4]
@@ -123,15 +178,17 @@ void dev_free(void *p, size_t bytes, cudaStream_t s);
 // kernels launchers (return cudaGetLastError of the launch)
 cudaError_t launch_push(hv_ctx *c, int species, int mode);
 cudaError_t launch_moments(hv_ctx *c, int init);
+bool uses_records(const hv_ctx *c);
 cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                float coef);
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
 cudaError_t launch_diag(hv_ctx *c);
-int push_grid_blocks(int device);
 int grid_reduce_blocks(int device);
 
 // sort: sorts species `s` of the context by cell (stable), swapping buffers
 hv_status sort_species(hv_ctx *c, int s);
+// equal split of species s into tile ranges (used before the first sort)
+cudaError_t tile_ranges_even(hv_ctx *c, int s);
 void sort_release(hv_ctx *c);
 // standalone key sort into perm with scratch from the allocation hook
 hv_status sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,

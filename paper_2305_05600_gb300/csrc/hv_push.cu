@@ -1,58 +1,85 @@
 // Particle kernel of the hybrid PIC step: field gather at x^n, Boris push
 // (Sec. 2.2, Eq. 9), deposit of n and J_i at the half-step position
-// (App. B, Eqs. 13 and 17), move to x^{n+1} (Eq. 10) and the FP32-Kahan /
+// (App. B, Eqs. 13 and 17), move to x^{n+1} (Eq. 10), and FP32-Kahan /
 // FP64 block partials of the kinetic energy and momentum.
 //
-// Layout: SoA float32 particles, one thread owns 4 consecutive particles
-// and moves them with 128-bit streaming loads/stores.  Fields are gathered
-// from a ghost-padded array holding {Ex,Ey,Ez,Bx},{By,Bz,-,-} per cell (32 B,
-// one sector).  Deposits are aggregated before they reach global memory:
-// first in registers over a thread's 4 particles, then across the warp by a
-// shuffle reduce-scatter over the lanes that share a deposit key (ions are
-// sorted by cell, so a warp's 128 particles usually span one or two cells),
-// and only then added to the padded accumulator with global reductions.
+// Layout: SoA float32 ions whose cell is stored as a voxel index of the
+// ghost-padded grid (two ghost layers), so no index decode or wrap is needed
+// on the hot path: the half-step cell is the voxel plus the cell shift, the
+// deposit stencil may reach into the ghost layers (folded back afterwards),
+// and the new cell after the move is looked up in a wrap table.  One thread
+// owns 4 consecutive ions and moves them with 128-bit streaming loads and
+// stores.  Fields are gathered from {Ex,Ey,Ez,Bx},{By,Bz,-,-} per voxel.
+//
+// Deposits are aggregated in registers before they reach global memory: a
+// lane owns 16 consecutive ions (sorted by cell) and sums their deposits
+// per run of equal deposit key, flushing a run with vector reductions.  For
+// QS in the x-z layout the accumulated quantities are
+// the per-cell moment sums s*(1, dx, dx^2, dz, dz^2) of Eq. 17's weights, so
+// every ion of a cell contributes to one 80-byte record; the fold kernel
+// applies the stencil.  For CIC, NGP and 3D QS the per-target contributions
+// are accumulated.
+#include <climits>
+
 #include "hv_internal.cuh"
+
+// Threads per block, resident blocks per SM the push kernel is compiled for
+// (register budget 65536 / (threads * blocks)), and ions per lane per tile.
+#ifndef HV_PUSH_THREADS
+#define HV_PUSH_THREADS 256
+#endif
+#ifndef HV_PUSH_MIN_BLOCKS
+#define HV_PUSH_MIN_BLOCKS 2
+#endif
+#ifndef HV_PUSH_CHUNK
+#define HV_PUSH_CHUNK 8
+#endif
 
 namespace hv {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = HV_PUSH_THREADS;
+constexpr int kChunk = HV_PUSH_CHUNK;  // consecutive ions per lane per tile
+constexpr int kTile = 32 * kChunk;     // ions per warp tile
 
 struct PushArgs {
   Soa s;
   int64_t n;
+  const int *tile_off;  // [ntiles + 1]
   const float4 *EB;
-  float4 *acc;
+  float4 *acc;       // per-target accumulator
+  float *accm;       // per-cell moment records (QS in the x-z layout)
+  const int *wrapvox;
   Geom g;
   PushConsts k;
-  double *part;  // [gridDim.x][4]
+  double *part;      // [gridDim.x][4]
   int *err;
 };
 
 template <int DIM, int SHAPE>
 struct Shape {
   static constexpr int NT = SHAPE == 0 ? 1 : (SHAPE == 1 ? (DIM == 2 ? 5 : 7) : (DIM == 2 ? 4 : 8));
+  static constexpr bool REC = SHAPE == 1 && DIM == 2;  // moment records
+  static constexpr int NV = REC ? kMono : NT * 4;
 };
 
-// Padded-index offset of target t from the key cell.
+// Voxel offset of gather/deposit target t from the key voxel.
 template <int DIM, int SHAPE>
 __device__ __forceinline__ int target_off(int t, const Geom &g) {
   if (SHAPE == 0) return 0;
   if (SHAPE == 1) {
-    if (DIM == 2) {
-      return t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? g.sz : -g.sz;
-    }
+    if (DIM == 2) return t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? g.sz : -g.sz;
     return t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? g.sy : t == 4 ? -g.sy
            : t == 5 ? g.sz : -g.sz;
   }
-  // CIC: base + {0,1} x {0,sy} x {0,sz}
   if (DIM == 2) return (t & 1) + ((t >> 1) & 1) * g.sz;
   return (t & 1) + ((t >> 1) & 1) * g.sy + ((t >> 2) & 1) * g.sz;
 }
 
-// Shape weights at relative coordinates (dx,dy,dz); returns the padded-index
-// shift from the particle's cell to the key cell (non-zero only for CIC,
-// whose 2^D stencil starts at the lower neighbour when d < 0).
+// Shape weights at relative coordinates (dx,dy,dz); returns the voxel shift
+// from the particle's cell to the key voxel (non-zero only for CIC, whose
+// 2^D stencil starts at the lower neighbour when d < 0).
 template <int DIM, int SHAPE>
 __device__ __forceinline__ int shape_weights(float dx, float dy, float dz, const Geom &g,
                                              float *wt) {
@@ -61,8 +88,8 @@ __device__ __forceinline__ int shape_weights(float dx, float dy, float dz, const
     return 0;
   }
   if (SHAPE == 1) {
-    // QS (Eq. 17).  In the x-z layout the two y neighbours of a single-cell y
-    // axis fold onto the cell: (3 - d^2)/6 + 2/12 = (4 - dx^2 - dz^2)/6.
+    // QS (Eq. 17).  In the x-z layout the two y neighbours of the single y
+    // cell fold onto the cell: (3 - |d|^2)/6 + 2/12 = (4 - dx^2 - dz^2)/6.
     const float c6 = 1.f / 6.f, c12 = 1.f / 12.f;
     const float ax = 1.f + dx, bx = 1.f - dx, az = 1.f + dz, bz = 1.f - dz;
     if (DIM == 2) {
@@ -103,21 +130,15 @@ __device__ __forceinline__ int shape_weights(float dx, float dy, float dz, const
   return shift;
 }
 
-__device__ __forceinline__ void red_v4(float4 *addr, float a, float b, float c, float d) {
+__device__ __forceinline__ void red_v4(float *addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
                "f"(c), "f"(d)
                : "memory");
 }
 
-__device__ __forceinline__ void red_f32(float *addr, float a) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
-}
-
-// Wrap a cell index that moved by at most one cell.
-__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // Shift a relative coordinate back into [-1, 1) after a move of less than
-// one cell width on either side; the subtraction of 2 is exact (Sterbenz).
+// one cell on either side; the subtraction of 2 is exact (Sterbenz).
 __device__ __forceinline__ int rebase(float &d) {
   const int m = (d >= 1.f) - (d < -1.f);
   d -= 2.f * (float)m;
@@ -131,258 +152,486 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
-// Reduce-scatter of 32 values across the warp: afterwards lane l holds the
-// warp sum of v[l].
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+// Deposit values of one ion: QS x-z records (moment sums) or per-target
+// contributions, both NV floats.
+template <int DIM, int SHAPE>
+__device__ __forceinline__ int deposit_values(float hx, float hy, float hz, float s, float vx,
+                                              float vy, float vz, const Geom &g, float *cv) {
+  using S = Shape<DIM, SHAPE>;
+  if (S::REC) {
+    const float sx = s * hx, sz = s * hz;
+    const float v3[3] = {vx, vy, vz};
+    cv[0] = s;
+    cv[1] = sx;
+    cv[2] = sx * hx;
+    cv[3] = sz;
+    cv[4] = sz * hz;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int j = 0; j < o; ++j) {
-      const float send = up ? v[j] : v[j + o];
-      const float keep = up ? v[j + o] : v[j];
-      v[j] = keep + __shfl_xor_sync(kFull, send, o);
+    for (int a = 0; a < 3; ++a) {
+      const float ta = s * v3[a];
+      const float tx = ta * hx, tz = ta * hz;
+      cv[5 * a + 5] = ta;
+      cv[5 * a + 6] = tx;
+      cv[5 * a + 7] = tx * hx;
+      cv[5 * a + 8] = tz;
+      cv[5 * a + 9] = tz * hz;
     }
+    return 0;
   }
-  return v[0];
+  float wt[S::NT];
+  const int shift = shape_weights<DIM, SHAPE>(hx, hy, hz, g, wt);
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    const float st = wt[t] * s;
+    cv[4 * t + 0] = st;
+    cv[4 * t + 1] = st * vx;
+    cv[4 * t + 2] = st * vy;
+    cv[4 * t + 3] = st * vz;
+  }
+  return shift;
+}
+
+// Add a lane's NV deposit values at `key` with vector reductions.
+template <int DIM, int SHAPE>
+__device__ __forceinline__ void flush_direct(const PushArgs &a, int key, const float *v) {
+  using S = Shape<DIM, SHAPE>;
+  if (S::REC) {
+    float *rec = a.accm + (size_t)key * kMono;
+#pragma unroll
+    for (int q = 0; q < kMono / 4; ++q) red_v4(rec + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t)
+      red_v4(reinterpret_cast<float *>(a.acc + key + target_off<DIM, SHAPE>(t, a.g)), v[4 * t],
+             v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+)
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait on a transaction barrier: gives up after a fixed number of
+// polls (a copy that never lands would otherwise hang the GPU) and returns
+// false so the caller can latch an error and stop.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Shared-memory layout of one push block (one supercell tile).
+//   stage: one kTile-ion staging buffer per warp (bulk-copied in and out)
+//   eb:    E, B of the tile and a halo of RE cells, 2 float4 per cell
+template <int DIM, int SHAPE>
+struct Layout {
+  using S = Shape<DIM, SHAPE>;
+  static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
+  static constexpr int TX = DIM == 2 ? kTile2X : kTile3;
+  static constexpr int TY = DIM == 2 ? 1 : kTile3;
+  static constexpr int TZ = DIM == 2 ? kTile2Z : kTile3;
+  // ions that drifted up to H cells out of their tile since the last sort
+  // still gather from and deposit into shared memory
+  static constexpr int H = DIM == 2 ? 2 : 1;
+  static constexpr int RE = H + 1;
+  static constexpr int EX = TX + 2 * RE, EY = DIM == 2 ? 1 : TY + 2 * RE, EZ = TZ + 2 * RE;
+  static constexpr int NEB = EX * EY * EZ;
+  static constexpr size_t stage_bytes = (size_t)NA * kTile * 4;
+  static constexpr size_t off_eb = stage_bytes * (kThreads / 32);
+  static constexpr size_t off_bar = off_eb + (size_t)NEB * 32;
+  static constexpr size_t bytes = off_bar + 8 * (kThreads / 32);
+};
+
+// Array slot of each particle field in a staging buffer.
+template <int DIM>
+struct Slot {
+  static constexpr int CELL = 0, OX = 1, OY = DIM == 3 ? 2 : 1, OZ = DIM == 3 ? 3 : 2,
+                       VX = OZ + 1, VY = OZ + 2, VZ = OZ + 3, W = OZ + 4;
+};
+
+template <int DIM>
+__device__ __forceinline__ void soa_ptrs(const Soa &s, void **p) {
+  p[Slot<DIM>::CELL] = s.cell;
+  p[Slot<DIM>::OX] = s.ox;
+  if (DIM == 3) p[Slot<DIM>::OY] = s.oy;
+  p[Slot<DIM>::OZ] = s.oz;
+  p[Slot<DIM>::VX] = s.vx;
+  p[Slot<DIM>::VY] = s.vy;
+  p[Slot<DIM>::VZ] = s.vz;
+  p[Slot<DIM>::W] = s.w;
+}
+
+// Padded coordinates of a voxel.
+__device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, int &jp, int &kp) {
+  const uint32_t q = fdiv((uint32_t)vox, g.div_px);
+  ip = vox - (int)q * g.px;
+  if (g.dim2) {
+    jp = kGhost;
+    kp = (int)q;
+  } else {
+    kp = (int)fdiv(q, g.div_py);
+    jp = (int)q - kp * g.py;
+  }
 }
 
 // MODE 0: full step.  MODE 1: start-up deposit at the current position with
 // the stored velocity (no push, no move, no write-back).
+//
+// One block per supercell tile.  Ions are kept sorted tile-major, so the
+// block's ion range [tile_off[t], tile_off[t+1]) (rounded to whole quads)
+// lies in the tile, give or take the drift since the last sort.  The block
+// stages E and B of the tile and a halo in shared memory; ions that drifted
+// further gather from global memory.  Each warp streams tiles of kTile ions
+// through shared memory with bulk copies; each lane owns kChunk consecutive
+// ions and sums their deposits in registers per run of equal deposit key,
+// flushing a run with vector reductions into the global accumulator.
 template <int DIM, int SHAPE, int MODE>
-__global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
-  constexpr int NT = Shape<DIM, SHAPE>::NT;
-  constexpr int NV = NT * 4;
-  static_assert(NV <= 32, "deposit vector must fit one warp");
+__global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(PushArgs a) {
+  using S = Shape<DIM, SHAPE>;
+  using L = Layout<DIM, SHAPE>;
+  using SL = Slot<DIM>;
+  constexpr int NT = S::NT;
+  constexpr int NV = S::NV;
+  constexpr int NA = L::NA;
+  constexpr int CQ = kChunk / 4;  // quads per lane per staging tile
+  constexpr int TQ = kTile / 4;   // quads per staging tile
+  constexpr bool CELLKEY = SHAPE != 2;  // runs keyed by cell (QS, NGP)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom &g = a.g;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+  constexpr int nwarps = kThreads / 32;
+  float(&T)[NA][kTile] = *reinterpret_cast<float(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
+  float4 *eb = reinterpret_cast<float4 *>(smem_raw + L::off_eb);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L::off_bar) + warp;
+
+  // tile origin and the block's range of quads
+  const int tile = blockIdx.x;
+  const int ti = tile % g.ntx, tj = (tile / g.ntx) % g.nty, tk = tile / (g.ntx * g.nty);
+  const int i0 = ti * L::TX, j0 = tj * L::TY, k0 = tk * L::TZ;
+  const int64_t nq = (a.n + 3) >> 2;
+  const int64_t qa = tile == 0 ? 0 : (int64_t)a.tile_off[tile] >> 2;
+  const int64_t qe = tile == g.ntiles - 1 ? nq : (int64_t)a.tile_off[tile + 1] >> 2;
+
+  // stage E, B of the tile + halo
+  if (MODE == 0) {
+    for (int c = threadIdx.x; c < L::NEB; c += kThreads) {
+      const int wx = c % L::EX, wy = (c / L::EX) % L::EY, wz = c / (L::EX * L::EY);
+      const int ip = i0 + wx - L::RE + kGhost, kp = k0 + wz - L::RE + kGhost;
+      const int jp = DIM == 2 ? 0 : j0 + wy - L::RE + kGhost;
+      if (ip < 0 || ip >= g.px || kp < 0 || kp >= g.pz || (DIM == 3 && (jp < 0 || jp >= g.py)))
+        continue;  // outside the padded grid: never read by an in-window ion
+      const int v = ip + (DIM == 2 ? 0 : jp * g.sy) + kp * g.sz;
+      eb[2 * c] = __ldg(a.EB + 2 * v);
+      eb[2 * c + 1] = __ldg(a.EB + 2 * v + 1);
+    }
+  }
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};
+  void *gp[8];
+  soa_ptrs<DIM>(a.s, gp);
+  bool failed = false;
+  int k = 0;
+  const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles
 
-  const int64_t nq = (a.n + 3) >> 2;
-  // contiguous range of quads per block (multiple of 32: whole warps)
-  int64_t per = (nq + gridDim.x - 1) / gridDim.x;
-  per = (per + 31) & ~int64_t(31);
-  const int64_t qb = (int64_t)blockIdx.x * per;
-  const int64_t qe = min(nq, qb + per);
-  const bool mx = g.nx > 1, my = DIM == 3 && g.ny > 1, mz = g.nz > 1;
-
-  for (int64_t q0 = qb + (int64_t)warp * 32; q0 < qe; q0 += (int64_t)nwarps * 32) {
-    const int64_t q = q0 + lane;
-    const bool has = q < qe;
-    int4 c4 = make_int4(0, 0, 0, 0);
-    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), Y = X, Z = X, VX = X, VY = X, VZ = X, W = X;
-    if (has) {
-      c4 = __ldcs(reinterpret_cast<const int4 *>(a.s.cell) + q);
-      X = __ldcs(reinterpret_cast<const float4 *>(a.s.ox) + q);
-      if (DIM == 3) Y = __ldcs(reinterpret_cast<const float4 *>(a.s.oy) + q);
-      Z = __ldcs(reinterpret_cast<const float4 *>(a.s.oz) + q);
-      VX = __ldcs(reinterpret_cast<const float4 *>(a.s.vx) + q);
-      VY = __ldcs(reinterpret_cast<const float4 *>(a.s.vy) + q);
-      VZ = __ldcs(reinterpret_cast<const float4 *>(a.s.vz) + q);
-      W = __ldcs(reinterpret_cast<const float4 *>(a.s.w) + q);
+  for (int64_t st = warp; st < nst && !failed; st += nwarps, ++k) {
+    const int64_t q0 = qa + st * TQ;
+    const int nqt = (int)min((int64_t)TQ, qe - q0);
+    if (lane == 0) {
+      bulk_wait_read_all();  // the previous store has read the buffer
+      const uint32_t bytes = (uint32_t)nqt * 16u;
+      mbar_expect_tx(bar, bytes * NA);
+#pragma unroll
+      for (int f = 0; f < NA; ++f)
+        bulk_load(T[f], reinterpret_cast<const char *>(gp[f]) + q0 * 16, bytes, bar);
     }
-    int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-    float ox[4] = {X.x, X.y, X.z, X.w}, oy[4] = {Y.x, Y.y, Y.z, Y.w},
-          oz[4] = {Z.x, Z.y, Z.z, Z.w};
-    float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w},
-          vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
-    const float ww[4] = {W.x, W.y, W.z, W.w};
+    if (!mbar_wait_bounded(bar, (uint32_t)(k & 1))) {
+      failed = true;
+      mbar_wait_bounded(bar, (uint32_t)(k & 1));  // one more bounded chance
+      break;
+    }
 
     float accv[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) accv[j] = 0.f;
-    int key = -1;
+    int key = INT_MIN;
+
+    // lanes start their chunk at a rotated quad so that the 128-bit shared
+    // loads of a quarter-warp hit distinct banks
+    const int rot = CQ > 1 ? (lane / (32 / kChunk)) % CQ : 0;
+#pragma unroll 1
+    for (int jj = 0; jj < CQ; ++jj) {
+      const int jq = (jj + rot) % CQ;
+      const int lq = lane * CQ + jq;  // quad within the staging tile
+      if (lq >= nqt) continue;
+      const int e0 = lq * 4;
+      const int4 c4 = *reinterpret_cast<const int4 *>(&T[SL::CELL][e0]);
+      int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float4 X = *reinterpret_cast<const float4 *>(&T[SL::OX][e0]);
+      const float4 Z = *reinterpret_cast<const float4 *>(&T[SL::OZ][e0]);
+      float4 Y = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (DIM == 3) Y = *reinterpret_cast<const float4 *>(&T[SL::OY][e0]);
+      const float4 VX = *reinterpret_cast<const float4 *>(&T[SL::VX][e0]);
+      const float4 VY = *reinterpret_cast<const float4 *>(&T[SL::VY][e0]);
+      const float4 VZ = *reinterpret_cast<const float4 *>(&T[SL::VZ][e0]);
+      const float4 W = *reinterpret_cast<const float4 *>(&T[SL::W][e0]);
+      float ox[4] = {X.x, X.y, X.z, X.w}, oy[4] = {Y.x, Y.y, Y.z, Y.w},
+            oz[4] = {Z.x, Z.y, Z.z, Z.w};
+      float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w},
+            vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
+      const float ww[4] = {W.x, W.y, W.z, W.w};
+      float rk[4] = {0.f, 0.f, 0.f, 0.f};
+      const int64_t ion0 = (q0 + lq) * 4;
 
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const bool valid = has && (q * 4 + p) < a.n;
-      if (!valid) continue;
-      // decode the cell (indices are validated at load; a corrupt one is
-      // latched and skipped rather than dereferenced)
-      const uint32_t c = (uint32_t)cc[p];
-      if (c >= (uint32_t)g.ncell) {
-        atomicOr(a.err, kErrIndex);
-        continue;
-      }
-      int i, j = 0, k;
-      if (DIM == 2) {
-        k = (int)fdiv(c, g.div_nx);
-        i = (int)c - k * g.nx;
-      } else {
-        const int qq = (int)fdiv(c, g.div_nx);
-        i = (int)c - qq * g.nx;
-        k = (int)fdiv((uint32_t)qq, g.div_ny);
-        j = qq - k * g.ny;
-      }
-      const float dy0 = DIM == 3 ? oy[p] : 0.f;
-      float vxp = vx[p], vyp = vy[p], vzp = vz[p];
+      for (int p = 0; p < 4; ++p) {
+        if (ion0 + p >= a.n) continue;
+        const int vox = cc[p];
+        if (vox < g.vlo || vox >= g.vhi) {
+          atomicOr(a.err, kErrIndex);
+          continue;
+        }
+        // cell relative to the tile; in the window if within H of the tile
+        int ip, jp, kp;
+        voxel_coords(g, vox, ip, jp, kp);
+        const int rx = ip - kGhost - i0, rz = kp - kGhost - k0;
+        const int ry = DIM == 2 ? 0 : jp - kGhost - j0;
+        const bool inwin = rx >= -L::H && rx < L::TX + L::H && rz >= -L::H &&
+                           rz < L::TZ + L::H && (DIM == 2 || (ry >= -L::H && ry < L::TY + L::H));
+        const int eslot = (rx + L::RE) + (DIM == 2 ? 0 : (ry + L::RE) * L::EX) +
+                          (rz + L::RE) * L::EX * L::EY;
+        const float dy0 = DIM == 3 ? oy[p] : 0.f;
+        float vxp = vx[p], vyp = vy[p], vzp = vz[p];
+        float hx = ox[p], hy = dy0, hz = oz[p];
+        int shx = 0, shy = 0, shz = 0;
 
-      if (MODE == 0) {
-        // gather E^n, B^n at x^n (same weights as the deposit)
-        float wt[NT];
-        const int kshift = shape_weights<DIM, SHAPE>(ox[p], dy0, oz[p], g, wt);
-        const int pc = (i + 1) + (DIM == 3 ? (j + 1) * g.sy : 0) + (k + 1) * g.sz + kshift;
-        float ex = 0.f, ey = 0.f, ez = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+        if (MODE == 0) {
+          // gather E^n, B^n at x^n with the deposit's weights (App. B)
+          float wt[NT];
+          const int ks_ = shape_weights<DIM, SHAPE>(ox[p], dy0, oz[p], g, wt);
+          float ex = 0.f, ey = 0.f, ez = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+          if (inwin) {
+            // window offset of the stencil base (CIC may start one cell lower)
+            int eb0 = eslot;
+            if (SHAPE == 2) {
+              eb0 += (ox[p] < 0.f ? -1 : 0) + (oz[p] < 0.f ? -L::EX * L::EY : 0);
+              if (DIM == 3) eb0 += dy0 < 0.f ? -L::EX : 0;
+            }
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          const int pt = pc + target_off<DIM, SHAPE>(t, g);
-          const float4 f0 = __ldg(a.EB + 2 * pt);
-          const float4 f1 = __ldg(a.EB + 2 * pt + 1);
-          ex = fmaf(wt[t], f0.x, ex);
-          ey = fmaf(wt[t], f0.y, ey);
-          ez = fmaf(wt[t], f0.z, ez);
-          bx = fmaf(wt[t], f0.w, bx);
-          by = fmaf(wt[t], f1.x, by);
-          bz = fmaf(wt[t], f1.y, bz);
-        }
-        // Boris: half E kick, rotation, half E kick (Eq. 9)
-        const float h = a.k.qmdt2;
-        const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
-        const float tx = h * bx, ty = h * by, tz = h * bz;
-        const float f = 2.f / (1.f + (tx * tx + ty * ty + tz * tz));
-        const float sx = f * tx, sy = f * ty, sz = f * tz;
-        const float vpx = vmx + (vmy * tz - vmz * ty);
-        const float vpy = vmy + (vmz * tx - vmx * tz);
-        const float vpz = vmz + (vmx * ty - vmy * tx);
-        vxp = vmx + (vpy * sz - vpz * sy) + h * ex;
-        vyp = vmy + (vpz * sx - vpx * sz) + h * ey;
-        vzp = vmz + (vpx * sy - vpy * sx) + h * ez;
-      }
-
-      // half-step and full-step positions (Eq. 10, App. B)
-      float hx = ox[p], hy = dy0, hz = oz[p];
-      float nxo = ox[p], nyo = dy0, nzo = oz[p];
-      int ih = i, jh = j, kh = k, in_ = i, jn = j, kn = k;
-      if (MODE == 0) {
-        bool ok = true;
-        if (mx) {
-          hx = ox[p] + vxp * a.k.cx;
-          nxo = ox[p] + vxp * (2.f * a.k.cx);
-          ok = ok && fabsf(nxo) < 3.f;
-        }
-        if (my) {
-          hy = dy0 + vyp * a.k.cy;
-          nyo = dy0 + vyp * (2.f * a.k.cy);
-          ok = ok && fabsf(nyo) < 3.f;
-        }
-        if (mz) {
-          hz = oz[p] + vzp * a.k.cz;
-          nzo = oz[p] + vzp * (2.f * a.k.cz);
-          ok = ok && fabsf(nzo) < 3.f;
-        }
-        if (!ok) {
-          // more than one cell per step or non-finite: latch and freeze
-          atomicOr(a.err, isfinite(vxp + vyp + vzp) ? kErrCfl : kErrNonFinite);
-          hx = nxo = ox[p];
-          hy = nyo = dy0;
-          hz = nzo = oz[p];
-          vxp = vx[p];
-          vyp = vy[p];
-          vzp = vz[p];
-        } else {
-          ih = wrap1(i + rebase(hx), g.nx);
-          in_ = wrap1(i + rebase(nxo), g.nx);
-          if (DIM == 3) {
-            jh = wrap1(j + rebase(hy), g.ny);
-            jn = wrap1(j + rebase(nyo), g.ny);
+            for (int t = 0; t < NT; ++t) {
+              int wo;
+              if (SHAPE == 0) wo = 0;
+              else if (SHAPE == 1)
+                wo = DIM == 2 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? L::EX : -L::EX)
+                              : (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? L::EX
+                                 : t == 4 ? -L::EX : t == 5 ? L::EX * L::EY : -L::EX * L::EY);
+              else
+                wo = DIM == 2 ? (t & 1) + ((t >> 1) & 1) * L::EX
+                              : (t & 1) + ((t >> 1) & 1) * L::EX + ((t >> 2) & 1) * L::EX * L::EY;
+              const float4 f0 = eb[2 * (eb0 + wo)];
+              const float4 f1 = eb[2 * (eb0 + wo) + 1];
+              ex = fmaf(wt[t], f0.x, ex);
+              ey = fmaf(wt[t], f0.y, ey);
+              ez = fmaf(wt[t], f0.z, ez);
+              bx = fmaf(wt[t], f0.w, bx);
+              by = fmaf(wt[t], f1.x, by);
+              bz = fmaf(wt[t], f1.y, bz);
+            }
+          } else {
+            const int pc = vox + ks_;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+              const int pt = pc + target_off<DIM, SHAPE>(t, g);
+              const float4 f0 = __ldg(a.EB + 2 * pt);
+              const float4 f1 = __ldg(a.EB + 2 * pt + 1);
+              ex = fmaf(wt[t], f0.x, ex);
+              ey = fmaf(wt[t], f0.y, ey);
+              ez = fmaf(wt[t], f0.z, ez);
+              bx = fmaf(wt[t], f0.w, bx);
+              by = fmaf(wt[t], f1.x, by);
+              bz = fmaf(wt[t], f1.y, bz);
+            }
           }
-          kh = wrap1(k + rebase(hz), g.nz);
-          kn = wrap1(k + rebase(nzo), g.nz);
+          // Boris: half E kick, rotation, half E kick (Eq. 9)
+          const float h = a.k.qmdt2;
+          const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
+          const float tx = h * bx, ty = h * by, tz = h * bz;
+          const float f = 2.f / (1.f + (tx * tx + ty * ty + tz * tz));
+          const float sx = f * tx, sy = f * ty, sz = f * tz;
+          const float vpx = vmx + (vmy * tz - vmz * ty);
+          const float vpy = vmy + (vmz * tx - vmx * tz);
+          const float vpz = vmz + (vmx * ty - vmy * tx);
+          vxp = vmx + (vpy * sz - vpz * sy) + h * ex;
+          vyp = vmy + (vpz * sx - vpx * sz) + h * ey;
+          vzp = vmz + (vpx * sy - vpy * sx) + h * ez;
+
+          // half-step and full-step positions (Eq. 10; App. B); the
+          // displacement coefficients are 0 along single-cell axes
+          hx = ox[p] + vxp * a.k.cx;
+          hz = oz[p] + vzp * a.k.cz;
+          float nxo = ox[p] + vxp * (2.f * a.k.cx);
+          float nzo = oz[p] + vzp * (2.f * a.k.cz);
+          float nyo = dy0;
+          bool ok = fabsf(nxo) < 3.f && fabsf(nzo) < 3.f;
+          if (DIM == 3) {
+            hy = dy0 + vyp * a.k.cy;
+            nyo = dy0 + vyp * (2.f * a.k.cy);
+            ok = ok && fabsf(nyo) < 3.f;
+          }
+          if (!ok) {
+            // more than one cell in a step, or non-finite: latch and freeze
+            atomicOr(a.err, isfinite(vxp + vyp + vzp) ? kErrCfl : kErrNonFinite);
+            hx = nxo = ox[p];
+            hy = nyo = dy0;
+            hz = nzo = oz[p];
+            vxp = vx[p];
+            vyp = vy[p];
+            vzp = vz[p];
+          }
+          shx = rebase(hx);
+          shz = rebase(hz);
+          const int mx = rebase(nxo), mz = rebase(nzo);
+          int my = 0;
+          if (DIM == 3) {
+            shy = rebase(hy);
+            my = rebase(nyo);
+          }
+          // new cell, wrapped into the interior
+          const int i1 = ip - kGhost + mx, k1 = kp - kGhost + mz;
+          const int j1 = DIM == 2 ? 0 : jp - kGhost + my;
+          const int iw = i1 < 0 ? i1 + g.nx : (i1 >= g.nx ? i1 - g.nx : i1);
+          const int kw = k1 < 0 ? k1 + g.nz : (k1 >= g.nz ? k1 - g.nz : k1);
+          const int jw = DIM == 2 ? 0 : (j1 < 0 ? j1 + g.ny : (j1 >= g.ny ? j1 - g.ny : j1));
+          cc[p] = voxel_of(g, iw, jw, kw);
+          ox[p] = nxo;
+          if (DIM == 3) oy[p] = nyo;
+          oz[p] = nzo;
+          vx[p] = vxp;
+          vy[p] = vyp;
+          vz[p] = vzp;
+          const float mw = a.k.mass * ww[p];
+          rk[0] += 0.5f * mw * (vxp * vxp + vyp * vyp + vzp * vzp);
+          rk[1] += mw * vxp;
+          rk[2] += mw * vyp;
+          rk[3] += mw * vzp;
         }
-        // write back into the quad registers
-        cc[p] = in_ + g.nx * (jn + g.ny * kn);
-        ox[p] = nxo;
-        if (DIM == 3) oy[p] = nyo;
-        oz[p] = nzo;
-        vx[p] = vxp;
-        vy[p] = vyp;
-        vz[p] = vzp;
+
+        // deposit q w S / V_c and q w v S / V_c at the half-step position
+        float cv[NV];
+        const int kshift = deposit_values<DIM, SHAPE>(hx, hy, hz, a.k.qvc * ww[p], vxp, vyp,
+                                                      vzp, g, cv);
+        const int pk = vox + shx + shz * g.sz + (DIM == 3 ? shy * g.sy : 0) + kshift;
+        const int own = vox;
+        if (pk == key) {
+#pragma unroll
+          for (int jv = 0; jv < NV; ++jv) accv[jv] += cv[jv];
+        } else if (!CELLKEY || pk == own || key == INT_MIN) {
+          // a new run: flush the current one and start from this ion
+          if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, accv);
+          key = pk;
+#pragma unroll
+          for (int jv = 0; jv < NV; ++jv) accv[jv] = cv[jv];
+        } else {
+          flush_direct<DIM, SHAPE>(a, pk, cv);  // crossed into another cell
+        }
       }
 
-      // deposit q w S / V_c and q w v S / V_c at the half-step position
-      float wt[NT];
-      const int kshift = shape_weights<DIM, SHAPE>(hx, hy, hz, g, wt);
-      const int pk = (ih + 1) + (DIM == 3 ? (jh + 1) * g.sy : 0) + (kh + 1) * g.sz + kshift;
-      const float s = a.k.qvc * ww[p];
-      float cv[NV];
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const float st = wt[t] * s;
-        cv[4 * t + 0] = st;
-        cv[4 * t + 1] = st * vxp;
-        cv[4 * t + 2] = st * vyp;
-        cv[4 * t + 3] = st * vzp;
-      }
-      if (key < 0 || pk == key) {
-        key = pk;
-#pragma unroll
-        for (int jv = 0; jv < NV; ++jv) accv[jv] += cv[jv];
-      } else {
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-          red_v4(a.acc + pk + target_off<DIM, SHAPE>(t, g), cv[4 * t], cv[4 * t + 1],
-                 cv[4 * t + 2], cv[4 * t + 3]);
-      }
       if (MODE == 0) {
-        const float mw = a.k.mass * ww[p];
-        kahan_add(ks[0], kc[0], 0.5f * mw * (vxp * vxp + vyp * vyp + vzp * vzp));
-        kahan_add(ks[1], kc[1], mw * vxp);
-        kahan_add(ks[2], kc[2], mw * vyp);
-        kahan_add(ks[3], kc[3], mw * vzp);
+        *reinterpret_cast<int4 *>(&T[SL::CELL][e0]) = make_int4(cc[0], cc[1], cc[2], cc[3]);
+        *reinterpret_cast<float4 *>(&T[SL::OX][e0]) = make_float4(ox[0], ox[1], ox[2], ox[3]);
+        if (DIM == 3)
+          *reinterpret_cast<float4 *>(&T[SL::OY][e0]) = make_float4(oy[0], oy[1], oy[2], oy[3]);
+        *reinterpret_cast<float4 *>(&T[SL::OZ][e0]) = make_float4(oz[0], oz[1], oz[2], oz[3]);
+        *reinterpret_cast<float4 *>(&T[SL::VX][e0]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+        *reinterpret_cast<float4 *>(&T[SL::VY][e0]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+        *reinterpret_cast<float4 *>(&T[SL::VZ][e0]) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) kahan_add(ks[m], kc[m], rk[m]);
       }
     }
+    if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, accv);
 
-    if (MODE == 0 && has) {
-      __stcs(reinterpret_cast<int4 *>(a.s.cell) + q, make_int4(cc[0], cc[1], cc[2], cc[3]));
-      __stcs(reinterpret_cast<float4 *>(a.s.ox) + q, make_float4(ox[0], ox[1], ox[2], ox[3]));
-      if (DIM == 3)
-        __stcs(reinterpret_cast<float4 *>(a.s.oy) + q, make_float4(oy[0], oy[1], oy[2], oy[3]));
-      __stcs(reinterpret_cast<float4 *>(a.s.oz) + q, make_float4(oz[0], oz[1], oz[2], oz[3]));
-      __stcs(reinterpret_cast<float4 *>(a.s.vx) + q, make_float4(vx[0], vx[1], vx[2], vx[3]));
-      __stcs(reinterpret_cast<float4 *>(a.s.vy) + q, make_float4(vy[0], vy[1], vy[2], vy[3]));
-      __stcs(reinterpret_cast<float4 *>(a.s.vz) + q, make_float4(vz[0], vz[1], vz[2], vz[3]));
-    }
-
-    // warp aggregation: lanes sharing a key are summed by a reduce-scatter;
-    // lane l then owns value l = (target l/4, channel l%4) of that key.
-    unsigned pending = __ballot_sync(kFull, key >= 0);
-    int rounds = 0;
-    while (pending) {
-      if (rounds == 3) {
-        // many distinct keys in this warp: the rest add their own sums
-        if (key >= 0 && ((pending >> lane) & 1u)) {
+    // make the staged results visible to the bulk copy and write back every
+    // field but w
+    fence_async_smem();
+    __syncwarp();
+    if (MODE == 0 && lane == 0) {
+      const uint32_t bytes = (uint32_t)nqt * 16u;
 #pragma unroll
-          for (int t = 0; t < NT; ++t)
-            red_v4(a.acc + key + target_off<DIM, SHAPE>(t, g), accv[4 * t], accv[4 * t + 1],
-                   accv[4 * t + 2], accv[4 * t + 3]);
-        }
-        break;
-      }
-      const int leader = __ffs(pending) - 1;
-      const int lkey = __shfl_sync(kFull, key, leader);
-      const unsigned peers = __ballot_sync(kFull, key == lkey);
-      const bool mine = (peers >> lane) & 1u;
-      float v[32];
-#pragma unroll
-      for (int jv = 0; jv < 32; ++jv) v[jv] = (jv < NV && mine) ? accv[jv] : 0.f;
-      const float tot = reduce_scatter32(v, lane);
-      if (lane < NV) {
-        const int t = lane >> 2;
-        float *dst = reinterpret_cast<float *>(a.acc + lkey + target_off<DIM, SHAPE>(t, g)) +
-                     (lane & 3);
-        red_f32(dst, tot);
-      }
-      pending &= ~peers;
-      ++rounds;
+      for (int f = 0; f < NA; ++f)
+        if (f != SL::W) bulk_store(reinterpret_cast<char *>(gp[f]) + q0 * 16, T[f], bytes);
+      bulk_commit();
     }
   }
+  if (failed && lane == 0) atomicOr(a.err, kErrTimeout);
+  if (lane == 0) bulk_wait_all();  // stores done before the block exits
+  __syncthreads();
 
   if (MODE == 0) {
     // FP64 block partials of W_K and P (deterministic order)
-    __shared__ double red[8][4];
+    __shared__ double red[nwarps][4];
     double d[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -404,8 +653,21 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
 }
 
 template <int DIM, int SHAPE, int MODE>
+size_t push_smem() {
+  return Layout<DIM, SHAPE>::bytes;
+}
+
+template <int DIM, int SHAPE, int MODE>
 cudaError_t launch_t(const PushArgs &a, int blocks, cudaStream_t s) {
-  push_kernel<DIM, SHAPE, MODE><<<blocks, 256, 0, s>>>(a);
+  const size_t smem = push_smem<DIM, SHAPE, MODE>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(push_kernel<DIM, SHAPE, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  push_kernel<DIM, SHAPE, MODE><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -420,15 +682,8 @@ cudaError_t launch_shape(int shape, const PushArgs &a, int blocks, cudaStream_t 
 
 }  // namespace
 
-int push_grid_blocks(int device) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, push_kernel<2, 1, 0>, 256, 0);
-  if (per < 1) per = 1;
-  if (sms < 1) sms = 1;
-  return sms * per;
-}
+bool uses_records(const hv_ctx *c) { return c->p.shape == 1 && c->g.dim2; }
+
 
 cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   Species &sp = c->sp[species];
@@ -436,8 +691,11 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   PushArgs a;
   a.s = sp.buf[sp.cur];
   a.n = sp.n;
+  a.tile_off = sp.tile_off;
   a.EB = c->EB;
   a.acc = c->acc;
+  a.accm = c->accm[c->accpar];
+  a.wrapvox = c->wrapvox;
   a.g = c->g;
   a.k.qmdt2 = (float)(0.5 * sp.q / sp.m * c->p.dt);
   a.k.cx = c->g.nx > 1 ? (float)(c->p.dt / c->p.dx) : 0.f;
@@ -449,12 +707,13 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.err = c->err;
   c->launches++;
   const int shape = c->p.shape;
+  const int blocks = c->g.ntiles;  // one block per supercell tile
   if (c->g.dim2) {
-    return mode == 0 ? launch_shape<2, 0>(shape, a, c->push_blocks, c->stream)
-                     : launch_shape<2, 1>(shape, a, c->push_blocks, c->stream);
+    return mode == 0 ? launch_shape<2, 0>(shape, a, blocks, c->stream)
+                     : launch_shape<2, 1>(shape, a, blocks, c->stream);
   }
-  return mode == 0 ? launch_shape<3, 0>(shape, a, c->push_blocks, c->stream)
-                   : launch_shape<3, 1>(shape, a, c->push_blocks, c->stream);
+  return mode == 0 ? launch_shape<3, 0>(shape, a, blocks, c->stream)
+                   : launch_shape<3, 1>(shape, a, blocks, c->stream);
 }
 
 }  // namespace hv

@@ -282,9 +282,11 @@ bool scratch_reserve(SortScratch *&s, int64_t n, cudaStream_t st) {
   return true;
 }
 
-// Radix passes over keys[n]; returns the buffer holding the permutation.
+// Radix passes over keys[n]; returns the buffers holding the permutation and
+// the sorted keys.
 cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratch *s,
-                       cudaStream_t st, int32_t **perm_out, int64_t *launches) {
+                       cudaStream_t st, int32_t **perm_out, int64_t *launches,
+                       int32_t **keys_out = nullptr) {
   const int bits = key_bits(nkeys);
   const int passes = (bits + 7) / 8;
   const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -309,7 +311,42 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
     out ^= 1;
   }
   *perm_out = const_cast<int32_t *>(vin);
+  if (keys_out) *keys_out = const_cast<int32_t *>(kin);
   return cudaSuccess;
+}
+
+// Supercell sort key of every ion from its voxel index.
+__global__ void supercell_key_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *key) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)vox[t];
+    const uint32_t q = fdiv(v, g.div_px);
+    const int ip = (int)(v - q * (uint32_t)g.px);
+    int jp = kGhost, kp;
+    if (g.dim2) {
+      kp = (int)q;
+    } else {
+      kp = (int)fdiv(q, g.div_py);
+      jp = (int)q - kp * g.py;
+    }
+    key[t] = supercell_key(g, ip - kGhost, jp - kGhost, kp - kGhost);
+  }
+}
+
+// Tile ranges from sorted keys: off[t] = first ion whose tile is >= t.
+__global__ void tile_offsets_kernel(const int32_t *skey, int64_t n, int tlog, int ntiles,
+                                    int *off) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tprev = i == 0 ? -1 : (skey[i - 1] >> tlog);
+    const int tcur = i == n ? ntiles : (skey[i] >> tlog);
+    for (int t = tprev + 1; t <= tcur; ++t) off[t] = (int)i;
+  }
+}
+
+__global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x)
+    off[t] = (int)(n * t / ntiles);
 }
 
 }  // namespace
@@ -319,18 +356,35 @@ hv_status sort_species(hv_ctx *c, int sidx) {
   if (sp.n <= 1) return HV_OK;
   if (!scratch_reserve(c->sort, sp.n, c->stream))
     return fail(HV_ENOMEM, "sort scratch allocation failed");
-  int32_t *perm = nullptr;
+  const Geom &g = c->g;
   Soa &in = sp.buf[sp.cur];
-  cudaError_t e = radix_perm(in.cell, sp.n, c->g.ncell, c->sort, c->stream, &perm, &c->launches);
+  int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 1024);
+  // keys in k[1]: the radix passes write k[0], k[1], ... so the input is
+  // consumed before it is overwritten
+  supercell_key_kernel<<<blocks, 256, 0, c->stream>>>(g, in.cell, sp.n, c->sort->k[1]);
+  c->launches++;
+  int32_t *perm = nullptr, *skeys = nullptr;
+  const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
+  cudaError_t e = radix_perm(c->sort->k[1], sp.n, nkeys, c->sort, c->stream, &perm, &c->launches,
+                             &skeys);
   if (e != cudaSuccess) return cuda_fail(e, "sort passes");
   Soa &out = sp.buf[sp.cur ^ 1];
-  int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 1024);
   gather_kernel<<<blocks, 256, 0, c->stream>>>(in, out, perm, sp.n);
-  c->launches++;
+  tile_offsets_kernel<<<(int)std::min<int64_t>((sp.n + 256) / 256, 8 * 1024), 256, 0,
+                        c->stream>>>(skeys, sp.n, g.tlog, g.ntiles, sp.tile_off);
+  c->launches += 2;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sort gather");
   sp.cur ^= 1;
   return HV_OK;
+}
+
+cudaError_t tile_ranges_even(hv_ctx *c, int s) {
+  Species &sp = c->sp[s];
+  tile_even_kernel<<<(c->g.ntiles + 256) / 256, 256, 0, c->stream>>>(sp.n, c->g.ntiles,
+                                                                       sp.tile_off);
+  c->launches++;
+  return cudaGetLastError();
 }
 
 void sort_release(hv_ctx *c) {

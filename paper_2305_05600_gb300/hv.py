@@ -62,6 +62,12 @@ class Prof(ctypes.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class Info(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int64), ("tile", ctypes.c_int32 * 3),
+                ("ntiles", ctypes.c_int32), ("nspecies", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 8), ("step", ctypes.c_int64)]
+
+
 assert ctypes.sizeof(Params) == 112, ctypes.sizeof(Params)
 
 _lib = None
@@ -73,7 +79,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
                            ctypes.c_void_p)
 
 EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_moments",
-           "hv_diag", "hv_get_ions", "hv_profile", "hv_profile_read", "hv_destroy",
+           "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
            "hv_sort_keys", "hv_last_error"]
 
 
@@ -87,7 +93,8 @@ def lib():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        # HV_LIB selects a prebuilt copy of libhv (e.g. a tuning variant)
+        path = os.environ.get("HV_LIB") or _build.build()
         L = ctypes.CDLL(path)
         P, I32, I64, V = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         L.hv_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
@@ -98,6 +105,7 @@ def lib():
         L.hv_moments.argtypes = [P, P, P, P, P, ctypes.c_int]
         L.hv_diag.argtypes = [P, ctypes.POINTER(Diag)]
         L.hv_get_ions.argtypes = [P, I32, ctypes.POINTER(I64), P, P, P, P, ctypes.c_int]
+        L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
         L.hv_profile.argtypes = [P, ctypes.c_int]
         L.hv_profile_read.argtypes = [P, ctypes.POINTER(Prof)]
         L.hv_destroy.argtypes = [P]
@@ -265,6 +273,25 @@ def hv_get_ions(ctx: Ctx, species: int = 0) -> dict:
     _check(lib().hv_get_ions(ctx.handle, species, ctypes.byref(n), cell.ctypes.data,
                              off.ctypes.data, v.ctypes.data, w.ctypes.data, 0))
     return {"cell": cell, "off": off, "v": v, "w": w}
+
+
+def hv_query(ctx: Ctx) -> dict:
+    info = Info()
+    _check(lib().hv_query(ctx.handle, ctypes.byref(info)))
+    return {"ncell": info.ncell, "tile": tuple(info.tile), "ntiles": info.ntiles,
+            "nspecies": info.nspecies, "n": list(info.n)[:info.nspecies], "step": info.step}
+
+
+def supercell_keys(cell, params, tile):
+    """Supercell sort keys of linear cell indices (the order hv_step sorts
+    ions into): tile index, then the cell inside the tile, x fastest."""
+    c = np.asarray(cell, dtype=np.int64)
+    nx, ny = int(params["nx"]), int(params["ny"])
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    tx, ty, tz = tile
+    ntx, nty = -(-nx // tx), -(-ny // ty)
+    t = (i // tx) + ntx * ((j // ty) + nty * (k // tz))
+    return t * (tx * ty * tz) + (i % tx) + tx * ((j % ty) + ty * (k % tz))
 
 
 def hv_profile(ctx: Ctx, enable: bool = True):

@@ -86,6 +86,12 @@ def small_workload(dim, shape):
     return wl
 
 
+def order_of(hvmod, ctx, p):
+    """The library's ion order (supercell-major cells) as an oracle sort key."""
+    tile = hvmod.hv_query(ctx)["tile"]
+    return lambda cell: hvmod.supercell_keys(cell, p, tile)
+
+
 def compare_particles(p, gpu, sp, vscale):
     po = phys_pos(p, sp.cell, sp.off)
     pg = phys_pos(p, gpu["cell"], gpu["off"].astype(np.float64))
@@ -110,7 +116,7 @@ def test_one_step_parity(hvmod, dim, shape):
     assert rel_l2(m0["n"].reshape(-1), sim.n_prev) < 1e-5
     assert rel_l2(m0["E"].reshape(3, -1), sim.E) < 1e-4
     hvmod.hv_step(ctx, 1)
-    sim.step(1, sort_every=1)
+    sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
     g = hvmod.hv_get_ions(ctx, 0)
     vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
     compare_particles(p, g, sim.species[0], vscale)
@@ -140,7 +146,7 @@ def test_smoothing_parity(hvmod):
     ctx = hvmod.load_workload(wl)
     sim = oracle_sim(wl)
     hvmod.hv_step(ctx, 2)
-    sim.step(2, sort_every=1)
+    sim.step(2, sort_every=1, key_fn=order_of(hvmod, ctx, wl.params))
     m = hvmod.hv_moments(ctx)
     assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
     assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
@@ -163,7 +169,7 @@ def test_quasi_1d_and_multispecies(hvmod):
     ctx = hvmod.load_workload(wl)
     sim = oracle_sim(wl)
     hvmod.hv_step(ctx, 3)
-    sim.step(3, sort_every=1)
+    sim.step(3, sort_every=1, key_fn=order_of(hvmod, ctx, wl.params))
     m = hvmod.hv_moments(ctx)
     assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
     assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
