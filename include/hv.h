@@ -194,6 +194,26 @@ void hv_destroy(hv_ctx *ctx);
 hv_status hv_sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
                        int32_t *counts, void *cuda_stream);
 
+/* The same stable key sort as hv_sort_keys, for callers that cannot allocate
+ * device memory: for example an application that hands the whole GPU to its
+ * own memory pool up front, or a latency-critical loop that must not enter
+ * the CUDA allocator because an allocation can synchronise the device.  This
+ * entry point allocates nothing (no cudaMalloc, no allocation hook): its
+ * scratch is one static device array of about 16.3 MB that every GPU which
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart; it is an interface convenience.
+ *   keys [n], perm [n], counts [nkeys] (may be NULL): device memory owned by
+ *   the caller, as for hv_sort_keys; n <= 1,048,576, larger n is rejected
+ *   with HV_EINVAL before any GPU work.
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress per device); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (the call clears what must start at zero), so calls that overlap
+ * on the GPU, from two streams or two threads, race and must be serialised
+ * by the caller.  Runs on cuda_stream and synchronises it. */
+hv_status hv_sort_keys_noalloc(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm,
+                               int32_t *counts, void *cuda_stream);
+
 /* Thread-local description of the last failure (never NULL). */
 const char *hv_last_error(void);
 

@@ -12,6 +12,7 @@
 //             scatter to table offset + rank.
 // A final gather applies the permutation to the particle arrays.
 #include <algorithm>
+#include <mutex>
 
 #include "hv_internal.cuh"
 
@@ -438,3 +439,95 @@ hv_status sort_keys(const int32_t *keys, int64_t n, int32_t nkeys, int32_t *perm
 }
 
 }  // namespace hv
+
+// ----------------------------------------------------------------------------
+// Key sort without any allocation: the same passes as hv_sort_keys, with their
+// scratch in one static device array that every GPU loading the library
+// holds until the process exits.
+// ----------------------------------------------------------------------------
+namespace hv {
+namespace {
+
+constexpr int64_t kNoAllocMaxKeys = int64_t(1) << 20;  // 1,048,576 keys
+constexpr int64_t kNoAllocTable = 256 * ((kNoAllocMaxKeys + kTile - 1) / kTile);
+constexpr int64_t kNoAllocBsum = (kNoAllocTable + kScanChunk - 1) / kScanChunk;
+// words: keys x2, values x2, digit table, chunk sums, error flag (+ padding)
+constexpr int64_t kNoAllocWords = 4 * kNoAllocMaxKeys + kNoAllocTable + kNoAllocBsum + 64;
+constexpr int kNoAllocMaxDevices = 64;
+
+// About 16.3 MB of device memory per GPU.
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+int32_t *g_noalloc_base[kNoAllocMaxDevices];
+
+// Device address of the static scratch on the current device, looked up once
+// per device (the first call on a device does this).
+hv_status noalloc_base(int32_t **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_sort_keys_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(HV_EINVAL, "hv_sort_keys_noalloc: device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return cuda_fail(e, "hv_sort_keys_noalloc: cudaGetSymbolAddress of the static scratch");
+    g_noalloc_base[dev] = static_cast<int32_t *>(p);
+  }
+  *out = g_noalloc_base[dev];
+  return HV_OK;
+}
+
+}  // namespace
+}  // namespace hv
+
+extern "C" hv_status hv_sort_keys_noalloc(const int32_t *keys, int64_t n, int32_t nkeys,
+                                          int32_t *perm, int32_t *counts, void *cuda_stream) {
+  using namespace hv;
+  if (n < 0 || nkeys < 1) return fail(HV_EINVAL, "hv_sort_keys_noalloc: n < 0 or nkeys < 1");
+  if (n > kNoAllocMaxKeys)
+    return fail(HV_EINVAL,
+                "hv_sort_keys_noalloc: n exceeds the 1048576-key limit of its static scratch");
+  if (n > 0 && (!keys || !perm)) return fail(HV_EINVAL, "hv_sort_keys_noalloc: null pointer");
+  int32_t *base = nullptr;
+  hv_status st = noalloc_base(&base);
+  if (st != HV_OK) return st;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  SortScratch s;
+  s.k[0] = base;
+  s.k[1] = base + kNoAllocMaxKeys;
+  s.v[0] = base + 2 * kNoAllocMaxKeys;
+  s.v[1] = base + 3 * kNoAllocMaxKeys;
+  s.table = base + 4 * kNoAllocMaxKeys;
+  s.bsum = s.table + kNoAllocTable;
+  int *bad = reinterpret_cast<int *>(s.bsum + kNoAllocBsum);
+  s.cap_n = kNoAllocMaxKeys;
+  s.cap_table = kNoAllocTable;
+  s.cap_bsum = kNoAllocBsum;
+  s.base = base;
+  s.bytes = 0;
+  // the flag and the counts must start at zero; every other word is written
+  // by the passes before it is read
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
+  if (e == cudaSuccess && counts)
+    e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)nkeys, stream);
+  int64_t launches = 0;
+  if (e == cudaSuccess && n > 0) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * 1024);
+    count_kernel<<<blocks, 256, 0, stream>>>(keys, n, nkeys, counts, bad);
+    e = cudaGetLastError();
+    int32_t *p = nullptr;
+    if (e == cudaSuccess) e = radix_perm(keys, n, nkeys, &s, stream, &p, &launches);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(perm, p, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, stream);
+  }
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_sort_keys_noalloc");
+  if (hbad) return fail(HV_EINVAL, "hv_sort_keys_noalloc: key out of range");
+  return HV_OK;
+}

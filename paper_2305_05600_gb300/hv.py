@@ -80,7 +80,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_moments",
            "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
-           "hv_sort_keys", "hv_last_error"]
+           "hv_sort_keys", "hv_sort_keys_noalloc", "hv_last_error"]
 
 
 def library_path() -> str:
@@ -111,6 +111,7 @@ def lib():
         L.hv_destroy.argtypes = [P]
         L.hv_destroy.restype = None
         L.hv_sort_keys.argtypes = [P, I64, I32, P, P, P]
+        L.hv_sort_keys_noalloc.argtypes = [P, I64, I32, P, P, P]
         L.hv_last_error.restype = ctypes.c_char_p
         for nm in EXPORTS:
             if nm != "hv_destroy" and nm != "hv_last_error":
@@ -319,6 +320,20 @@ def hv_sort_keys(keys, nkeys: int, stream=None):
     counts = torch.empty(int(nkeys), dtype=torch.int32, device=keys.device)
     _check(lib().hv_sort_keys(keys.data_ptr(), n, int(nkeys), perm.data_ptr(),
                               counts.data_ptr(), _stream_handle(stream)))
+    return perm, counts
+
+
+def hv_sort_keys_noalloc(keys, nkeys: int, perm, counts=None, stream=None):
+    """The allocation-free key sort: the caller supplies the output tensors
+    (int32 CUDA perm [n] and optional counts [nkeys]); the library uses only
+    its static device scratch (n <= 1,048,576)."""
+    import torch
+    if keys.dtype != torch.int32 or not keys.is_cuda or perm.dtype != torch.int32:
+        raise TypeError("keys and perm must be int32 CUDA tensors")
+    n = keys.numel()
+    _check(lib().hv_sort_keys_noalloc(keys.data_ptr(), n, int(nkeys), perm.data_ptr(),
+                                      counts.data_ptr() if counts is not None else None,
+                                      _stream_handle(stream)))
     return perm, counts
 
 
