@@ -509,9 +509,20 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       l0 = c->launches;
     }
     for (int k = 0; k < c->p.nsub; ++k) {
-      e = launch_field_stage(c, c->B, c->B, c->Bs, 0.5f * h);
-      if (e == cudaSuccess) e = launch_field_stage(c, c->Bs, c->B, c->B, h);
+      if (fused_substeps(c)) {
+        // B and B* alternate so that a substep never writes what it reads
+        e = launch_substep(c, (k & 1) ? c->Bs : c->B, (k & 1) ? c->B : c->Bs, h);
+      } else {
+        e = launch_field_stage(c, c->B, c->B, c->Bs, 0.5f * h);
+        if (e == cudaSuccess) e = launch_field_stage(c, c->Bs, c->B, c->B, h);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "field stage");
+    }
+    if (fused_substeps(c) && (c->p.nsub & 1)) {
+      // an odd number of fused substeps leaves B^{n+1} in B*: copy it back
+      e = cudaMemcpyAsync(c->B, c->Bs, sizeof(float4) * c->g.ncell, cudaMemcpyDeviceToDevice,
+                          c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "field copy");
     }
     if (ps) {
       cudaEventRecord(ev.e[4], c->stream);

@@ -385,6 +385,167 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// One whole explicit-midpoint substep in the x-z layout, fused:
+//   B* = B - (h/2) curl E(B),  B_out = B - h curl E(B*)
+// A 32x16 tile of outputs needs B on a halo of 6 cells: each Ohm evaluation
+// reaches 2 cells (J = curl B, then lap J) and each curl of E one more.
+// Every input is loaded once into shared memory; both stages then run from
+// there.
+// ----------------------------------------------------------------------------
+namespace sub2d {
+constexpr int SX = 32, SZ = 16, SH = 6;
+__host__ __device__ constexpr int W(int r) { return SX + 2 * r; }
+__host__ __device__ constexpr int N(int r) { return (SX + 2 * r) * (SZ + 2 * r); }
+constexpr int kB = 0;                          // B on R6 (3 planes)
+constexpr int kM = kB + 3 * N(6);              // moments on R5 (4 planes: n, Jix, Jiy, Jiz)
+constexpr int kJ = kM + 4 * N(5);              // J on R5 (stage 1) / R2 (stage 2)
+constexpr int kE = kJ + 3 * N(5);              // E on R4 (stage 1) / R1 (stage 2)
+constexpr int kS = kE + 3 * N(4);              // B* on R3
+constexpr int kFloats = kS + 3 * N(3);
+__device__ __forceinline__ int at(int r, int x, int z) { return (x + r) + (z + r) * W(r); }
+}  // namespace sub2d
+
+struct SubArgs {
+  Geom g;
+  FieldConsts k;
+  const float4 *B;
+  float4 *Bout;
+  const float4 *mom;
+  float h;
+};
+
+// E from Ohm's law at tile point (x, z), with B, J on their own regions.
+__device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int x, int z,
+                                      const float *Bp, int rb, const float *Jp, int rj,
+                                      float &ex, float &ey, float &ez) {
+  using namespace sub2d;
+  const int nb = N(rb), nj = N(rj), nm = N(5);
+  const float *mn = sm + kM, *mjx = mn + nm, *mjy = mjx + nm, *mjz = mjy + nm;
+  const int im = at(5, x, z);
+  const float n0 = fmaxf(mn[im], k.n_floor);
+  auto pe = [&](int i) {
+    const float f = fmaxf(mn[i], k.n_floor);
+    return k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
+  };
+  const float gpx = (pe(im + 1) - pe(im - 1)) * k.idx2;
+  const float gpz = (pe(im + W(5)) - pe(im - W(5))) * k.idz2;
+  const int ij = at(rj, x, z), wj = W(rj);
+  const float *Jx = Jp, *Jy = Jp + nj, *Jz = Jp + 2 * nj;
+  const float jx = Jx[ij], jy = Jy[ij], jz = Jz[ij];
+  const float lx = (Jx[ij + 1] + Jx[ij - 1] - 2.f * jx) * k.ilx + (Jx[ij + wj] + Jx[ij - wj] - 2.f * jx) * k.ilz;
+  const float ly = (Jy[ij + 1] + Jy[ij - 1] - 2.f * jy) * k.ilx + (Jy[ij + wj] + Jy[ij - wj] - 2.f * jy) * k.ilz;
+  const float lz = (Jz[ij + 1] + Jz[ij - 1] - 2.f * jz) * k.ilx + (Jz[ij + wj] + Jz[ij - wj] - 2.f * jz) * k.ilz;
+  const int ib = at(rb, x, z);
+  const float bx = Bp[ib], by = Bp[nb + ib], bz = Bp[2 * nb + ib];
+  const float ux = jx - mjx[im], uy = jy - mjy[im], uz = jz - mjz[im];
+  const float inv = 1.f / n0;
+  ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx;
+  ey = (uz * bx - ux * bz) * inv + k.eta * jy - k.eta_h * ly;
+  ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz;
+}
+
+// J = curl B (y derivatives vanish in the x-z layout) on region rj from B on rb.
+template <int rb, int rj>
+__device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, float *Jp) {
+  using namespace sub2d;
+  const int nb = N(rb), nj = N(rj), wb = W(rb);
+  for (int t_ = (int)threadIdx.x; t_ < N(rj); t_ += blockDim.x) {
+      const int x = t_ % W(rj) - rj, z = t_ / W(rj) - rj;
+      const int b = at(rb, x, z);
+      const float *Bx = Bp, *By = Bp + nb, *Bz = Bp + 2 * nb;
+      const int j = at(rj, x, z);
+      Jp[j] = -(By[b + wb] - By[b - wb]) * k.idz2;
+      Jp[nj + j] = (Bx[b + wb] - Bx[b - wb]) * k.idz2 - (Bz[b + 1] - Bz[b - 1]) * k.idx2;
+      Jp[2 * nj + j] = (By[b + 1] - By[b - 1]) * k.idx2;
+    }
+}
+
+__global__ void __launch_bounds__(256) substep2d_kernel(SubArgs a) {
+  using namespace sub2d;
+  extern __shared__ float sm[];
+  const Geom &g = a.g;
+  const FieldConsts &k = a.k;
+  const int ntx = (g.nx + SX - 1) / SX;
+  const int x0 = (blockIdx.x % ntx) * SX, z0 = (blockIdx.x / ntx) * SZ;
+  float *Bp = sm + kB, *Mp = sm + kM, *Jp = sm + kJ, *Ep = sm + kE, *Sp = sm + kS;
+  auto gidx = [&](int x, int z) {
+    const int ii = wrap_near(x0 + x, g.nx, SX + SH);
+    const int kk = wrap_near(z0 + z, g.nz, SZ + SH);
+    return ii + g.nx * kk;
+  };
+  // load B on R6 and the moments on R5
+  for (int t_ = (int)threadIdx.x; t_ < N(6); t_ += blockDim.x) {
+      const int x = t_ % W(6) - 6, z = t_ / W(6) - 6;
+      const float4 b = a.B[gidx(x, z)];
+      const int i = at(6, x, z);
+      Bp[i] = b.x;
+      Bp[N(6) + i] = b.y;
+      Bp[2 * N(6) + i] = b.z;
+    }
+  for (int t_ = (int)threadIdx.x; t_ < N(5); t_ += blockDim.x) {
+      const int x = t_ % W(5) - 5, z = t_ / W(5) - 5;
+      const float4 m = a.mom[gidx(x, z)];
+      const int i = at(5, x, z);
+      Mp[i] = m.x;
+      Mp[N(5) + i] = m.y;
+      Mp[2 * N(5) + i] = m.z;
+      Mp[3 * N(5) + i] = m.w;
+    }
+  __syncthreads();
+  // stage 1: J(B) on R5, E on R4, B* on R3
+  curl2d<6, 5>(k, Bp, Jp);
+  __syncthreads();
+  for (int t_ = (int)threadIdx.x; t_ < N(4); t_ += blockDim.x) {
+      const int x = t_ % W(4) - 4, z = t_ / W(4) - 4;
+      float ex, ey, ez;
+      ohm2d(sm, k, x, z, Bp, 6, Jp, 5, ex, ey, ez);
+      const int i = at(4, x, z);
+      Ep[i] = ex;
+      Ep[N(4) + i] = ey;
+      Ep[2 * N(4) + i] = ez;
+    }
+  __syncthreads();
+  const float c1 = 0.5f * a.h;
+  for (int t_ = (int)threadIdx.x; t_ < N(3); t_ += blockDim.x) {
+      const int x = t_ % W(3) - 3, z = t_ / W(3) - 3;
+      const int e = at(4, x, z), w = W(4), b = at(6, x, z), s = at(3, x, z);
+      const float *Ex = Ep, *Ey = Ep + N(4), *Ez = Ep + 2 * N(4);
+      const float cx = -(Ey[e + w] - Ey[e - w]) * k.idz2;
+      const float cy = (Ex[e + w] - Ex[e - w]) * k.idz2 - (Ez[e + 1] - Ez[e - 1]) * k.idx2;
+      const float cz = (Ey[e + 1] - Ey[e - 1]) * k.idx2;
+      Sp[s] = Bp[b] - c1 * cx;
+      Sp[N(3) + s] = Bp[N(6) + b] - c1 * cy;
+      Sp[2 * N(3) + s] = Bp[2 * N(6) + b] - c1 * cz;
+    }
+  __syncthreads();
+  // stage 2: J(B*) on R2, E on R1, B_out on the tile
+  curl2d<3, 2>(k, Sp, Jp);
+  __syncthreads();
+  for (int t_ = (int)threadIdx.x; t_ < N(1); t_ += blockDim.x) {
+      const int x = t_ % W(1) - 1, z = t_ / W(1) - 1;
+      float ex, ey, ez;
+      ohm2d(sm, k, x, z, Sp, 3, Jp, 2, ex, ey, ez);
+      const int i = at(1, x, z);
+      Ep[i] = ex;
+      Ep[N(1) + i] = ey;
+      Ep[2 * N(1) + i] = ez;
+    }
+  __syncthreads();
+  for (int t_ = (int)threadIdx.x; t_ < SX * SZ; t_ += blockDim.x) {
+      const int x = t_ % SX, z = t_ / SX;
+      const int gx = x0 + x, gz = z0 + z;
+      if (gx >= g.nx || gz >= g.nz) continue;
+      const int e = at(1, x, z), w = W(1), b = at(6, x, z);
+      const float *Ex = Ep, *Ey = Ep + N(1), *Ez = Ep + 2 * N(1);
+      const float cx = -(Ey[e + w] - Ey[e - w]) * k.idz2;
+      const float cy = (Ex[e + w] - Ex[e - w]) * k.idz2 - (Ez[e + 1] - Ez[e - 1]) * k.idx2;
+      const float cz = (Ey[e + 1] - Ey[e - 1]) * k.idx2;
+      a.Bout[gx + g.nx * gz] = make_float4(Bp[b] - a.h * cx, Bp[N(6) + b] - a.h * cy,
+                                           Bp[2 * N(6) + b] - a.h * cz, 0.f);
+    }
+}
+
 FieldConsts field_consts(const hv_ctx *c) {
   FieldConsts k;
   const hv_params &p = c->p;
@@ -556,6 +717,31 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   a.EB = nullptr;
   c->launches++;
   return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
+}
+
+bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0; }
+
+cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) {
+  SubArgs a;
+  a.g = c->g;
+  a.k = field_consts(c);
+  a.B = Bin;
+  a.Bout = Bout;
+  a.mom = c->mprev;
+  a.h = h;
+  const size_t smem = sub2d::kFloats * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(substep2d_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int ntx = (c->g.nx + sub2d::SX - 1) / sub2d::SX;
+  const int ntz = (c->g.nz + sub2d::SZ - 1) / sub2d::SZ;
+  c->launches++;
+  substep2d_kernel<<<ntx * ntz, 256, smem, c->stream>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {

@@ -182,6 +182,9 @@ bool uses_records(const hv_ctx *c);
 cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                float coef);
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
+// whole explicit-midpoint substeps fused in one kernel (x-z layout)
+bool fused_substeps(const hv_ctx *c);
+cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h);
 cudaError_t launch_diag(hv_ctx *c);
 int grid_reduce_blocks(int device);
 
