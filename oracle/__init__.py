@@ -94,6 +94,10 @@ def lib():
             L.hvo_step.argtypes = [P, P, I64, P, P, P, P, P, P, P]
             L.hvo_sort_stable.argtypes = [P, I64, I64, P, P, P]
             L.hvo_sort_stable.restype = ctypes.c_int
+            L.hvo_filter_net.argtypes = [P, P, P, ctypes.c_int, P, P, P]
+            L.hvo_filter_apply.argtypes = [P, P, P, D, D, ctypes.c_int, P, P]
+            L.hvo_filter_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P, P]
+            L.hvo_filter_loss_grad.restype = D
             _lib = L
     return _lib
 
@@ -291,6 +295,53 @@ def sort_stable(keys, nkeys):
     if rc != 0:
         raise ValueError("key out of range")
     return perm, counts, offsets
+
+
+FILTER_NPARAM = 3492
+
+
+def bf16(a) -> np.ndarray:
+    """Round to bfloat16 (nearest even) and return as float64."""
+    f = np.asarray(a, dtype=np.float32).copy()
+    u = f.view(np.uint32)
+    lsb = (u >> 16) & 1
+    r = ((u.astype(np.uint64) + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    special = (u & 0x7F800000) == 0x7F800000
+    r[special] = u[special]
+    return r.view(np.float32).astype(np.float64)
+
+
+def filter_net(g, params, x, round_bf16=True):
+    """Network output f for normalised moments x [4][ncell]; also h1, h2."""
+    P = _f64(params)
+    x = _f64(x).reshape(4, -1)
+    nce = ncell(g)
+    f = np.zeros(4 * nce)
+    h1 = np.zeros(16 * nce)
+    h2 = np.zeros(16 * nce)
+    lib().hvo_filter_net(ctypes.byref(g), _p(P), _p(x), int(round_bf16), _p(f), _p(h1), _p(h2))
+    return f.reshape(4, -1), h1.reshape(16, -1), h2.reshape(16, -1)
+
+
+def filter_apply(g, params, scale, nmin, rmax, m, round_bf16=True):
+    P = _f64(params)
+    s = _f64(scale)
+    m = _f64(m).reshape(4, -1)
+    y = np.zeros_like(m)
+    lib().hvo_filter_apply(ctypes.byref(g), _p(P), _p(s), float(nmin), float(rmax),
+                           int(round_bf16), _p(m), _p(y))
+    return y
+
+
+def filter_loss_grad(g, params, scale, m, target, round_bf16=True):
+    P = _f64(params)
+    s = _f64(scale)
+    m = _f64(m).reshape(4, -1)
+    t = _f64(target).reshape(4, -1)
+    grad = np.zeros(FILTER_NPARAM)
+    loss = lib().hvo_filter_loss_grad(ctypes.byref(g), _p(P), _p(s), int(round_bf16), _p(m),
+                                      _p(t), _p(grad))
+    return loss, grad
 
 
 class Sim:

@@ -520,3 +520,196 @@ int hvo_sort_stable(const int64_t *key, int64_t n, int64_t nkeys, int64_t *perm,
   free(next);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned moment filter (not in the paper: a residual convolutional filter */
+/* of the deposited moments, with the paper's binomial smoothing (Sec. 2.2) */
+/* as the fallback).  Written for the x-z layout (ny = 1).                  */
+/*   x_c = m_c / s_c  (c = n, Jx, Jy, Jz)                                   */
+/*   h1 = bf16(relu(conv3x3(bf16(x); W1, b1)))       4 -> 16 channels      */
+/*   h2 = bf16(relu(conv3x3(h1; W2, b2)))            16 -> 16               */
+/*   f  = conv3x3(h2; W3, b3)                        16 -> 4                */
+/*   y_c = m_c + s_c f_c                                                   */
+/* conv3x3 is a periodic cross-correlation: out[o](i,k) = b[o] +            */
+/* sum_c sum_{a,b in -1..1} W[o][c][b+1][a+1] in[c](i+a, k+b).              */
+/* Gate: a cell keeps the binomial-smoothed moments (one (1/4,1/2,1/4)      */
+/* pass per axis of the raw deposit) where n < nmin or |s_n f_n| >          */
+/* rmax * max(n, n_floor).  `round` = 0 disables the bf16 rounding (used    */
+/* by the finite-difference gradient pins).                                 */
+/* Parameter layout (floats): W1[16][4][3][3] b1[16] W2[16][16][3][3]       */
+/* b2[16] W3[4][16][3][3] b3[4]  (3492 values).                             */
+/* ------------------------------------------------------------------------ */
+
+static double bf16_round(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf / nan */
+  uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7fffu + lsb) & 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+static void conv3x3(const hvo_grid *g, const double *in, int cin, const double *W,
+                    const double *b, int cout, double *out) {
+  int64_t nx = g->nx, nz = g->nz, nc = nx * nz;
+  for (int o = 0; o < cout; ++o)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t i = 0; i < nx; ++i) {
+        double s = b[o];
+        for (int c = 0; c < cin; ++c)
+          for (int db = -1; db <= 1; ++db)
+            for (int da = -1; da <= 1; ++da) {
+              int64_t ii = wrapi(i + da, nx), kk = wrapi(k + db, nz);
+              s += W[((o * cin + c) * 3 + (db + 1)) * 3 + (da + 1)] * in[c * nc + kk * nx + ii];
+            }
+        out[o * nc + k * nx + i] = s;
+      }
+}
+
+/* Forward pass of the network on x [4][ncell]; writes f [4][ncell] and (if
+ * non-NULL) the layer outputs h1, h2 [16][ncell]. */
+void hvo_filter_net(const hvo_grid *g, const double *P, const double *x, int round_bf16,
+                    double *f, double *h1o, double *h2o) {
+  int64_t nc = g->nx * g->nz;
+  const double *W1 = P, *b1 = W1 + 16 * 4 * 9, *W2 = b1 + 16, *b2 = W2 + 16 * 16 * 9;
+  const double *W3 = b2 + 16, *b3 = W3 + 4 * 16 * 9;
+  double *xb = (double *)malloc(sizeof(double) * 4 * nc);
+  double *h1 = (double *)malloc(sizeof(double) * 16 * nc);
+  double *h2 = (double *)malloc(sizeof(double) * 16 * nc);
+  for (int64_t t = 0; t < 4 * nc; ++t) xb[t] = round_bf16 ? bf16_round(x[t]) : x[t];
+  conv3x3(g, xb, 4, W1, b1, 16, h1);
+  for (int64_t t = 0; t < 16 * nc; ++t) {
+    double v = h1[t] > 0.0 ? h1[t] : 0.0;
+    h1[t] = round_bf16 ? bf16_round(v) : v;
+  }
+  conv3x3(g, h1, 16, W2, b2, 16, h2);
+  for (int64_t t = 0; t < 16 * nc; ++t) {
+    double v = h2[t] > 0.0 ? h2[t] : 0.0;
+    h2[t] = round_bf16 ? bf16_round(v) : v;
+  }
+  conv3x3(g, h2, 16, W3, b3, 4, f);
+  if (h1o) memcpy(h1o, h1, sizeof(double) * 16 * nc);
+  if (h2o) memcpy(h2o, h2, sizeof(double) * 16 * nc);
+  free(xb);
+  free(h1);
+  free(h2);
+}
+
+/* The filter with its gate: m [4][ncell] (n, Jx, Jy, Jz) in, y [4][ncell]
+ * out.  Parameters are used as given (the caller passes bf16 values when
+ * emulating the device); s[4] are the channel scales. */
+void hvo_filter_apply(const hvo_grid *g, const double *P, const double *s, double nmin,
+                      double rmax, int round_bf16, const double *m, double *y) {
+  int64_t nc = g->nx * g->nz;
+  double *x = (double *)malloc(sizeof(double) * 4 * nc);
+  double *f = (double *)malloc(sizeof(double) * 4 * nc);
+  double *sm = (double *)malloc(sizeof(double) * 4 * nc);
+  for (int c = 0; c < 4; ++c)
+    for (int64_t t = 0; t < nc; ++t) x[c * nc + t] = m[c * nc + t] / s[c];
+  hvo_filter_net(g, P, x, round_bf16, f, NULL, NULL);
+  memcpy(sm, m, sizeof(double) * 4 * nc);
+  hvo_smooth(g, sm, 4, 1);
+  for (int64_t t = 0; t < nc; ++t) {
+    double n = m[t];
+    double r = fabs(s[0] * f[t]);
+    double ref = n > g->n_floor ? n : g->n_floor;
+    int fallback = (n < nmin) || (r > rmax * ref);
+    for (int c = 0; c < 4; ++c)
+      y[c * nc + t] = fallback ? sm[c * nc + t] : m[c * nc + t] + s[c] * f[c * nc + t];
+  }
+  free(x);
+  free(f);
+  free(sm);
+}
+
+/* Loss and gradient for one training pair (no gate): loss = mean over
+ * cells and channels of ((x + f(x)) - t)^2 with x = m / s, t = target / s.
+ * grad [3492] receives d loss / d P.  Backward in FP64 through the same
+ * rounded activations as the forward (straight-through at the bf16
+ * rounding points). */
+double hvo_filter_loss_grad(const hvo_grid *g, const double *P, const double *s,
+                            int round_bf16, const double *m, const double *target,
+                            double *grad) {
+  int64_t nx = g->nx, nz = g->nz, nc = nx * nz;
+  const double *W2 = P + 16 * 4 * 9 + 16, *W3 = W2 + 16 * 16 * 9 + 16;
+  double *x = (double *)malloc(sizeof(double) * 4 * nc);
+  double *xb = (double *)malloc(sizeof(double) * 4 * nc);
+  double *f = (double *)malloc(sizeof(double) * 4 * nc);
+  double *h1 = (double *)malloc(sizeof(double) * 16 * nc);
+  double *h2 = (double *)malloc(sizeof(double) * 16 * nc);
+  double *df = (double *)malloc(sizeof(double) * 4 * nc);
+  double *dh2 = (double *)calloc((size_t)(16 * nc), sizeof(double));
+  double *dh1 = (double *)calloc((size_t)(16 * nc), sizeof(double));
+  for (int c = 0; c < 4; ++c)
+    for (int64_t t = 0; t < nc; ++t) x[c * nc + t] = m[c * nc + t] / s[c];
+  for (int64_t t = 0; t < 4 * nc; ++t) xb[t] = round_bf16 ? bf16_round(x[t]) : x[t];
+  hvo_filter_net(g, P, x, round_bf16, f, h1, h2);
+  double loss = 0.0, norm = 1.0 / (double)(4 * nc);
+  for (int c = 0; c < 4; ++c)
+    for (int64_t t = 0; t < nc; ++t) {
+      double e = x[c * nc + t] + f[c * nc + t] - target[c * nc + t] / s[c];
+      loss += e * e * norm;
+      df[c * nc + t] = 2.0 * e * norm;
+    }
+  for (int q = 0; q < 3492; ++q) grad[q] = 0.0;
+  double *gW1 = grad, *gb1 = gW1 + 16 * 4 * 9, *gW2 = gb1 + 16, *gb2 = gW2 + 16 * 16 * 9;
+  double *gW3 = gb2 + 16, *gb3 = gW3 + 4 * 16 * 9;
+  /* layer 3: f = conv(h2; W3) + b3 */
+  for (int o = 0; o < 4; ++o)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t i = 0; i < nx; ++i) {
+        double d = df[o * nc + k * nx + i];
+        gb3[o] += d;
+        for (int c = 0; c < 16; ++c)
+          for (int db = -1; db <= 1; ++db)
+            for (int da = -1; da <= 1; ++da) {
+              int64_t src = c * nc + wrapi(k + db, nz) * nx + wrapi(i + da, nx);
+              int w = ((o * 16 + c) * 3 + (db + 1)) * 3 + (da + 1);
+              gW3[w] += d * h2[src];
+              dh2[src] += d * W3[w];
+            }
+      }
+  for (int64_t t = 0; t < 16 * nc; ++t)
+    if (h2[t] <= 0.0) dh2[t] = 0.0; /* relu' (h2 is post-relu) */
+  /* layer 2: h2 = relu(conv(h1; W2) + b2) */
+  for (int o = 0; o < 16; ++o)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t i = 0; i < nx; ++i) {
+        double d = dh2[o * nc + k * nx + i];
+        gb2[o] += d;
+        for (int c = 0; c < 16; ++c)
+          for (int db = -1; db <= 1; ++db)
+            for (int da = -1; da <= 1; ++da) {
+              int64_t src = c * nc + wrapi(k + db, nz) * nx + wrapi(i + da, nx);
+              int w = ((o * 16 + c) * 3 + (db + 1)) * 3 + (da + 1);
+              gW2[w] += d * h1[src];
+              dh1[src] += d * W2[w];
+            }
+      }
+  for (int64_t t = 0; t < 16 * nc; ++t)
+    if (h1[t] <= 0.0) dh1[t] = 0.0;
+  /* layer 1: h1 = relu(conv(xb; W1) + b1) */
+  for (int o = 0; o < 16; ++o)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t i = 0; i < nx; ++i) {
+        double d = dh1[o * nc + k * nx + i];
+        gb1[o] += d;
+        for (int c = 0; c < 4; ++c)
+          for (int db = -1; db <= 1; ++db)
+            for (int da = -1; da <= 1; ++da) {
+              int64_t src = c * nc + wrapi(k + db, nz) * nx + wrapi(i + da, nx);
+              gW1[((o * 4 + c) * 3 + (db + 1)) * 3 + (da + 1)] += d * xb[src];
+            }
+      }
+  free(x);
+  free(xb);
+  free(f);
+  free(h1);
+  free(h2);
+  free(df);
+  free(dh2);
+  free(dh1);
+  return loss;
+}
