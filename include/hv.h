@@ -168,6 +168,30 @@ hv_status hv_diag(hv_ctx *ctx, hv_diag_t *out);
 hv_status hv_get_ions(hv_ctx *ctx, int32_t species, int64_t *n_out, int32_t *cell,
                       float *off3, float *v3, float *w, int on_device);
 
+/* Learned moment filter (not in the paper; an addition to its binomial
+ * smoothing of noisy moments, Sec. 2.2): a residual 3x3 convolutional
+ * network 4 -> 16 -> 16 -> 4 with ReLU between layers and periodic padding,
+ * applied to the deposited half-step moments m = (n, Jx, Jy, Jz) of the x-z
+ * layout in place of the binomial passes:
+ *   x = m / scale4,  h1 = bf16(relu(conv(bf16(x), W1) + b1)),
+ *   h2 = bf16(relu(conv(h1, W2) + b2)),  f = conv(h2, W3) + b3,
+ *   m' = m + scale4 * f,
+ * except where n < gate_nmin or |scale4[0] f_n| > gate_rmax max(n, n_floor);
+ * there m' is one (1/4, 1/2, 1/4) pass per axis of m.  conv is the periodic
+ * cross-correlation out[o](i,k) = b[o] + sum_c sum_{a,b} W[o][c][b+1][a+1]
+ * in[c](i+a, k+b).  params (host, 3492 floats, used as bf16):
+ * W1[16][4][3][3] b1[16] W2[16][16][3][3] b2[16] W3[4][16][3][3] b3[4].
+ * params = NULL turns the filter off.  HV_EINVAL for a 3D grid or bad
+ * values.  Takes effect from the next deposit. */
+hv_status hv_set_filter(hv_ctx *ctx, const float *params, const float *scale4, double gate_nmin,
+                        double gate_rmax);
+
+/* Apply the context's learned filter (with its gate) to moments m4
+ * [4][nz][ny][nx] (n, Jx, Jy, Jz), writing y4 of the same shape; both in host
+ * (on_device = 0) or device memory.  For inspection and training data.
+ * HV_ESTATE when no filter is set.  Synchronises. */
+hv_status hv_filter_moments(hv_ctx *ctx, const float *m4, float *y4, int on_device);
+
 /* Fill *out with the context's layout: the library keeps ions sorted
  * tile-major (supercell tile index, then the linear cell inside the tile,
  * both x fastest) whenever it sorts them, with tile extents as reported. */

@@ -648,6 +648,83 @@ hv_status hv_get_ions(hv_ctx *c, int32_t species, int64_t *n_out, int32_t *cell,
   return latched(c, nullptr);
 }
 
+hv_status hv_set_filter(hv_ctx *c, const float *params, const float *scale4, double gate_nmin,
+                        double gate_rmax) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (!params) {
+    c->filter_on = 0;
+    return HV_OK;
+  }
+  if (!c->g.dim2) return fail(HV_EINVAL, "the learned filter is built for the x-z layout (ny = 1)");
+  if (!scale4) return fail(HV_EINVAL, "scale4 is NULL");
+  for (int i = 0; i < kFilterParams; ++i)
+    if (!std::isfinite(params[i])) return fail(HV_EINVAL, "non-finite filter parameter");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(scale4[i]) || scale4[i] <= 0.f)
+      return fail(HV_EINVAL, "filter scales must be finite and > 0");
+  if (!std::isfinite(gate_nmin) || !std::isfinite(gate_rmax) || gate_rmax < 0)
+    return fail(HV_EINVAL, "gate thresholds must be finite (rmax >= 0)");
+  std::vector<__nv_bfloat16> w;
+  std::vector<float> bias;
+  pack_filter(params, w, bias);
+  if (!c->filt.w) {
+    c->filt.w = (__nv_bfloat16 *)ctx_alloc(c, sizeof(__nv_bfloat16) * w.size());
+    c->filt.bias = (float *)ctx_alloc(c, sizeof(float) * bias.size());
+    if (!c->filt.w || !c->filt.bias) return fail(HV_ENOMEM, "filter allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(c->filt.w, w.data(), sizeof(__nv_bfloat16) * w.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->filt.bias, bias.data(), sizeof(float) * bias.size(),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_set_filter upload");
+  for (int i = 0; i < 4; ++i) c->filt.scale[i] = scale4[i];
+  c->filt.nmin = (float)gate_nmin;
+  c->filt.rmax = (float)gate_rmax;
+  c->filter_on = 1;
+  return HV_OK;
+}
+
+hv_status hv_filter_moments(hv_ctx *c, const float *m4, float *y4, int on_device) {
+  if (!c || !m4 || !y4) return fail(HV_EINVAL, "null argument");
+  if (!c->filter_on) return fail(HV_ESTATE, "no filter set");
+  const size_t nc = (size_t)c->g.ncell;
+  float4 *din = (float4 *)dev_alloc(sizeof(float4) * nc, c->stream);
+  float4 *dout = (float4 *)dev_alloc(sizeof(float4) * nc, c->stream);
+  if (!din || !dout) {
+    dev_free(din, sizeof(float4) * nc, c->stream);
+    dev_free(dout, sizeof(float4) * nc, c->stream);
+    return fail(HV_ENOMEM, "hv_filter_moments scratch");
+  }
+  // [4][ncell] component-major in and out
+  std::vector<float4> h(nc);
+  std::vector<float> hm(4 * nc);
+  cudaError_t e = cudaMemcpy(hm.data(), m4, sizeof(float) * 4 * nc,
+                             on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+  for (size_t i = 0; i < nc && e == cudaSuccess; ++i)
+    h[i] = make_float4(hm[i], hm[nc + i], hm[2 * nc + i], hm[3 * nc + i]);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(din, h.data(), sizeof(float4) * nc, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_filter(c, c->filt, din, dout);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), dout, sizeof(float4) * nc, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dev_free(din, sizeof(float4) * nc, c->stream);
+  dev_free(dout, sizeof(float4) * nc, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_filter_moments");
+  for (size_t i = 0; i < nc; ++i) {
+    hm[i] = h[i].x;
+    hm[nc + i] = h[i].y;
+    hm[2 * nc + i] = h[i].z;
+    hm[3 * nc + i] = h[i].w;
+  }
+  e = cudaMemcpy(y4, hm.data(), sizeof(float) * 4 * nc,
+                 on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_filter_moments copy-out");
+  return HV_OK;
+}
+
 hv_status hv_query(const hv_ctx *c, hv_info_t *out) {
   if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
   memset(out, 0, sizeof(*out));

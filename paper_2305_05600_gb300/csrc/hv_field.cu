@@ -677,8 +677,8 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
   a.ext_out = c->mext;
   a.raw_out = c->mtmp;
   a.init = init;
-  const int passes = c->p.smooth_passes;
-  a.fuse = passes == 0;
+  const int passes = c->filter_on ? 0 : c->p.smooth_passes;
+  a.fuse = passes == 0 && !c->filter_on;
   const int nb = elem_blocks(c->g.ncell);
   c->launches++;
   if (uses_records(c)) {
@@ -688,16 +688,23 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
     fold_kernel<<<nb, 256, 0, c->stream>>>(a);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || passes == 0) return e;
+  if (e != cudaSuccess || a.fuse) return e;
   float4 *src = c->mtmp, *dst = c->mhalf;
-  for (int p = 0; p < passes; ++p) {
-    c->launches++;
-    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, src, dst);
-    e = cudaGetLastError();
+  if (c->filter_on) {
+    // learned filter (gated binomial fallback) on the folded deposit
+    e = launch_filter(c, c->filt, c->mtmp, c->mhalf);
     if (e != cudaSuccess) return e;
-    float4 *t = src;
-    src = dst;
-    dst = t;
+    src = c->mhalf;
+  } else {
+    for (int p = 0; p < passes; ++p) {
+      c->launches++;
+      smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, src, dst);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      float4 *t = src;
+      src = dst;
+      dst = t;
+    }
   }
   c->launches++;
   extrap_kernel<<<nb, 256, 0, c->stream>>>(c->g.ncell, src, c->mprev, c->mprev, c->mext, init);

@@ -1,10 +1,12 @@
 // Internal declarations shared by the libhv translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/hv.h"
 
@@ -127,6 +129,17 @@ struct PushConsts {
 
 struct SortScratch;
 
+// Learned moment filter: packed bf16 weights (W1 [16][48], W2 [16][144],
+// W3 [8][144], B matrices stored [n][K]), biases b1[16] b2[16] b3[8], channel
+// scales and the gate thresholds.
+constexpr int kFilterParams = 3492;
+struct FilterParams {
+  __nv_bfloat16 *w;
+  float *bias;
+  float scale[4];
+  float nmin, rmax;
+};
+
 }  // namespace hv
 
 struct hv_ctx {
@@ -142,6 +155,8 @@ struct hv_ctx {
                         // (QS in the x-z layout), used alternately
   int accpar;           // record buffer the next deposit writes
   int *wrapvox;         // padded [npad]: voxel of the interior image
+  int filter_on;        // learned filter replaces the binomial smoothing
+  hv::FilterParams filt;
   float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}
   float4 *mhalf, *mext, *mprev, *mtmp;  // interior moments {n,Jx,Jy,Jz}
   double *pushpart;     // [kMaxSpecies][push_blocks][4]
@@ -182,6 +197,10 @@ bool uses_records(const hv_ctx *c);
 cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                float coef);
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
+// learned moment filter (x-z layout)
+cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out);
+void pack_filter(const float *P, std::vector<__nv_bfloat16> &w, std::vector<float> &bias);
+int filter_weight_count();
 // whole explicit-midpoint substeps fused in one kernel (x-z layout)
 bool fused_substeps(const hv_ctx *c);
 cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h);

@@ -80,7 +80,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_moments",
            "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
-           "hv_sort_keys", "hv_sort_keys_noalloc", "hv_last_error"]
+           "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
+           "hv_last_error"]
 
 
 def library_path() -> str:
@@ -106,6 +107,8 @@ def lib():
         L.hv_diag.argtypes = [P, ctypes.POINTER(Diag)]
         L.hv_get_ions.argtypes = [P, I32, ctypes.POINTER(I64), P, P, P, P, ctypes.c_int]
         L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
+        L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
+        L.hv_filter_moments.argtypes = [P, P, P, ctypes.c_int]
         L.hv_profile.argtypes = [P, ctypes.c_int]
         L.hv_profile_read.argtypes = [P, ctypes.POINTER(Prof)]
         L.hv_destroy.argtypes = [P]
@@ -274,6 +277,31 @@ def hv_get_ions(ctx: Ctx, species: int = 0) -> dict:
     _check(lib().hv_get_ions(ctx.handle, species, ctypes.byref(n), cell.ctypes.data,
                              off.ctypes.data, v.ctypes.data, w.ctypes.data, 0))
     return {"cell": cell, "off": off, "v": v, "w": w}
+
+
+FILTER_NPARAM = 3492
+
+
+def hv_set_filter(ctx: Ctx, params=None, scale=(1.0, 1.0, 1.0, 1.0), gate_nmin=0.0,
+                  gate_rmax=1.0):
+    """Install the learned moment filter (params: 3492 floats) or remove it
+    (params=None)."""
+    if params is None:
+        _check(lib().hv_set_filter(ctx.handle, None, None, 0.0, 0.0))
+        return
+    P = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    if P.size != FILTER_NPARAM:
+        raise ValueError(f"filter needs {FILTER_NPARAM} parameters")
+    S = np.ascontiguousarray(np.asarray(scale, dtype=np.float32).reshape(4))
+    _check(lib().hv_set_filter(ctx.handle, P.ctypes.data, S.ctypes.data, float(gate_nmin),
+                               float(gate_rmax)))
+
+
+def hv_filter_moments(ctx: Ctx, m4) -> np.ndarray:
+    m = np.ascontiguousarray(np.asarray(m4, dtype=np.float32))
+    y = np.zeros_like(m)
+    _check(lib().hv_filter_moments(ctx.handle, m.ctypes.data, y.ctypes.data, 0))
+    return y
 
 
 def hv_query(ctx: Ctx) -> dict:
