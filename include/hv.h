@@ -192,6 +192,28 @@ hv_status hv_set_filter(hv_ctx *ctx, const float *params, const float *scale4, d
  * HV_ESTATE when no filter is set.  Synchronises. */
 hv_status hv_filter_moments(hv_ctx *ctx, const float *m4, float *y4, int on_device);
 
+/* Training of the learned filter on pairs the method generates (a
+ * low-particle-count deposit m and a high-count deposit t of the same state):
+ * loss = mean over cells, channels and pairs of (m/s + f(m/s) - t/s)^2 with
+ * the network of hv_set_filter (no gate).  The forward pass and the
+ * backward-data convolutions run on bf16 tensor cores with FP32
+ * accumulation; weight gradients are accumulated in FP32; Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) updates FP32 master parameters and
+ * refreshes the context's bf16 inference weights.
+ * hv_filter_train_init: set the starting parameters (3492 floats, host) and
+ * scales, reset Adam, and install the filter with its gate open.
+ * hv_filter_grad: loss and gradient (3492 floats, host) at the current
+ * parameters, without an update.  hv_filter_train_step: one Adam step with
+ * learning rate lr.  m and t are [nb][4][nz][ny][nx] float32 (host or device
+ * per on_device).  hv_filter_get_params: the FP32 master parameters.
+ * The x-z layout only.  All synchronise. */
+hv_status hv_filter_train_init(hv_ctx *ctx, const float *params, const float *scale4);
+hv_status hv_filter_grad(hv_ctx *ctx, const float *m, const float *t, int32_t nb,
+                         float *grad_out, double *loss_out, int on_device);
+hv_status hv_filter_train_step(hv_ctx *ctx, const float *m, const float *t, int32_t nb,
+                               double lr, double *loss_out, int on_device);
+hv_status hv_filter_get_params(hv_ctx *ctx, float *params_out);
+
 /* Fill *out with the context's layout: the library keeps ions sorted
  * tile-major (supercell tile index, then the linear cell inside the tile,
  * both x fastest) whenever it sorts them, with tile extents as reported. */

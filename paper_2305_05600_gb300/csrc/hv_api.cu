@@ -725,6 +725,99 @@ hv_status hv_filter_moments(hv_ctx *c, const float *m4, float *y4, int on_device
   return HV_OK;
 }
 
+hv_status hv_filter_train_init(hv_ctx *c, const float *params, const float *scale4) {
+  if (!c || !params || !scale4) return fail(HV_EINVAL, "null argument");
+  hv_status st = hv_set_filter(c, params, scale4, 0.0, 1e30);
+  if (st != HV_OK) return st;
+  if (!c->tr_P) {
+    c->tr_P = (float *)ctx_alloc(c, sizeof(float) * 4 * kFilterParams);
+    c->tr_wt = (__nv_bfloat16 *)ctx_alloc(c, sizeof(__nv_bfloat16) * filter_train_weight_count());
+    c->tr_loss = (double *)ctx_alloc(c, sizeof(double));
+    if (!c->tr_P || !c->tr_wt || !c->tr_loss) return fail(HV_ENOMEM, "training allocation failed");
+    c->tr_m1 = c->tr_P + kFilterParams;
+    c->tr_m2 = c->tr_m1 + kFilterParams;
+    c->tr_grad = c->tr_m2 + kFilterParams;
+  }
+  std::vector<__nv_bfloat16> wt;
+  pack_filter_transposed(params, wt);
+  cudaError_t e = cudaMemcpyAsync(c->tr_P, params, sizeof(float) * kFilterParams,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->tr_m1, 0, sizeof(float) * 3 * kFilterParams, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->tr_wt, wt.data(), sizeof(__nv_bfloat16) * wt.size(),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_filter_train_init");
+  c->tr_step = 0;
+  return HV_OK;
+}
+
+// gradient (and optionally an Adam step) on nb pairs [nb][4][ncell]
+static hv_status filter_train(hv_ctx *c, const float *m, const float *t, int32_t nb, double lr,
+                              int update, float *grad_out, double *loss_out, int on_device) {
+  if (!c || !m || !t || nb < 1) return fail(HV_EINVAL, "bad training arguments");
+  if (!c->tr_P) return fail(HV_ESTATE, "call hv_filter_train_init first");
+  const size_t nc = (size_t)c->g.ncell, nfl = 4 * nc * (size_t)nb;
+  float *raw = (float *)dev_alloc(sizeof(float) * 2 * nfl, c->stream);
+  float4 *il = (float4 *)dev_alloc(sizeof(float4) * 2 * nc * nb, c->stream);
+  if (!raw || !il) {
+    dev_free(raw, sizeof(float) * 2 * nfl, c->stream);
+    dev_free(il, sizeof(float4) * 2 * nc * nb, c->stream);
+    return fail(HV_ENOMEM, "training scratch");
+  }
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(raw, m, sizeof(float) * nfl, k, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw + nfl, t, sizeof(float) * nfl, k, c->stream);
+  if (e == cudaSuccess) e = launch_interleave4(c, nb, raw, il);
+  if (e == cudaSuccess) e = launch_interleave4(c, nb, raw + nfl, il + nc * nb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->tr_loss, 0, sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = launch_filter_grad(c, c->filt, c->tr_wt, il, il + nc * nb, nb, c->tr_grad, c->tr_loss);
+  if (e == cudaSuccess && grad_out)
+    e = cudaMemcpyAsync(grad_out, c->tr_grad, sizeof(float) * kFilterParams,
+                        cudaMemcpyDeviceToHost, c->stream);
+  double loss = 0.0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&loss, c->tr_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) {
+    if (update) {
+      c->tr_step++;
+      e = launch_adam(c, c->tr_P, c->tr_grad, c->tr_m1, c->tr_m2, c->tr_step, (float)lr, c->filt,
+                      c->tr_wt);
+    } else {
+      e = cudaMemsetAsync(c->tr_grad, 0, sizeof(float) * kFilterParams, c->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dev_free(raw, sizeof(float) * 2 * nfl, c->stream);
+  dev_free(il, sizeof(float4) * 2 * nc * nb, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "filter training");
+  if (loss_out) *loss_out = loss;
+  return HV_OK;
+}
+
+hv_status hv_filter_grad(hv_ctx *c, const float *m, const float *t, int32_t nb, float *grad_out,
+                         double *loss_out, int on_device) {
+  return filter_train(c, m, t, nb, 0.0, 0, grad_out, loss_out, on_device);
+}
+
+hv_status hv_filter_train_step(hv_ctx *c, const float *m, const float *t, int32_t nb, double lr,
+                               double *loss_out, int on_device) {
+  if (!std::isfinite(lr) || lr <= 0) return fail(HV_EINVAL, "lr must be finite and > 0");
+  return filter_train(c, m, t, nb, lr, 1, nullptr, loss_out, on_device);
+}
+
+hv_status hv_filter_get_params(hv_ctx *c, float *params_out) {
+  if (!c || !params_out) return fail(HV_EINVAL, "null argument");
+  if (!c->tr_P) return fail(HV_ESTATE, "no training state");
+  cudaError_t e = cudaMemcpyAsync(params_out, c->tr_P, sizeof(float) * kFilterParams,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_filter_get_params");
+  return HV_OK;
+}
+
 hv_status hv_query(const hv_ctx *c, hv_info_t *out) {
   if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
   memset(out, 0, sizeof(*out));

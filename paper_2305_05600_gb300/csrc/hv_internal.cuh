@@ -157,6 +157,12 @@ struct hv_ctx {
   int *wrapvox;         // padded [npad]: voxel of the interior image
   int filter_on;        // learned filter replaces the binomial smoothing
   hv::FilterParams filt;
+  // filter training state: FP32 master parameters, Adam moments, gradient,
+  // transposed bf16 weights for the backward pass
+  float *tr_P, *tr_m1, *tr_m2, *tr_grad;
+  __nv_bfloat16 *tr_wt;
+  double *tr_loss;
+  int tr_step;
   float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}
   float4 *mhalf, *mext, *mprev, *mtmp;  // interior moments {n,Jx,Jy,Jz}
   double *pushpart;     // [kMaxSpecies][push_blocks][4]
@@ -201,6 +207,14 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
 cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out);
 void pack_filter(const float *P, std::vector<__nv_bfloat16> &w, std::vector<float> &bias);
 int filter_weight_count();
+size_t filter_train_weight_count();
+void pack_filter_transposed(const float *P, std::vector<__nv_bfloat16> &wt);
+cudaError_t launch_filter_grad(hv_ctx *c, const FilterParams &fp, const __nv_bfloat16 *wt,
+                               const float4 *m, const float4 *tg, int nbatch, float *grad,
+                               double *loss);
+cudaError_t launch_adam(hv_ctx *c, float *P, float *grad, float *m1, float *m2, int t, float lr,
+                        const FilterParams &fp, __nv_bfloat16 *wt);
+cudaError_t launch_interleave4(hv_ctx *c, int nb, const float *in, float4 *out);
 // whole explicit-midpoint substeps fused in one kernel (x-z layout)
 bool fused_substeps(const hv_ctx *c);
 cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h);

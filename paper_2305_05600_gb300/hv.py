@@ -81,6 +81,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_moments",
            "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
+           "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
+           "hv_filter_get_params",
            "hv_last_error"]
 
 
@@ -109,6 +111,12 @@ def lib():
         L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
         L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
         L.hv_filter_moments.argtypes = [P, P, P, ctypes.c_int]
+        L.hv_filter_train_init.argtypes = [P, P, P]
+        L.hv_filter_grad.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_int]
+        L.hv_filter_train_step.argtypes = [P, P, P, I32, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.hv_filter_get_params.argtypes = [P, P]
         L.hv_profile.argtypes = [P, ctypes.c_int]
         L.hv_profile_read.argtypes = [P, ctypes.POINTER(Prof)]
         L.hv_destroy.argtypes = [P]
@@ -302,6 +310,46 @@ def hv_filter_moments(ctx: Ctx, m4) -> np.ndarray:
     y = np.zeros_like(m)
     _check(lib().hv_filter_moments(ctx.handle, m.ctypes.data, y.ctypes.data, 0))
     return y
+
+
+def hv_filter_train_init(ctx: Ctx, params, scale=(1.0, 1.0, 1.0, 1.0)):
+    P = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    S = np.ascontiguousarray(np.asarray(scale, dtype=np.float32).reshape(4))
+    _check(lib().hv_filter_train_init(ctx.handle, P.ctypes.data, S.ctypes.data))
+
+
+def _pairs(m, t):
+    m = np.ascontiguousarray(np.asarray(m, dtype=np.float32))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+    if m.shape != t.shape:
+        raise ValueError("input and target batches differ in shape")
+    nb = m.shape[0] if m.ndim > 2 else 1
+    return m, t, nb
+
+
+def hv_filter_grad(ctx: Ctx, m, t):
+    """(loss, gradient[3492]) of a batch of pairs [nb][4][...] at the current
+    parameters."""
+    m, t, nb = _pairs(m, t)
+    g = np.zeros(FILTER_NPARAM, np.float32)
+    loss = ctypes.c_double()
+    _check(lib().hv_filter_grad(ctx.handle, m.ctypes.data, t.ctypes.data, nb, g.ctypes.data,
+                                ctypes.byref(loss), 0))
+    return loss.value, g
+
+
+def hv_filter_train_step(ctx: Ctx, m, t, lr: float) -> float:
+    m, t, nb = _pairs(m, t)
+    loss = ctypes.c_double()
+    _check(lib().hv_filter_train_step(ctx.handle, m.ctypes.data, t.ctypes.data, nb, float(lr),
+                                      ctypes.byref(loss), 0))
+    return loss.value
+
+
+def hv_filter_get_params(ctx: Ctx) -> np.ndarray:
+    P = np.zeros(FILTER_NPARAM, np.float32)
+    _check(lib().hv_filter_get_params(ctx.handle, P.ctypes.data))
+    return P
 
 
 def hv_query(ctx: Ctx) -> dict:

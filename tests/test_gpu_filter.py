@@ -115,3 +115,67 @@ def test_step_with_filter_matches_oracle_composition(hvmod):
     assert err_n < 1e-3, err_n
     assert err_B < 1e-6, err_B
     ctx.close()
+
+
+def test_training_gradient_matches_oracle(hvmod):
+    """Loss and gradient of a batch of two pairs against the oracle (FP64
+    backward through the same bf16-rounded forward).  The GPU rounds the
+    back-propagated signals to bf16 for the tensor-core convolutions
+    (relative 2^-9 per value), so the gradient is compared by relative L2
+    (<= 3e-2) and direction (cosine >= 0.999); the loss to 1e-3."""
+    rng = np.random.default_rng(21)
+    p = I.base_params(32, 1, 32, 0.25, 1.0, 0.25, 0.02, 10, Te=0.1)
+    ctx = hvmod.hv_init_grid(p, None)
+    nc = 32 * 32
+    P = random_params(rng, 0.2)
+    scale = np.array([1.0, 0.5, 0.5, 0.5])
+    hvmod.hv_filter_train_init(ctx, P, scale)
+    ms, ts = [], []
+    for b in range(2):
+        t = np.zeros((4, nc))
+        t[0] = 1.0 + 0.3 * rng.normal(size=nc)
+        t[1:] = 0.2 * rng.normal(size=(3, nc))
+        m = t + 0.1 * rng.normal(size=t.shape)
+        ms.append(m.astype(np.float32))
+        ts.append(t.astype(np.float32))
+    m = np.stack(ms).reshape(2, 4, 32, 1, 32)
+    t = np.stack(ts).reshape(2, 4, 32, 1, 32)
+    loss, grad = hvmod.hv_filter_grad(ctx, m, t)
+    g = oracle_grid(p)
+    lo, go = 0.0, np.zeros(O.FILTER_NPARAM)
+    for b in range(2):
+        l_b, g_b = O.filter_loss_grad(g, P, scale, ms[b].astype(np.float64),
+                                      ts[b].astype(np.float64), round_bf16=True)
+        lo += l_b / 2
+        go += g_b / 2
+    assert abs(loss - lo) < 1e-3 * lo, (loss, lo)
+    rel = np.linalg.norm(grad - go) / np.linalg.norm(go)
+    cos = grad.dot(go) / (np.linalg.norm(grad) * np.linalg.norm(go))
+    assert rel < 3e-2 and cos > 0.999, (rel, cos)
+    ctx.close()
+
+
+def test_training_reduces_denoising_loss(hvmod):
+    """Adam steps on noisy/clean pairs lower the loss and the trained
+    parameters move the filtered moments toward the clean ones."""
+    rng = np.random.default_rng(22)
+    p = I.base_params(64, 1, 32, 0.25, 1.0, 0.25, 0.02, 10, Te=0.1)
+    ctx = hvmod.hv_init_grid(p, None)
+    x = (np.arange(64) + 0.5) / 64
+    z = (np.arange(32) + 0.5) / 32
+    X, Z = np.meshgrid(x, z)
+    clean = np.zeros((4, 32, 64))
+    clean[0] = 1.0 + 0.3 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Z)
+    clean[1] = 0.2 * np.cos(2 * np.pi * Z)
+    clean[2] = 0.1 * np.sin(4 * np.pi * X)
+    noisy = [clean + 0.15 * rng.normal(size=clean.shape) for _ in range(4)]
+    m = np.stack(noisy).reshape(4, 4, 32, 1, 64).astype(np.float32)
+    t = np.stack([clean] * 4).reshape(4, 4, 32, 1, 64).astype(np.float32)
+    hvmod.hv_filter_train_init(ctx, np.zeros(O.FILTER_NPARAM) + 0.01 * rng.normal(size=O.FILTER_NPARAM))
+    first = hvmod.hv_filter_train_step(ctx, m, t, 3e-3)
+    for _ in range(150):
+        last = hvmod.hv_filter_train_step(ctx, m, t, 3e-3)
+    assert last < 0.5 * first, (first, last)
+    P = hvmod.hv_filter_get_params(ctx)
+    assert np.isfinite(P).all()
+    ctx.close()
