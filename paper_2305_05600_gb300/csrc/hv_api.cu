@@ -144,11 +144,6 @@ Geom make_geom(const hv_params *p) {
   return g;
 }
 
-int linear_to_voxel(const Geom &g, int c) {
-  const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
-  return voxel_of(g, i, j, k);
-}
-
 __host__ __device__ int voxel_to_linear(const Geom &g, int v) {
   const int k = v / g.sz - kGhost;
   const int r = v % g.sz;
@@ -161,6 +156,38 @@ __global__ void vox_to_linear_kernel(Geom g, const int *in, int *out, int64_t n)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)
     out[t] = voxel_to_linear(g, in[t]);
+}
+
+// Check loaded ions and convert them in place: cell index -> voxel index,
+// relative coordinates along single-cell axes -> 0.  Bits of *bad: 1 bad
+// cell, 2 bad offset, 4 non-finite velocity or weight.
+__global__ void load_check_kernel(Geom g, Soa s, int64_t n, int *bad) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = s.cell[t];
+    int flag = 0;
+    if (c < 0 || c >= g.ncell) {
+      flag |= 1;
+      s.cell[t] = g.vlo;  // keep the array valid for the (discarded) buffer
+    } else {
+      const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+      s.cell[t] = voxel_of(g, i, j, k);
+    }
+    float *o[3] = {s.ox, s.oy, s.oz};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+      if (!o[a]) continue;
+      if (nn[a] == 1) {
+        o[a][t] = 0.f;
+      } else {
+        const float v = o[a][t];
+        if (!(v >= -1.f && v < 1.f)) flag |= 2;
+      }
+    }
+    if (!isfinite(s.vx[t]) || !isfinite(s.vy[t]) || !isfinite(s.vz[t]) || !isfinite(s.w[t]))
+      flag |= 4;
+    if (flag) atomicOr(bad, flag);
+  }
 }
 
 // wrap table: voxel of the interior image of every padded voxel
@@ -385,32 +412,6 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
   if (n < 0 || n >= ((int64_t)1 << 31) - 4) return fail(HV_EINVAL, "n must be in [0, 2^31 - 4)");
   if (n > 0 && (!cell || !off3 || !v3 || !w)) return fail(HV_EINVAL, "null particle array");
   const Geom &g = c->g;
-  // host copies for validation (and upload)
-  std::vector<int32_t> hc(n);
-  std::vector<float> ho(3 * n), hv_(3 * n), hw(n);
-  if (n > 0) {
-    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    cudaError_t e = cudaMemcpy(hc.data(), cell, sizeof(int32_t) * n, k);
-    if (e == cudaSuccess) e = cudaMemcpy(ho.data(), off3, sizeof(float) * 3 * n, k);
-    if (e == cudaSuccess) e = cudaMemcpy(hv_.data(), v3, sizeof(float) * 3 * n, k);
-    if (e == cudaSuccess) e = cudaMemcpy(hw.data(), w, sizeof(float) * n, k);
-    if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions copy");
-  }
-  const int dims[3] = {g.nx, g.ny, g.nz};
-  for (int64_t i = 0; i < n; ++i) {
-    if (hc[i] < 0 || hc[i] >= g.ncell) return fail(HV_EINVAL, "cell index out of range");
-    hc[i] = linear_to_voxel(g, hc[i]);
-    for (int a = 0; a < 3; ++a) {
-      float &o = ho[a * n + i];
-      if (dims[a] == 1 || (a == 1 && g.dim2)) {
-        o = 0.f;  // single-cell axis: coordinate is irrelevant
-      } else if (!(o >= -1.f && o < 1.f)) {
-        return fail(HV_EINVAL, "relative coordinate outside [-1, 1) or non-finite");
-      }
-      if (!std::isfinite(hv_[a * n + i])) return fail(HV_EINVAL, "non-finite velocity");
-    }
-    if (!std::isfinite(hw[i])) return fail(HV_EINVAL, "non-finite weight");
-  }
   Species &sp = c->sp[species];
   sp.q = q;
   sp.m = m;
@@ -419,11 +420,13 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
   if (sp.cap == 0) sp.cap = 4;
   const size_t arr = align256(sizeof(float) * sp.cap);
   const int narr = g.dim2 ? 7 : 8;
-  std::vector<float> zeros;
   for (int b = 0; b < 2; ++b) {
     sp.bytes[b] = arr * narr;
     sp.base[b] = dev_alloc(sp.bytes[b], c->stream);
-    if (!sp.base[b]) return fail(HV_ENOMEM, "particle allocation failed");
+    if (!sp.base[b]) {
+      if (b == 1) dev_free(sp.base[0], sp.bytes[0], c->stream);
+      return fail(HV_ENOMEM, "particle allocation failed");
+    }
     cudaMemsetAsync(sp.base[b], 0, sp.bytes[b], c->stream);
     char *p = (char *)sp.base[b];
     Soa &s = sp.buf[b];
@@ -438,30 +441,50 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
     s.w = (float *)(p + arr * slot++);
   }
   sp.tile_off = (int *)dev_alloc(sizeof(int) * (g.ntiles + 1), c->stream);
-  if (!sp.tile_off) return fail(HV_ENOMEM, "tile range allocation failed");
-  c->nspecies++;
-  sp.cur = 0;
-  {
-    cudaError_t e = tile_ranges_even(c, species);
-    if (e != cudaSuccess) return cuda_fail(e, "tile ranges");
+  if (!sp.tile_off) {
+    for (int b = 0; b < 2; ++b) dev_free(sp.base[b], sp.bytes[b], c->stream);
+    return fail(HV_ENOMEM, "tile range allocation failed");
   }
+  sp.cur = 0;
+  // copy straight from the caller's arrays, then check and convert on the
+  // device (interior cell -> voxel, single-cell-axis offsets -> 0)
+  cudaError_t e = cudaSuccess;
   if (n > 0) {
     Soa &s = sp.buf[0];
-    cudaError_t e = cudaMemcpyAsync(s.cell, hc.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.ox, ho.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && s.oy)
-      e = cudaMemcpyAsync(s.oy, ho.data() + n, 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.oz, ho.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.vx, hv_.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.vy, hv_.data() + n, 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.vz, hv_.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.w, hw.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions upload");
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t b4 = 4 * (size_t)n;
+    e = cudaMemcpyAsync(s.cell, cell, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.ox, off3, b4, k, c->stream);
+    if (e == cudaSuccess && s.oy) e = cudaMemcpyAsync(s.oy, off3 + n, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.oz, off3 + 2 * n, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.vx, v3, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.vy, v3 + n, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.vz, v3 + 2 * n, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.w, w, b4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) {
+      const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+      load_check_kernel<<<blocks, 256, 0, c->stream>>>(g, s, n, c->err);
+      e = cudaGetLastError();
+    }
   }
+  int bad = 0;
+  if (e == cudaSuccess && n > 0)
+    e = cudaMemcpyAsync(&bad, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess || bad) {
+    for (int b = 0; b < 2; ++b) dev_free(sp.base[b], sp.bytes[b], c->stream);
+    dev_free(sp.tile_off, sizeof(int) * (g.ntiles + 1), c->stream);
+    memset(&sp, 0, sizeof(sp));
+    if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions upload");
+    if (bad & 1) return fail(HV_EINVAL, "cell index out of range");
+    if (bad & 2) return fail(HV_EINVAL, "relative coordinate outside [-1, 1) or non-finite");
+    return fail(HV_EINVAL, "non-finite velocity or weight");
+  }
+  c->nspecies++;
+  e = tile_ranges_even(c, species);
+  if (e != cudaSuccess) return cuda_fail(e, "tile ranges");
   return HV_OK;
 }
 
