@@ -7,14 +7,16 @@
 // ghost-padded grid (two ghost layers), so no index decode or wrap is needed
 // on the hot path: the half-step cell is the voxel plus the cell shift, the
 // deposit stencil may reach into the ghost layers (folded back afterwards),
-// and the new cell after the move is looked up in a wrap table.  One thread
-// owns 4 consecutive ions and moves them with 128-bit streaming loads and
-// stores.  Fields are gathered from {Ex,Ey,Ez,Bx},{By,Bz,-,-} per voxel.
+// and the new cell after the move is wrapped into the interior.  Ions move
+// between global memory and per-warp shared staging buffers with bulk
+// copies.  Fields are gathered from {Ex,Ey,Ez,Bx},{By,Bz,-,-} per voxel.
 //
 // Deposits are aggregated in registers before they reach global memory: a
-// lane owns 16 consecutive ions (sorted by cell) and sums their deposits
-// per run of equal deposit key, flushing a run with vector reductions.  For
-// QS in the x-z layout the accumulated quantities are
+// lane takes kChunk consecutive ions and sums their deposits per run of
+// equal deposit key, flushing a run with vector reductions.  In the x-z
+// layout each warp first counting-sorts its staging tile by cell in shared
+// memory, so the runs stay long however far the ions have drifted since the
+// last global sort.  For QS in the x-z layout the accumulated quantities are
 // the per-cell moment sums s*(1, dx, dx^2, dz, dz^2) of Eq. 17's weights, so
 // every ion of a cell contributes to one 80-byte record; the fold kernel
 // applies the stencil.  For CIC, NGP and 3D QS the per-target contributions
@@ -277,26 +279,47 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-// Shared-memory layout of one push block (one supercell tile).
-//   stage: one kTile-ion staging buffer per warp (bulk-copied in and out)
-//   eb:    E, B of the tile and a halo of RE cells, 2 float4 per cell
-template <int DIM, int SHAPE>
-struct Layout {
-  using S = Shape<DIM, SHAPE>;
-  static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
+// Supercell window: the tile and a halo of RE cells.  Ions that drifted up
+// to H cells out of their tile since the last sort still gather from the
+// window in shared memory.
+template <int DIM>
+struct Win {
   static constexpr int TX = DIM == 2 ? kTile2X : kTile3;
   static constexpr int TY = DIM == 2 ? 1 : kTile3;
   static constexpr int TZ = DIM == 2 ? kTile2Z : kTile3;
-  // ions that drifted up to H cells out of their tile since the last sort
-  // still gather from and deposit into shared memory
   static constexpr int H = DIM == 2 ? 2 : 1;
   static constexpr int RE = H + 1;
   static constexpr int EX = TX + 2 * RE, EY = DIM == 2 ? 1 : TY + 2 * RE, EZ = TZ + 2 * RE;
   static constexpr int NEB = EX * EY * EZ;
+};
+
+// In the x-z layout every staging tile is counting-sorted by cell (the
+// window cells, plus one bin for every other cell) before it is processed,
+// so that a lane's consecutive ions share a deposit cell however far the
+// ions have drifted from the order of the last global sort.
+constexpr int kBins = 512;
+static_assert(Win<2>::NEB < kBins, "window cells + overflow bin must fit the bins");
+static_assert((kChunk & (kChunk - 1)) == 0 && kChunk <= 32, "chunk must be a power of two");
+
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory layout of one push block (one supercell tile).
+//   stage: one kTile-ion staging buffer per warp (bulk-copied in and out)
+//   hist, perm: per-warp bins and processing order (sorted layout only)
+//   eb:    E, B of the window, 2 float4 per cell
+template <int DIM, int SHAPE>
+struct Layout {
+  static constexpr bool SORT = DIM == 2;
+  static constexpr int NW = kThreads / 32;
+  static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
   static constexpr size_t stage_bytes = (size_t)NA * kTile * 4;
-  static constexpr size_t off_eb = stage_bytes * (kThreads / 32);
-  static constexpr size_t off_bar = off_eb + (size_t)NEB * 32;
-  static constexpr size_t bytes = off_bar + 8 * (kThreads / 32);
+  static constexpr size_t hist_bytes = SORT ? kBins * 4 : 0;
+  static constexpr size_t perm_bytes = SORT ? align_up(kTile * 2, 16) : 0;
+  static constexpr size_t off_hist = stage_bytes * NW;
+  static constexpr size_t off_perm = off_hist + hist_bytes * NW;
+  static constexpr size_t off_eb = align_up(off_perm + perm_bytes * NW, 16);
+  static constexpr size_t off_bar = off_eb + (size_t)Win<DIM>::NEB * 32;
+  static constexpr size_t bytes = off_bar + 8 * NW;
 };
 
 // Array slot of each particle field in a staging buffer.
@@ -331,6 +354,200 @@ __device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, in
   }
 }
 
+// Sort bin of a voxel in the x-z layout: its window cell, or the last bin.
+__device__ __forceinline__ int sort_bin(const Geom &g, int vox, int i0, int k0) {
+  using W = Win<2>;
+  if (vox < g.vlo || vox >= g.vhi) return kBins - 1;
+  int ip, jp, kp;
+  voxel_coords(g, vox, ip, jp, kp);
+  const int rx = ip - kGhost - i0 + W::RE, rz = kp - kGhost - k0 + W::RE;
+  return ((unsigned)rx < (unsigned)W::EX && (unsigned)rz < (unsigned)W::EZ) ? rx + rz * W::EX
+                                                                          : kBins - 1;
+}
+
+// One ion of the step: gather E^n, B^n at x^n, Boris push, move to x^{n+1}
+// (MODE 0; the state is updated in place and the kinetic-energy/momentum
+// terms are added to rk), then the deposit values at the half-step
+// position.  Returns the voxel of the deposit key, or INT_MIN for a corrupt
+// cell index (latched in the error word; the ion is left as it is).
+template <int DIM, int SHAPE, int MODE>
+__device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int i0, int j0,
+                                        int k0, int &vox, float &ox, float &oy, float &oz,
+                                        float &vx, float &vy, float &vz, float w, float *cv,
+                                        float *rk) {
+  using W = Win<DIM>;
+  constexpr int NT = Shape<DIM, SHAPE>::NT;
+  const Geom &g = a.g;
+  const int vox0 = vox;
+  if (vox0 < g.vlo || vox0 >= g.vhi) {
+    atomicOr(a.err, kErrIndex);
+    return INT_MIN;
+  }
+  // cell relative to the tile; in the window if within H of the tile
+  int ip, jp, kp;
+  voxel_coords(g, vox0, ip, jp, kp);
+  const int rx = ip - kGhost - i0, rz = kp - kGhost - k0;
+  const int ry = DIM == 2 ? 0 : jp - kGhost - j0;
+  const bool inwin = rx >= -W::H && rx < W::TX + W::H && rz >= -W::H && rz < W::TZ + W::H &&
+                     (DIM == 2 || (ry >= -W::H && ry < W::TY + W::H));
+  const int eslot = (rx + W::RE) + (DIM == 2 ? 0 : (ry + W::RE) * W::EX) +
+                    (rz + W::RE) * W::EX * W::EY;
+  const float dy0 = DIM == 3 ? oy : 0.f;
+  float vxp = vx, vyp = vy, vzp = vz;
+  float hx = ox, hy = dy0, hz = oz;
+  int shx = 0, shy = 0, shz = 0;
+
+  if (MODE == 0) {
+    // gather E^n, B^n at x^n with the deposit's weights (App. B)
+    float wt[NT];
+    const int ks_ = shape_weights<DIM, SHAPE>(ox, dy0, oz, g, wt);
+    float ex = 0.f, ey = 0.f, ez = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    if (inwin) {
+      // window offset of the stencil base (CIC may start one cell lower)
+      int eb0 = eslot;
+      if (SHAPE == 2) {
+        eb0 += (ox < 0.f ? -1 : 0) + (oz < 0.f ? -W::EX * W::EY : 0);
+        if (DIM == 3) eb0 += dy0 < 0.f ? -W::EX : 0;
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        int wo;
+        if (SHAPE == 0) wo = 0;
+        else if (SHAPE == 1)
+          wo = DIM == 2 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? W::EX : -W::EX)
+                        : (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? W::EX
+                           : t == 4 ? -W::EX : t == 5 ? W::EX * W::EY : -W::EX * W::EY);
+        else
+          wo = DIM == 2 ? (t & 1) + ((t >> 1) & 1) * W::EX
+                        : (t & 1) + ((t >> 1) & 1) * W::EX + ((t >> 2) & 1) * W::EX * W::EY;
+        const float4 f0 = eb[2 * (eb0 + wo)];
+        const float4 f1 = eb[2 * (eb0 + wo) + 1];
+        ex = fmaf(wt[t], f0.x, ex);
+        ey = fmaf(wt[t], f0.y, ey);
+        ez = fmaf(wt[t], f0.z, ez);
+        bx = fmaf(wt[t], f0.w, bx);
+        by = fmaf(wt[t], f1.x, by);
+        bz = fmaf(wt[t], f1.y, bz);
+      }
+    } else {
+      const int pc = vox0 + ks_;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int pt = pc + target_off<DIM, SHAPE>(t, g);
+        const float4 f0 = __ldg(a.EB + 2 * pt);
+        const float4 f1 = __ldg(a.EB + 2 * pt + 1);
+        ex = fmaf(wt[t], f0.x, ex);
+        ey = fmaf(wt[t], f0.y, ey);
+        ez = fmaf(wt[t], f0.z, ez);
+        bx = fmaf(wt[t], f0.w, bx);
+        by = fmaf(wt[t], f1.x, by);
+        bz = fmaf(wt[t], f1.y, bz);
+      }
+    }
+    // Boris: half E kick, rotation, half E kick (Eq. 9)
+    const float h = a.k.qmdt2;
+    const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
+    const float tx = h * bx, ty = h * by, tz = h * bz;
+    const float f = 2.f / (1.f + (tx * tx + ty * ty + tz * tz));
+    const float sx = f * tx, sy = f * ty, sz = f * tz;
+    const float vpx = vmx + (vmy * tz - vmz * ty);
+    const float vpy = vmy + (vmz * tx - vmx * tz);
+    const float vpz = vmz + (vmx * ty - vmy * tx);
+    vxp = vmx + (vpy * sz - vpz * sy) + h * ex;
+    vyp = vmy + (vpz * sx - vpx * sz) + h * ey;
+    vzp = vmz + (vpx * sy - vpy * sx) + h * ez;
+
+    // half-step and full-step positions (Eq. 10; App. B); the
+    // displacement coefficients are 0 along single-cell axes
+    hx = ox + vxp * a.k.cx;
+    hz = oz + vzp * a.k.cz;
+    float nxo = ox + vxp * (2.f * a.k.cx);
+    float nzo = oz + vzp * (2.f * a.k.cz);
+    float nyo = dy0;
+    bool ok = fabsf(nxo) < 3.f && fabsf(nzo) < 3.f;
+    if (DIM == 3) {
+      hy = dy0 + vyp * a.k.cy;
+      nyo = dy0 + vyp * (2.f * a.k.cy);
+      ok = ok && fabsf(nyo) < 3.f;
+    }
+    if (!ok) {
+      // more than one cell in a step, or non-finite: latch and freeze
+      atomicOr(a.err, isfinite(vxp + vyp + vzp) ? kErrCfl : kErrNonFinite);
+      hx = nxo = ox;
+      hy = nyo = dy0;
+      hz = nzo = oz;
+      vxp = vx;
+      vyp = vy;
+      vzp = vz;
+    }
+    shx = rebase(hx);
+    shz = rebase(hz);
+    const int mx = rebase(nxo), mz = rebase(nzo);
+    int my = 0;
+    if (DIM == 3) {
+      shy = rebase(hy);
+      my = rebase(nyo);
+    }
+    // new cell, wrapped into the interior
+    const int i1 = ip - kGhost + mx, k1 = kp - kGhost + mz;
+    const int j1 = DIM == 2 ? 0 : jp - kGhost + my;
+    const int iw = i1 < 0 ? i1 + g.nx : (i1 >= g.nx ? i1 - g.nx : i1);
+    const int kw = k1 < 0 ? k1 + g.nz : (k1 >= g.nz ? k1 - g.nz : k1);
+    const int jw = DIM == 2 ? 0 : (j1 < 0 ? j1 + g.ny : (j1 >= g.ny ? j1 - g.ny : j1));
+    vox = voxel_of(g, iw, jw, kw);
+    ox = nxo;
+    if (DIM == 3) oy = nyo;
+    oz = nzo;
+    vx = vxp;
+    vy = vyp;
+    vz = vzp;
+    const float mw = a.k.mass * w;
+    rk[0] += 0.5f * mw * (vxp * vxp + vyp * vyp + vzp * vzp);
+    rk[1] += mw * vxp;
+    rk[2] += mw * vyp;
+    rk[3] += mw * vzp;
+  }
+
+  // deposit q w S / V_c and q w v S / V_c at the half-step position
+  const int kshift = deposit_values<DIM, SHAPE>(hx, hy, hz, a.k.qvc * w, vxp, vyp, vzp, g, cv);
+  return vox0 + shx + shz * g.sz + (DIM == 3 ? shy * g.sy : 0) + kshift;
+}
+
+// A lane's register run: the deposit values summed over consecutive ions
+// with the same deposit key.  For QS and NGP (keys are cells) an ion that
+// left the run's cell is flushed on its own while the run continues; a new
+// run starts only with an ion whose key is its own cell.
+template <int DIM, int SHAPE>
+struct Run {
+  static constexpr int NV = Shape<DIM, SHAPE>::NV;
+  static constexpr bool CELLKEY = SHAPE != 2;
+  int key;
+  float acc[NV];
+
+  __device__ __forceinline__ void reset() {
+    key = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.f;
+  }
+  __device__ __forceinline__ void add(const PushArgs &a, int pk, int own, const float *cv) {
+    if (pk == key) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) acc[j] += cv[j];
+    } else if (!CELLKEY || pk == own || key == INT_MIN) {
+      if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
+      key = pk;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) acc[j] = cv[j];
+    } else {
+      flush_direct<DIM, SHAPE>(a, pk, cv);
+    }
+  }
+  __device__ __forceinline__ void finish(const PushArgs &a) {
+    if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
+    key = INT_MIN;
+  }
+};
+
 // MODE 0: full step.  MODE 1: start-up deposit at the current position with
 // the stored velocity (no push, no move, no write-back).
 //
@@ -339,43 +556,45 @@ __device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, in
 // lies in the tile, give or take the drift since the last sort.  The block
 // stages E and B of the tile and a halo in shared memory; ions that drifted
 // further gather from global memory.  Each warp streams tiles of kTile ions
-// through shared memory with bulk copies; each lane owns kChunk consecutive
-// ions and sums their deposits in registers per run of equal deposit key,
-// flushing a run with vector reductions into the global accumulator.
+// through shared memory with bulk copies.  In the x-z layout the warp
+// counting-sorts each staging tile by cell and each lane takes kChunk
+// consecutive ions of that order; in 3D each lane takes kChunk consecutive
+// ions of the memory order.  A lane sums the deposits of its ions in
+// registers per run of equal deposit key, flushing a run with vector
+// reductions into the global accumulator.
 template <int DIM, int SHAPE, int MODE>
 __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(PushArgs a) {
-  using S = Shape<DIM, SHAPE>;
   using L = Layout<DIM, SHAPE>;
+  using W = Win<DIM>;
   using SL = Slot<DIM>;
-  constexpr int NT = S::NT;
-  constexpr int NV = S::NV;
+  constexpr int NV = Shape<DIM, SHAPE>::NV;
   constexpr int NA = L::NA;
   constexpr int CQ = kChunk / 4;  // quads per lane per staging tile
   constexpr int TQ = kTile / 4;   // quads per staging tile
-  constexpr bool CELLKEY = SHAPE != 2;  // runs keyed by cell (QS, NGP)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom &g = a.g;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int nwarps = kThreads / 32;
   float(&T)[NA][kTile] = *reinterpret_cast<float(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
+  int(&TC)[NA][kTile] = *reinterpret_cast<int(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
   float4 *eb = reinterpret_cast<float4 *>(smem_raw + L::off_eb);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L::off_bar) + warp;
 
   // tile origin and the block's range of quads
   const int tile = blockIdx.x;
   const int ti = tile % g.ntx, tj = (tile / g.ntx) % g.nty, tk = tile / (g.ntx * g.nty);
-  const int i0 = ti * L::TX, j0 = tj * L::TY, k0 = tk * L::TZ;
+  const int i0 = ti * W::TX, j0 = tj * W::TY, k0 = tk * W::TZ;
   const int64_t nq = (a.n + 3) >> 2;
   const int64_t qa = tile == 0 ? 0 : (int64_t)a.tile_off[tile] >> 2;
   const int64_t qe = tile == g.ntiles - 1 ? nq : (int64_t)a.tile_off[tile + 1] >> 2;
 
-  // stage E, B of the tile + halo
+  // stage E, B of the window
   if (MODE == 0) {
-    for (int c = threadIdx.x; c < L::NEB; c += kThreads) {
-      const int wx = c % L::EX, wy = (c / L::EX) % L::EY, wz = c / (L::EX * L::EY);
-      const int ip = i0 + wx - L::RE + kGhost, kp = k0 + wz - L::RE + kGhost;
-      const int jp = DIM == 2 ? 0 : j0 + wy - L::RE + kGhost;
+    for (int c = threadIdx.x; c < W::NEB; c += kThreads) {
+      const int wx = c % W::EX, wy = (c / W::EX) % W::EY, wz = c / (W::EX * W::EY);
+      const int ip = i0 + wx - W::RE + kGhost, kp = k0 + wz - W::RE + kGhost;
+      const int jp = DIM == 2 ? 0 : j0 + wy - W::RE + kGhost;
       if (ip < 0 || ip >= g.px || kp < 0 || kp >= g.pz || (DIM == 3 && (jp < 0 || jp >= g.py)))
         continue;  // outside the padded grid: never read by an in-window ion
       const int v = ip + (DIM == 2 ? 0 : jp * g.sy) + kp * g.sz;
@@ -413,205 +632,153 @@ __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(Push
       break;
     }
 
-    float accv[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) accv[j] = 0.f;
-    int key = INT_MIN;
+    Run<DIM, SHAPE> run;
+    run.reset();
+    float rk[4] = {0.f, 0.f, 0.f, 0.f};
 
-    // lanes start their chunk at a rotated quad so that the 128-bit shared
-    // loads of a quarter-warp hit distinct banks
-    const int rot = CQ > 1 ? (lane / (32 / kChunk)) % CQ : 0;
-#pragma unroll 1
-    for (int jj = 0; jj < CQ; ++jj) {
-      const int jq = (jj + rot) % CQ;
-      const int lq = lane * CQ + jq;  // quad within the staging tile
-      if (lq >= nqt) continue;
-      const int e0 = lq * 4;
-      const int4 c4 = *reinterpret_cast<const int4 *>(&T[SL::CELL][e0]);
-      int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-      const float4 X = *reinterpret_cast<const float4 *>(&T[SL::OX][e0]);
-      const float4 Z = *reinterpret_cast<const float4 *>(&T[SL::OZ][e0]);
-      float4 Y = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (DIM == 3) Y = *reinterpret_cast<const float4 *>(&T[SL::OY][e0]);
-      const float4 VX = *reinterpret_cast<const float4 *>(&T[SL::VX][e0]);
-      const float4 VY = *reinterpret_cast<const float4 *>(&T[SL::VY][e0]);
-      const float4 VZ = *reinterpret_cast<const float4 *>(&T[SL::VZ][e0]);
-      const float4 W = *reinterpret_cast<const float4 *>(&T[SL::W][e0]);
-      float ox[4] = {X.x, X.y, X.z, X.w}, oy[4] = {Y.x, Y.y, Y.z, Y.w},
-            oz[4] = {Z.x, Z.y, Z.z, Z.w};
-      float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w},
-            vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
-      const float ww[4] = {W.x, W.y, W.z, W.w};
-      float rk[4] = {0.f, 0.f, 0.f, 0.f};
-      const int64_t ion0 = (q0 + lq) * 4;
-
+    if constexpr (L::SORT) {
+      int *hist = reinterpret_cast<int *>(smem_raw + L::off_hist + L::hist_bytes * warp);
+      uint16_t *perm = reinterpret_cast<uint16_t *>(smem_raw + L::off_perm + L::perm_bytes * warp);
+      const int nion = (int)min((int64_t)nqt * 4, a.n - q0 * 4);
+      // lanes start their chunk at a rotated ion so that a warp's shared
+      // loads of one field hit distinct banks
+      const int rot = lane / (32 / kChunk);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        if (ion0 + p >= a.n) continue;
-        const int vox = cc[p];
-        if (vox < g.vlo || vox >= g.vhi) {
-          atomicOr(a.err, kErrIndex);
-          continue;
-        }
-        // cell relative to the tile; in the window if within H of the tile
-        int ip, jp, kp;
-        voxel_coords(g, vox, ip, jp, kp);
-        const int rx = ip - kGhost - i0, rz = kp - kGhost - k0;
-        const int ry = DIM == 2 ? 0 : jp - kGhost - j0;
-        const bool inwin = rx >= -L::H && rx < L::TX + L::H && rz >= -L::H &&
-                           rz < L::TZ + L::H && (DIM == 2 || (ry >= -L::H && ry < L::TY + L::H));
-        const int eslot = (rx + L::RE) + (DIM == 2 ? 0 : (ry + L::RE) * L::EX) +
-                          (rz + L::RE) * L::EX * L::EY;
-        const float dy0 = DIM == 3 ? oy[p] : 0.f;
-        float vxp = vx[p], vyp = vy[p], vzp = vz[p];
-        float hx = ox[p], hy = dy0, hz = oz[p];
-        int shx = 0, shy = 0, shz = 0;
-
-        if (MODE == 0) {
-          // gather E^n, B^n at x^n with the deposit's weights (App. B)
-          float wt[NT];
-          const int ks_ = shape_weights<DIM, SHAPE>(ox[p], dy0, oz[p], g, wt);
-          float ex = 0.f, ey = 0.f, ez = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-          if (inwin) {
-            // window offset of the stencil base (CIC may start one cell lower)
-            int eb0 = eslot;
-            if (SHAPE == 2) {
-              eb0 += (ox[p] < 0.f ? -1 : 0) + (oz[p] < 0.f ? -L::EX * L::EY : 0);
-              if (DIM == 3) eb0 += dy0 < 0.f ? -L::EX : 0;
-            }
+      for (int b = lane * 4; b < kBins; b += 128)
+        *reinterpret_cast<int4 *>(hist + b) = make_int4(0, 0, 0, 0);
+      __syncwarp();
+      // bin of every ion and its rank in the bin
+      uint32_t br[kChunk];
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-              int wo;
-              if (SHAPE == 0) wo = 0;
-              else if (SHAPE == 1)
-                wo = DIM == 2 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? L::EX : -L::EX)
-                              : (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? -1 : t == 3 ? L::EX
-                                 : t == 4 ? -L::EX : t == 5 ? L::EX * L::EY : -L::EX * L::EY);
-              else
-                wo = DIM == 2 ? (t & 1) + ((t >> 1) & 1) * L::EX
-                              : (t & 1) + ((t >> 1) & 1) * L::EX + ((t >> 2) & 1) * L::EX * L::EY;
-              const float4 f0 = eb[2 * (eb0 + wo)];
-              const float4 f1 = eb[2 * (eb0 + wo) + 1];
-              ex = fmaf(wt[t], f0.x, ex);
-              ey = fmaf(wt[t], f0.y, ey);
-              ez = fmaf(wt[t], f0.z, ez);
-              bx = fmaf(wt[t], f0.w, bx);
-              by = fmaf(wt[t], f1.x, by);
-              bz = fmaf(wt[t], f1.y, bz);
-            }
-          } else {
-            const int pc = vox + ks_;
-#pragma unroll
-            for (int t = 0; t < NT; ++t) {
-              const int pt = pc + target_off<DIM, SHAPE>(t, g);
-              const float4 f0 = __ldg(a.EB + 2 * pt);
-              const float4 f1 = __ldg(a.EB + 2 * pt + 1);
-              ex = fmaf(wt[t], f0.x, ex);
-              ey = fmaf(wt[t], f0.y, ey);
-              ez = fmaf(wt[t], f0.z, ez);
-              bx = fmaf(wt[t], f0.w, bx);
-              by = fmaf(wt[t], f1.x, by);
-              bz = fmaf(wt[t], f1.y, bz);
-            }
-          }
-          // Boris: half E kick, rotation, half E kick (Eq. 9)
-          const float h = a.k.qmdt2;
-          const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
-          const float tx = h * bx, ty = h * by, tz = h * bz;
-          const float f = 2.f / (1.f + (tx * tx + ty * ty + tz * tz));
-          const float sx = f * tx, sy = f * ty, sz = f * tz;
-          const float vpx = vmx + (vmy * tz - vmz * ty);
-          const float vpy = vmy + (vmz * tx - vmx * tz);
-          const float vpz = vmz + (vmx * ty - vmy * tx);
-          vxp = vmx + (vpy * sz - vpz * sy) + h * ex;
-          vyp = vmy + (vpz * sx - vpx * sz) + h * ey;
-          vzp = vmz + (vpx * sy - vpy * sx) + h * ez;
-
-          // half-step and full-step positions (Eq. 10; App. B); the
-          // displacement coefficients are 0 along single-cell axes
-          hx = ox[p] + vxp * a.k.cx;
-          hz = oz[p] + vzp * a.k.cz;
-          float nxo = ox[p] + vxp * (2.f * a.k.cx);
-          float nzo = oz[p] + vzp * (2.f * a.k.cz);
-          float nyo = dy0;
-          bool ok = fabsf(nxo) < 3.f && fabsf(nzo) < 3.f;
-          if (DIM == 3) {
-            hy = dy0 + vyp * a.k.cy;
-            nyo = dy0 + vyp * (2.f * a.k.cy);
-            ok = ok && fabsf(nyo) < 3.f;
-          }
-          if (!ok) {
-            // more than one cell in a step, or non-finite: latch and freeze
-            atomicOr(a.err, isfinite(vxp + vyp + vzp) ? kErrCfl : kErrNonFinite);
-            hx = nxo = ox[p];
-            hy = nyo = dy0;
-            hz = nzo = oz[p];
-            vxp = vx[p];
-            vyp = vy[p];
-            vzp = vz[p];
-          }
-          shx = rebase(hx);
-          shz = rebase(hz);
-          const int mx = rebase(nxo), mz = rebase(nzo);
-          int my = 0;
-          if (DIM == 3) {
-            shy = rebase(hy);
-            my = rebase(nyo);
-          }
-          // new cell, wrapped into the interior
-          const int i1 = ip - kGhost + mx, k1 = kp - kGhost + mz;
-          const int j1 = DIM == 2 ? 0 : jp - kGhost + my;
-          const int iw = i1 < 0 ? i1 + g.nx : (i1 >= g.nx ? i1 - g.nx : i1);
-          const int kw = k1 < 0 ? k1 + g.nz : (k1 >= g.nz ? k1 - g.nz : k1);
-          const int jw = DIM == 2 ? 0 : (j1 < 0 ? j1 + g.ny : (j1 >= g.ny ? j1 - g.ny : j1));
-          cc[p] = voxel_of(g, iw, jw, kw);
-          ox[p] = nxo;
-          if (DIM == 3) oy[p] = nyo;
-          oz[p] = nzo;
-          vx[p] = vxp;
-          vy[p] = vyp;
-          vz[p] = vzp;
-          const float mw = a.k.mass * ww[p];
-          rk[0] += 0.5f * mw * (vxp * vxp + vyp * vyp + vzp * vzp);
-          rk[1] += mw * vxp;
-          rk[2] += mw * vyp;
-          rk[3] += mw * vzp;
-        }
-
-        // deposit q w S / V_c and q w v S / V_c at the half-step position
-        float cv[NV];
-        const int kshift = deposit_values<DIM, SHAPE>(hx, hy, hz, a.k.qvc * ww[p], vxp, vyp,
-                                                      vzp, g, cv);
-        const int pk = vox + shx + shz * g.sz + (DIM == 3 ? shy * g.sy : 0) + kshift;
-        const int own = vox;
-        if (pk == key) {
-#pragma unroll
-          for (int jv = 0; jv < NV; ++jv) accv[jv] += cv[jv];
-        } else if (!CELLKEY || pk == own || key == INT_MIN) {
-          // a new run: flush the current one and start from this ion
-          if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, accv);
-          key = pk;
-#pragma unroll
-          for (int jv = 0; jv < NV; ++jv) accv[jv] = cv[jv];
-        } else {
-          flush_direct<DIM, SHAPE>(a, pk, cv);  // crossed into another cell
+      for (int j = 0; j < kChunk; ++j) {
+        const int e = lane * kChunk + ((j + rot) & (kChunk - 1));
+        br[j] = 0xffffffffu;
+        if (e < nion) {
+          const int bin = sort_bin(g, TC[SL::CELL][e], i0, k0);
+          const int r = atomicAdd(hist + bin, 1);
+          br[j] = ((uint32_t)bin << 16) | (uint32_t)r;
         }
       }
-
-      if (MODE == 0) {
-        *reinterpret_cast<int4 *>(&T[SL::CELL][e0]) = make_int4(cc[0], cc[1], cc[2], cc[3]);
-        *reinterpret_cast<float4 *>(&T[SL::OX][e0]) = make_float4(ox[0], ox[1], ox[2], ox[3]);
-        if (DIM == 3)
-          *reinterpret_cast<float4 *>(&T[SL::OY][e0]) = make_float4(oy[0], oy[1], oy[2], oy[3]);
-        *reinterpret_cast<float4 *>(&T[SL::OZ][e0]) = make_float4(oz[0], oz[1], oz[2], oz[3]);
-        *reinterpret_cast<float4 *>(&T[SL::VX][e0]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-        *reinterpret_cast<float4 *>(&T[SL::VY][e0]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
-        *reinterpret_cast<float4 *>(&T[SL::VZ][e0]) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+      __syncwarp();
+      // exclusive scan of the bins: each lane owns kBins / 32 consecutive bins
+      {
+        constexpr int PB = kBins / 32;
+        int v[PB];
+        int4 *h4 = reinterpret_cast<int4 *>(hist + lane * PB);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) kahan_add(ks[m], kc[m], rk[m]);
+        for (int q = 0; q < PB / 4; ++q) {
+          const int4 x = h4[q];
+          v[4 * q] = x.x;
+          v[4 * q + 1] = x.y;
+          v[4 * q + 2] = x.z;
+          v[4 * q + 3] = x.w;
+        }
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+          const int t = v[q];
+          v[q] = tot;
+          tot += t;
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int base = incl - tot;
+#pragma unroll
+        for (int q = 0; q < PB / 4; ++q)
+          h4[q] = make_int4(v[4 * q] + base, v[4 * q + 1] + base, v[4 * q + 2] + base,
+                            v[4 * q + 3] + base);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        if (br[j] == 0xffffffffu) continue;
+        const int e = lane * kChunk + ((j + rot) & (kChunk - 1));
+        perm[hist[br[j] >> 16] + (int)(br[j] & 0xffffu)] = (uint16_t)e;
+      }
+      __syncwarp();
+
+      // the lane's kChunk consecutive positions of the sorted order
+#pragma unroll 1
+      for (int j = 0; j < kChunk; ++j) {
+        const int pos = lane * kChunk + ((j + rot) & (kChunk - 1));
+        if (pos >= nion) continue;
+        const int e = perm[pos];
+        int vox = TC[SL::CELL][e];
+        float ox = T[SL::OX][e], oy = 0.f, oz = T[SL::OZ][e];
+        float vx = T[SL::VX][e], vy = T[SL::VY][e], vz = T[SL::VZ][e];
+        const float w = T[SL::W][e];
+        const int own = vox;
+        float cv[NV];
+        const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, vox, ox, oy, oz, vx, vy,
+                                                  vz, w, cv, rk);
+        if (pk == INT_MIN) continue;
+        if (MODE == 0) {
+          TC[SL::CELL][e] = vox;
+          T[SL::OX][e] = ox;
+          T[SL::OZ][e] = oz;
+          T[SL::VX][e] = vx;
+          T[SL::VY][e] = vy;
+          T[SL::VZ][e] = vz;
+        }
+        run.add(a, pk, own, cv);
+      }
+    } else {
+      // quads of the memory order; lanes start at a rotated quad so that the
+      // 128-bit shared loads of a quarter-warp hit distinct banks
+      const int rot = CQ > 1 ? (lane / (32 / kChunk)) % CQ : 0;
+#pragma unroll 1
+      for (int jj = 0; jj < CQ; ++jj) {
+        const int jq = (jj + rot) % CQ;
+        const int lq = lane * CQ + jq;  // quad within the staging tile
+        if (lq >= nqt) continue;
+        const int e0 = lq * 4;
+        const int4 c4 = *reinterpret_cast<const int4 *>(&TC[SL::CELL][e0]);
+        int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+        const float4 X = *reinterpret_cast<const float4 *>(&T[SL::OX][e0]);
+        const float4 Z = *reinterpret_cast<const float4 *>(&T[SL::OZ][e0]);
+        float4 Y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (DIM == 3) Y = *reinterpret_cast<const float4 *>(&T[SL::OY][e0]);
+        const float4 VX = *reinterpret_cast<const float4 *>(&T[SL::VX][e0]);
+        const float4 VY = *reinterpret_cast<const float4 *>(&T[SL::VY][e0]);
+        const float4 VZ = *reinterpret_cast<const float4 *>(&T[SL::VZ][e0]);
+        const float4 Wq = *reinterpret_cast<const float4 *>(&T[SL::W][e0]);
+        float ox[4] = {X.x, X.y, X.z, X.w}, oy[4] = {Y.x, Y.y, Y.z, Y.w},
+              oz[4] = {Z.x, Z.y, Z.z, Z.w};
+        float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w},
+              vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
+        const float ww[4] = {Wq.x, Wq.y, Wq.z, Wq.w};
+        const int64_t ion0 = (q0 + lq) * 4;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if (ion0 + p >= a.n) continue;
+          const int own = cc[p];
+          float cv[NV];
+          const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, cc[p], ox[p], oy[p],
+                                                    oz[p], vx[p], vy[p], vz[p], ww[p], cv, rk);
+          if (pk == INT_MIN) continue;
+          run.add(a, pk, own, cv);
+        }
+        if (MODE == 0) {
+          *reinterpret_cast<int4 *>(&TC[SL::CELL][e0]) = make_int4(cc[0], cc[1], cc[2], cc[3]);
+          *reinterpret_cast<float4 *>(&T[SL::OX][e0]) = make_float4(ox[0], ox[1], ox[2], ox[3]);
+          if (DIM == 3)
+            *reinterpret_cast<float4 *>(&T[SL::OY][e0]) = make_float4(oy[0], oy[1], oy[2], oy[3]);
+          *reinterpret_cast<float4 *>(&T[SL::OZ][e0]) = make_float4(oz[0], oz[1], oz[2], oz[3]);
+          *reinterpret_cast<float4 *>(&T[SL::VX][e0]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+          *reinterpret_cast<float4 *>(&T[SL::VY][e0]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+          *reinterpret_cast<float4 *>(&T[SL::VZ][e0]) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+        }
       }
     }
-    if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, accv);
+    run.finish(a);
+    if (MODE == 0) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) kahan_add(ks[m], kc[m], rk[m]);
+    }
 
     // make the staged results visible to the bulk copy and write back every
     // field but w
