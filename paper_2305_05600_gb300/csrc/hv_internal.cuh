@@ -176,6 +176,8 @@ struct hv_ctx {
   int started;
   // sort scratch (lazily sized to the largest species)
   hv::SortScratch *sort;
+  int32_t *bucket;      // step sort: key counts / cursors and scan sums
+  size_t bucket_bytes;
   // profiling
   int prof_on;
   hv_prof_t prof;

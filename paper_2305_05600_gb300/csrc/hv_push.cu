@@ -13,28 +13,30 @@
 //
 // Deposits are aggregated in registers before they reach global memory: a
 // lane takes kChunk consecutive ions and sums their deposits per run of
-// equal deposit key, flushing a run with vector reductions.  In the x-z
-// layout each warp first counting-sorts its staging tile by cell in shared
-// memory, so the runs stay long however far the ions have drifted since the
-// last global sort.  For QS in the x-z layout the accumulated quantities are
-// the per-cell moment sums s*(1, dx, dx^2, dz, dz^2) of Eq. 17's weights, so
-// every ion of a cell contributes to one 80-byte record; the fold kernel
-// applies the stencil.  For CIC, NGP and 3D QS the per-target contributions
-// are accumulated.
+// equal deposit key, flushing a run with vector reductions; the runs are
+// long because the ions are kept sorted by cell (hv_sort.cu).  For QS in the
+// x-z layout the accumulated quantities are the per-cell moment sums
+// s*(1, dx, dx^2, dz, dz^2) of Eq. 17's weights, so every ion of a cell
+// contributes to one 80-byte record; the fold kernel applies the stencil.
+// For CIC, NGP and 3D QS the per-target contributions are accumulated.
 #include <climits>
 
 #include "hv_internal.cuh"
 
 // Threads per block, resident blocks per SM the push kernel is compiled for
-// (register budget 65536 / (threads * blocks)), and ions per lane per tile.
+// (register budget 65536 / (threads * blocks)), ions per lane per staging
+// tile, and ions a lane loads with one vector access.
 #ifndef HV_PUSH_THREADS
-#define HV_PUSH_THREADS 256
+#define HV_PUSH_THREADS 128
 #endif
 #ifndef HV_PUSH_MIN_BLOCKS
-#define HV_PUSH_MIN_BLOCKS 2
+#define HV_PUSH_MIN_BLOCKS 5
 #endif
 #ifndef HV_PUSH_CHUNK
 #define HV_PUSH_CHUNK 8
+#endif
+#ifndef HV_PUSH_GROUP
+#define HV_PUSH_GROUP 2
 #endif
 
 namespace hv {
@@ -44,6 +46,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = HV_PUSH_THREADS;
 constexpr int kChunk = HV_PUSH_CHUNK;  // consecutive ions per lane per tile
 constexpr int kTile = 32 * kChunk;     // ions per warp tile
+constexpr int kGroup = HV_PUSH_GROUP;  // ions a lane moves with one vector access
 
 struct PushArgs {
   Soa s;
@@ -154,43 +157,41 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
-// Deposit values of one ion: QS x-z records (moment sums) or per-target
-// contributions, both NV floats.
+// Deposit of one ion in factored form: its NV values are the products
+// f[i] * sv[c] of the factors f and sv = s * (1, vx, vy, vz), s = q w / V_c.
+// QS x-z records: f = (1, dx, dx^2, dz, dz^2), value 5c + i (moment sums);
+// other shapes: f = the target weights, value 4i + c.  Returns the voxel
+// shift of the deposit key.
 template <int DIM, int SHAPE>
-__device__ __forceinline__ int deposit_values(float hx, float hy, float hz, float s, float vx,
-                                              float vy, float vz, const Geom &g, float *cv) {
-  using S = Shape<DIM, SHAPE>;
-  if (S::REC) {
-    const float sx = s * hx, sz = s * hz;
-    const float v3[3] = {vx, vy, vz};
-    cv[0] = s;
-    cv[1] = sx;
-    cv[2] = sx * hx;
-    cv[3] = sz;
-    cv[4] = sz * hz;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float ta = s * v3[a];
-      const float tx = ta * hx, tz = ta * hz;
-      cv[5 * a + 5] = ta;
-      cv[5 * a + 6] = tx;
-      cv[5 * a + 7] = tx * hx;
-      cv[5 * a + 8] = tz;
-      cv[5 * a + 9] = tz * hz;
-    }
+struct Dep {
+  static constexpr int NF = Shape<DIM, SHAPE>::REC ? 5 : Shape<DIM, SHAPE>::NT;
+  float f[NF];
+  float sv[4];
+  __device__ __forceinline__ float value(int j) const {
+    return Shape<DIM, SHAPE>::REC ? f[j % 5] * sv[j / 5] : f[j / 4] * sv[j % 4];
+  }
+  __device__ __forceinline__ float fma_into(int j, float acc) const {
+    return Shape<DIM, SHAPE>::REC ? fmaf(f[j % 5], sv[j / 5], acc) : fmaf(f[j / 4], sv[j % 4], acc);
+  }
+};
+
+template <int DIM, int SHAPE>
+__device__ __forceinline__ int deposit_factors(float hx, float hy, float hz, float s, float vx,
+                                               float vy, float vz, const Geom &g,
+                                               Dep<DIM, SHAPE> &d) {
+  d.sv[0] = s;
+  d.sv[1] = s * vx;
+  d.sv[2] = s * vy;
+  d.sv[3] = s * vz;
+  if (Shape<DIM, SHAPE>::REC) {
+    d.f[0] = 1.f;
+    d.f[1] = hx;
+    d.f[2] = hx * hx;
+    d.f[3] = hz;
+    d.f[4] = hz * hz;
     return 0;
   }
-  float wt[S::NT];
-  const int shift = shape_weights<DIM, SHAPE>(hx, hy, hz, g, wt);
-#pragma unroll
-  for (int t = 0; t < S::NT; ++t) {
-    const float st = wt[t] * s;
-    cv[4 * t + 0] = st;
-    cv[4 * t + 1] = st * vx;
-    cv[4 * t + 2] = st * vy;
-    cv[4 * t + 3] = st * vz;
-  }
-  return shift;
+  return shape_weights<DIM, SHAPE>(hx, hy, hz, g, d.f);
 }
 
 // Add a lane's NV deposit values at `key` with vector reductions.
@@ -293,31 +294,20 @@ struct Win {
   static constexpr int NEB = EX * EY * EZ;
 };
 
-// In the x-z layout every staging tile is counting-sorted by cell (the
-// window cells, plus one bin for every other cell) before it is processed,
-// so that a lane's consecutive ions share a deposit cell however far the
-// ions have drifted from the order of the last global sort.
-constexpr int kBins = 512;
-static_assert(Win<2>::NEB < kBins, "window cells + overflow bin must fit the bins");
-static_assert((kChunk & (kChunk - 1)) == 0 && kChunk <= 32, "chunk must be a power of two");
+static_assert(kChunk == 8 || kChunk == 16 || kChunk == 32, "chunk: 8, 16 or 32 ions per lane");
+static_assert(kGroup == 4 || kGroup == 2, "ion group: 4 or 2");
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Shared-memory layout of one push block (one supercell tile).
 //   stage: one kTile-ion staging buffer per warp (bulk-copied in and out)
-//   hist, perm: per-warp bins and processing order (sorted layout only)
 //   eb:    E, B of the window, 2 float4 per cell
 template <int DIM, int SHAPE>
 struct Layout {
-  static constexpr bool SORT = DIM == 2;
   static constexpr int NW = kThreads / 32;
   static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
   static constexpr size_t stage_bytes = (size_t)NA * kTile * 4;
-  static constexpr size_t hist_bytes = SORT ? kBins * 4 : 0;
-  static constexpr size_t perm_bytes = SORT ? align_up(kTile * 2, 16) : 0;
-  static constexpr size_t off_hist = stage_bytes * NW;
-  static constexpr size_t off_perm = off_hist + hist_bytes * NW;
-  static constexpr size_t off_eb = align_up(off_perm + perm_bytes * NW, 16);
+  static constexpr size_t off_eb = align_up(stage_bytes * NW, 16);
   static constexpr size_t off_bar = off_eb + (size_t)Win<DIM>::NEB * 32;
   static constexpr size_t bytes = off_bar + 8 * NW;
 };
@@ -329,16 +319,48 @@ struct Slot {
                        VX = OZ + 1, VY = OZ + 2, VZ = OZ + 3, W = OZ + 4;
 };
 
+// kGroup consecutive 32-bit values of a staging array (128- or 64-bit
+// shared accesses).
+template <int G, class E>
+__device__ __forceinline__ void ldv(const E *src, E *out) {
+  static_assert(sizeof(E) == 4 && (G == 4 || G == 2), "4 or 2 values of 32 bits");
+  if constexpr (G == 4) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(src);
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = __builtin_bit_cast(E, u[i]);
+  } else {
+    const uint2 v = *reinterpret_cast<const uint2 *>(src);
+    out[0] = __builtin_bit_cast(E, v.x);
+    out[1] = __builtin_bit_cast(E, v.y);
+  }
+}
+
+template <int G, class E>
+__device__ __forceinline__ void stv(E *dst, const E *in) {
+  if constexpr (G == 4) {
+    *reinterpret_cast<uint4 *>(dst) =
+        make_uint4(__builtin_bit_cast(uint32_t, in[0]), __builtin_bit_cast(uint32_t, in[1]),
+                   __builtin_bit_cast(uint32_t, in[2]), __builtin_bit_cast(uint32_t, in[3]));
+  } else {
+    *reinterpret_cast<uint2 *>(dst) =
+        make_uint2(__builtin_bit_cast(uint32_t, in[0]), __builtin_bit_cast(uint32_t, in[1]));
+  }
+}
+
+// Global array of staging slot f (f is a compile-time constant at every
+// use, so no pointer is held in registers).
 template <int DIM>
-__device__ __forceinline__ void soa_ptrs(const Soa &s, void **p) {
-  p[Slot<DIM>::CELL] = s.cell;
-  p[Slot<DIM>::OX] = s.ox;
-  if (DIM == 3) p[Slot<DIM>::OY] = s.oy;
-  p[Slot<DIM>::OZ] = s.oz;
-  p[Slot<DIM>::VX] = s.vx;
-  p[Slot<DIM>::VY] = s.vy;
-  p[Slot<DIM>::VZ] = s.vz;
-  p[Slot<DIM>::W] = s.w;
+__device__ __forceinline__ char *field_ptr(const Soa &s, int f) {
+  using SL = Slot<DIM>;
+  if (f == SL::CELL) return reinterpret_cast<char *>(s.cell);
+  if (f == SL::OX) return reinterpret_cast<char *>(s.ox);
+  if (DIM == 3 && f == SL::OY) return reinterpret_cast<char *>(s.oy);
+  if (f == SL::OZ) return reinterpret_cast<char *>(s.oz);
+  if (f == SL::VX) return reinterpret_cast<char *>(s.vx);
+  if (f == SL::VY) return reinterpret_cast<char *>(s.vy);
+  if (f == SL::VZ) return reinterpret_cast<char *>(s.vz);
+  return reinterpret_cast<char *>(s.w);
 }
 
 // Padded coordinates of a voxel.
@@ -354,17 +376,6 @@ __device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, in
   }
 }
 
-// Sort bin of a voxel in the x-z layout: its window cell, or the last bin.
-__device__ __forceinline__ int sort_bin(const Geom &g, int vox, int i0, int k0) {
-  using W = Win<2>;
-  if (vox < g.vlo || vox >= g.vhi) return kBins - 1;
-  int ip, jp, kp;
-  voxel_coords(g, vox, ip, jp, kp);
-  const int rx = ip - kGhost - i0 + W::RE, rz = kp - kGhost - k0 + W::RE;
-  return ((unsigned)rx < (unsigned)W::EX && (unsigned)rz < (unsigned)W::EZ) ? rx + rz * W::EX
-                                                                          : kBins - 1;
-}
-
 // One ion of the step: gather E^n, B^n at x^n, Boris push, move to x^{n+1}
 // (MODE 0; the state is updated in place and the kinetic-energy/momentum
 // terms are added to rk), then the deposit values at the half-step
@@ -373,8 +384,8 @@ __device__ __forceinline__ int sort_bin(const Geom &g, int vox, int i0, int k0) 
 template <int DIM, int SHAPE, int MODE>
 __device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int i0, int j0,
                                         int k0, int &vox, float &ox, float &oy, float &oz,
-                                        float &vx, float &vy, float &vz, float w, float *cv,
-                                        float *rk) {
+                                        float &vx, float &vy, float &vz, float w,
+                                        Dep<DIM, SHAPE> &dep, float *rk) {
   using W = Win<DIM>;
   constexpr int NT = Shape<DIM, SHAPE>::NT;
   const Geom &g = a.g;
@@ -448,7 +459,8 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int
     const float h = a.k.qmdt2;
     const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
     const float tx = h * bx, ty = h * by, tz = h * bz;
-    const float f = 2.f / (1.f + (tx * tx + ty * ty + tz * tz));
+    // 2 * rn(1/x) equals rn(2/x): scaling by 2 is exact
+    const float f = 2.f * __frcp_rn(1.f + (tx * tx + ty * ty + tz * tz));
     const float sx = f * tx, sy = f * ty, sz = f * tz;
     const float vpx = vmx + (vmy * tz - vmz * ty);
     const float vpy = vmy + (vmz * tx - vmx * tz);
@@ -509,7 +521,7 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int
   }
 
   // deposit q w S / V_c and q w v S / V_c at the half-step position
-  const int kshift = deposit_values<DIM, SHAPE>(hx, hy, hz, a.k.qvc * w, vxp, vyp, vzp, g, cv);
+  const int kshift = deposit_factors<DIM, SHAPE>(hx, hy, hz, a.k.qvc * w, vxp, vyp, vzp, g, dep);
   return vox0 + shx + shz * g.sz + (DIM == 3 ? shy * g.sy : 0) + kshift;
 }
 
@@ -529,16 +541,20 @@ struct Run {
 #pragma unroll
     for (int j = 0; j < NV; ++j) acc[j] = 0.f;
   }
-  __device__ __forceinline__ void add(const PushArgs &a, int pk, int own, const float *cv) {
+  __device__ __forceinline__ void add(const PushArgs &a, int pk, int own,
+                                      const Dep<DIM, SHAPE> &d) {
     if (pk == key) {
 #pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] += cv[j];
+      for (int j = 0; j < NV; ++j) acc[j] = d.fma_into(j, acc[j]);
     } else if (!CELLKEY || pk == own || key == INT_MIN) {
       if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
       key = pk;
 #pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] = cv[j];
+      for (int j = 0; j < NV; ++j) acc[j] = d.value(j);
     } else {
+      float cv[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) cv[j] = d.value(j);
       flush_direct<DIM, SHAPE>(a, pk, cv);
     }
   }
@@ -556,21 +572,20 @@ struct Run {
 // lies in the tile, give or take the drift since the last sort.  The block
 // stages E and B of the tile and a halo in shared memory; ions that drifted
 // further gather from global memory.  Each warp streams tiles of kTile ions
-// through shared memory with bulk copies.  In the x-z layout the warp
-// counting-sorts each staging tile by cell and each lane takes kChunk
-// consecutive ions of that order; in 3D each lane takes kChunk consecutive
-// ions of the memory order.  A lane sums the deposits of its ions in
-// registers per run of equal deposit key, flushing a run with vector
-// reductions into the global accumulator.
+// through shared memory with bulk copies; each lane takes kChunk consecutive
+// ions and sums their deposits in registers per run of equal deposit key,
+// flushing a run with vector reductions into the global accumulator.  The
+// staging tile is written back in place with bulk copies.
 template <int DIM, int SHAPE, int MODE>
-__global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(PushArgs a) {
+// (3D: the larger staging and window buffers allow two blocks per SM)
+__global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
+    push_kernel(PushArgs a) {
   using L = Layout<DIM, SHAPE>;
   using W = Win<DIM>;
   using SL = Slot<DIM>;
-  constexpr int NV = Shape<DIM, SHAPE>::NV;
   constexpr int NA = L::NA;
-  constexpr int CQ = kChunk / 4;  // quads per lane per staging tile
-  constexpr int TQ = kTile / 4;   // quads per staging tile
+  constexpr int CG = kChunk / kGroup;  // ion groups per lane per staging tile
+  constexpr int TQ = kTile / 4;        // quads per staging tile
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom &g = a.g;
   const int lane = threadIdx.x & 31;
@@ -609,8 +624,6 @@ __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(Push
   __syncthreads();
 
   float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};
-  void *gp[8];
-  soa_ptrs<DIM>(a.s, gp);
   bool failed = false;
   int k = 0;
   const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles
@@ -624,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(Push
       mbar_expect_tx(bar, bytes * NA);
 #pragma unroll
       for (int f = 0; f < NA; ++f)
-        bulk_load(T[f], reinterpret_cast<const char *>(gp[f]) + q0 * 16, bytes, bar);
+        bulk_load(T[f], field_ptr<DIM>(a.s, f) + q0 * 16, bytes, bar);
     }
     if (!mbar_wait_bounded(bar, (uint32_t)(k & 1))) {
       failed = true;
@@ -636,142 +649,43 @@ __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(Push
     run.reset();
     float rk[4] = {0.f, 0.f, 0.f, 0.f};
 
-    if constexpr (L::SORT) {
-      int *hist = reinterpret_cast<int *>(smem_raw + L::off_hist + L::hist_bytes * warp);
-      uint16_t *perm = reinterpret_cast<uint16_t *>(smem_raw + L::off_perm + L::perm_bytes * warp);
-      const int nion = (int)min((int64_t)nqt * 4, a.n - q0 * 4);
-      // lanes start their chunk at a rotated ion so that a warp's shared
-      // loads of one field hit distinct banks
-      const int rot = lane / (32 / kChunk);
-#pragma unroll
-      for (int b = lane * 4; b < kBins; b += 128)
-        *reinterpret_cast<int4 *>(hist + b) = make_int4(0, 0, 0, 0);
-      __syncwarp();
-      // bin of every ion and its rank in the bin
-      uint32_t br[kChunk];
-#pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
-        const int e = lane * kChunk + ((j + rot) & (kChunk - 1));
-        br[j] = 0xffffffffu;
-        if (e < nion) {
-          const int bin = sort_bin(g, TC[SL::CELL][e], i0, k0);
-          const int r = atomicAdd(hist + bin, 1);
-          br[j] = ((uint32_t)bin << 16) | (uint32_t)r;
-        }
-      }
-      __syncwarp();
-      // exclusive scan of the bins: each lane owns kBins / 32 consecutive bins
-      {
-        constexpr int PB = kBins / 32;
-        int v[PB];
-        int4 *h4 = reinterpret_cast<int4 *>(hist + lane * PB);
-#pragma unroll
-        for (int q = 0; q < PB / 4; ++q) {
-          const int4 x = h4[q];
-          v[4 * q] = x.x;
-          v[4 * q + 1] = x.y;
-          v[4 * q + 2] = x.z;
-          v[4 * q + 3] = x.w;
-        }
-        int tot = 0;
-#pragma unroll
-        for (int q = 0; q < PB; ++q) {
-          const int t = v[q];
-          v[q] = tot;
-          tot += t;
-        }
-        int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int base = incl - tot;
-#pragma unroll
-        for (int q = 0; q < PB / 4; ++q)
-          h4[q] = make_int4(v[4 * q] + base, v[4 * q + 1] + base, v[4 * q + 2] + base,
-                            v[4 * q + 3] + base);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
-        if (br[j] == 0xffffffffu) continue;
-        const int e = lane * kChunk + ((j + rot) & (kChunk - 1));
-        perm[hist[br[j] >> 16] + (int)(br[j] & 0xffffu)] = (uint16_t)e;
-      }
-      __syncwarp();
-
-      // the lane's kChunk consecutive positions of the sorted order
+    // groups of kGroup ions of the memory order; lanes start at a rotated
+    // group so that the vector shared loads of a phase hit distinct banks
+    const int rot = CG > 1 ? (lane / (32 / kChunk)) % CG : 0;
 #pragma unroll 1
-      for (int j = 0; j < kChunk; ++j) {
-        const int pos = lane * kChunk + ((j + rot) & (kChunk - 1));
-        if (pos >= nion) continue;
-        const int e = perm[pos];
-        int vox = TC[SL::CELL][e];
-        float ox = T[SL::OX][e], oy = 0.f, oz = T[SL::OZ][e];
-        float vx = T[SL::VX][e], vy = T[SL::VY][e], vz = T[SL::VZ][e];
-        const float w = T[SL::W][e];
-        const int own = vox;
-        float cv[NV];
-        const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, vox, ox, oy, oz, vx, vy,
-                                                  vz, w, cv, rk);
+    for (int jj = 0; jj < CG; ++jj) {
+      const int lg = lane * CG + (jj + rot) % CG;  // group within the staging tile
+      const int e0 = lg * kGroup;
+      if (e0 >= nqt * 4) continue;
+      int cc[kGroup];
+      float ox[kGroup], oy[kGroup], oz[kGroup], vx[kGroup], vy[kGroup], vz[kGroup], ww[kGroup];
+      ldv<kGroup>(&TC[SL::CELL][e0], cc);
+      ldv<kGroup>(&T[SL::OX][e0], ox);
+      if (DIM == 3) ldv<kGroup>(&T[SL::OY][e0], oy);
+      ldv<kGroup>(&T[SL::OZ][e0], oz);
+      ldv<kGroup>(&T[SL::VX][e0], vx);
+      ldv<kGroup>(&T[SL::VY][e0], vy);
+      ldv<kGroup>(&T[SL::VZ][e0], vz);
+      ldv<kGroup>(&T[SL::W][e0], ww);
+      const int64_t nvalid = a.n - (q0 * 4 + e0);  // ions of the group that exist
+#pragma unroll
+      for (int p = 0; p < kGroup; ++p) {
+        if (p >= nvalid) continue;
+        const int own = cc[p];
+        Dep<DIM, SHAPE> dep;
+        const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, cc[p], ox[p], oy[p], oz[p],
+                                                  vx[p], vy[p], vz[p], ww[p], dep, rk);
         if (pk == INT_MIN) continue;
-        if (MODE == 0) {
-          TC[SL::CELL][e] = vox;
-          T[SL::OX][e] = ox;
-          T[SL::OZ][e] = oz;
-          T[SL::VX][e] = vx;
-          T[SL::VY][e] = vy;
-          T[SL::VZ][e] = vz;
-        }
-        run.add(a, pk, own, cv);
+        run.add(a, pk, own, dep);
       }
-    } else {
-      // quads of the memory order; lanes start at a rotated quad so that the
-      // 128-bit shared loads of a quarter-warp hit distinct banks
-      const int rot = CQ > 1 ? (lane / (32 / kChunk)) % CQ : 0;
-#pragma unroll 1
-      for (int jj = 0; jj < CQ; ++jj) {
-        const int jq = (jj + rot) % CQ;
-        const int lq = lane * CQ + jq;  // quad within the staging tile
-        if (lq >= nqt) continue;
-        const int e0 = lq * 4;
-        const int4 c4 = *reinterpret_cast<const int4 *>(&TC[SL::CELL][e0]);
-        int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-        const float4 X = *reinterpret_cast<const float4 *>(&T[SL::OX][e0]);
-        const float4 Z = *reinterpret_cast<const float4 *>(&T[SL::OZ][e0]);
-        float4 Y = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (DIM == 3) Y = *reinterpret_cast<const float4 *>(&T[SL::OY][e0]);
-        const float4 VX = *reinterpret_cast<const float4 *>(&T[SL::VX][e0]);
-        const float4 VY = *reinterpret_cast<const float4 *>(&T[SL::VY][e0]);
-        const float4 VZ = *reinterpret_cast<const float4 *>(&T[SL::VZ][e0]);
-        const float4 Wq = *reinterpret_cast<const float4 *>(&T[SL::W][e0]);
-        float ox[4] = {X.x, X.y, X.z, X.w}, oy[4] = {Y.x, Y.y, Y.z, Y.w},
-              oz[4] = {Z.x, Z.y, Z.z, Z.w};
-        float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w},
-              vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
-        const float ww[4] = {Wq.x, Wq.y, Wq.z, Wq.w};
-        const int64_t ion0 = (q0 + lq) * 4;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          if (ion0 + p >= a.n) continue;
-          const int own = cc[p];
-          float cv[NV];
-          const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, cc[p], ox[p], oy[p],
-                                                    oz[p], vx[p], vy[p], vz[p], ww[p], cv, rk);
-          if (pk == INT_MIN) continue;
-          run.add(a, pk, own, cv);
-        }
-        if (MODE == 0) {
-          *reinterpret_cast<int4 *>(&TC[SL::CELL][e0]) = make_int4(cc[0], cc[1], cc[2], cc[3]);
-          *reinterpret_cast<float4 *>(&T[SL::OX][e0]) = make_float4(ox[0], ox[1], ox[2], ox[3]);
-          if (DIM == 3)
-            *reinterpret_cast<float4 *>(&T[SL::OY][e0]) = make_float4(oy[0], oy[1], oy[2], oy[3]);
-          *reinterpret_cast<float4 *>(&T[SL::OZ][e0]) = make_float4(oz[0], oz[1], oz[2], oz[3]);
-          *reinterpret_cast<float4 *>(&T[SL::VX][e0]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-          *reinterpret_cast<float4 *>(&T[SL::VY][e0]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
-          *reinterpret_cast<float4 *>(&T[SL::VZ][e0]) = make_float4(vz[0], vz[1], vz[2], vz[3]);
-        }
+      if (MODE == 0) {
+        stv<kGroup>(&TC[SL::CELL][e0], cc);
+        stv<kGroup>(&T[SL::OX][e0], ox);
+        if (DIM == 3) stv<kGroup>(&T[SL::OY][e0], oy);
+        stv<kGroup>(&T[SL::OZ][e0], oz);
+        stv<kGroup>(&T[SL::VX][e0], vx);
+        stv<kGroup>(&T[SL::VY][e0], vy);
+        stv<kGroup>(&T[SL::VZ][e0], vz);
       }
     }
     run.finish(a);
@@ -788,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, HV_PUSH_MIN_BLOCKS) push_kernel(Push
       const uint32_t bytes = (uint32_t)nqt * 16u;
 #pragma unroll
       for (int f = 0; f < NA; ++f)
-        if (f != SL::W) bulk_store(reinterpret_cast<char *>(gp[f]) + q0 * 16, T[f], bytes);
+        if (f != SL::W) bulk_store(field_ptr<DIM>(a.s, f) + q0 * 16, T[f], bytes);
       bulk_commit();
     }
   }

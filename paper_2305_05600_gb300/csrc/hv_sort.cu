@@ -1,9 +1,10 @@
-// Stable sort of ions by cell (a device of the GPU layout: it keeps a
-// warp's particles in one or two cells so that gathers hit cache and
-// deposits aggregate; the method's result changes only through FP32
-// summation order).
+// Sorting (a device of the GPU layout: it keeps a warp's particles in one or
+// two cells so that gathers hit shared memory and deposits aggregate; the
+// method's result changes only through FP32 summation order).
 //
-// Least-significant-digit radix sort on (key, index) pairs with 8-bit
+// The step sorts each species by supercell key with one counting-sort pass
+// (sort_species).  The stable key sort of the ABI (hv_sort_keys) is a
+// least-significant-digit radix sort on (key, index) pairs with 8-bit
 // digits, ceil(log2(nkeys)/8) passes.  Each pass is reduce-then-scan, so no
 // kernel waits on another block:
 //   upsweep   per 4096-key tile digit counts -> table[digit][tile]
@@ -200,23 +201,6 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys
   }
 }
 
-// Apply the permutation to every particle array: out[i] = in[perm[i]].
-__global__ void __launch_bounds__(256) gather_kernel(Soa in, Soa out, const int32_t *perm,
-                                                     int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int src = perm[i];
-    out.cell[i] = in.cell[src];
-    out.ox[i] = in.ox[src];
-    if (in.oy) out.oy[i] = in.oy[src];
-    out.oz[i] = in.oz[src];
-    out.vx[i] = in.vx[src];
-    out.vy[i] = in.vy[src];
-    out.vz[i] = in.vz[src];
-    out.w[i] = in.w[src];
-  }
-}
-
 // Count keys (warp-aggregated atomics) and flag out-of-range keys.  The loop
 // advances whole warps together so that every lane of a warp takes part in
 // the ballot and match of each round.
@@ -316,33 +300,79 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
   return cudaSuccess;
 }
 
-// Supercell sort key of every ion from its voxel index.
-__global__ void supercell_key_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *key) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t v = (uint32_t)vox[t];
-    const uint32_t q = fdiv(v, g.div_px);
-    const int ip = (int)(v - q * (uint32_t)g.px);
-    int jp = kGhost, kp;
-    if (g.dim2) {
-      kp = (int)q;
-    } else {
-      kp = (int)fdiv(q, g.div_py);
-      jp = (int)q - kp * g.py;
-    }
-    key[t] = supercell_key(g, ip - kGhost, jp - kGhost, kp - kGhost);
+// Supercell sort key of an ion from its voxel index (tile extents are
+// powers of two); a voxel outside the interior gets the last key, so a
+// corrupt index stays inside the arrays (the push reports it).
+__device__ __forceinline__ int ion_key(const Geom &g, int vox) {
+  if (vox < g.vlo || vox >= g.vhi) return (g.ntiles << g.tlog) - 1;
+  const uint32_t v = (uint32_t)vox;
+  const uint32_t q = fdiv(v, g.div_px);
+  const int i = (int)(v - q * (uint32_t)g.px) - kGhost;
+  int j = 0, k;
+  if (g.dim2) {
+    k = (int)q - kGhost;
+  } else {
+    const int kp = (int)fdiv(q, g.div_py);
+    j = (int)q - kp * g.py - kGhost;
+    k = kp - kGhost;
+  }
+  const int lx = __ffs(g.tx) - 1, ly = __ffs(g.ty) - 1, lz = __ffs(g.tz) - 1;
+  const int tile = (i >> lx) + g.ntx * ((j >> ly) + g.nty * (k >> lz));
+  const int local = (i & (g.tx - 1)) + ((j & (g.ty - 1)) << lx) + ((k & (g.tz - 1)) << (lx + ly));
+  return (tile << g.tlog) + local;
+}
+
+// The step's sort: a counting sort of the ions by supercell key.  Counts
+// (warp-aggregated atomics), an exclusive scan of the counts, then every
+// ion is copied once to the next free slot of its key (atomic cursors,
+// warp-aggregated).  Ions of one key keep no particular order among
+// themselves; the deposit sums them in any order.
+__global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < n;
+    const unsigned act = __ballot_sync(kFull, valid);
+    if (!valid) continue;
+    const int key = ion_key(g, vox[i]);
+    const unsigned peers = __match_any_sync(act, key);
+    if (lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
   }
 }
 
-// Tile ranges from sorted keys: off[t] = first ion whose tile is >= t.
-__global__ void tile_offsets_kernel(const int32_t *skey, int64_t n, int tlog, int ntiles,
-                                    int *off) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int tprev = i == 0 ? -1 : (skey[i - 1] >> tlog);
-    const int tcur = i == n ? ntiles : (skey[i] >> tlog);
-    for (int t = tprev + 1; t <= tcur; ++t) off[t] = (int)i;
+__global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, int32_t *cursor) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < n;
+    const unsigned act = __ballot_sync(kFull, valid);
+    if (!valid) continue;
+    const int key = ion_key(g, in.cell[i]);
+    const unsigned peers = __match_any_sync(act, key);
+    const int leader = __ffs(peers) - 1;
+    int first = 0;
+    if (lane == leader) first = atomicAdd(&cursor[key], __popc(peers));
+    first = __shfl_sync(act, first, leader);
+    const int dst = first + __popc(peers & ((1u << lane) - 1u));
+    out.cell[dst] = in.cell[i];
+    out.ox[dst] = in.ox[i];
+    if (in.oy) out.oy[dst] = in.oy[i];
+    out.oz[dst] = in.oz[i];
+    out.vx[dst] = in.vx[i];
+    out.vy[dst] = in.vy[i];
+    out.vz[dst] = in.vz[i];
+    out.w[dst] = in.w[i];
   }
+}
+
+// Tile ranges from the scanned key counts: tile t starts at its first key.
+__global__ void tile_starts_kernel(const int32_t *off, int tlog, int ntiles, int64_t n, int *tile_off) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x)
+    tile_off[t] = t == ntiles ? (int)n : off[(int64_t)t << tlog];
 }
 
 __global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
@@ -355,27 +385,31 @@ __global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
 hv_status sort_species(hv_ctx *c, int sidx) {
   Species &sp = c->sp[sidx];
   if (sp.n <= 1) return HV_OK;
-  if (!scratch_reserve(c->sort, sp.n, c->stream))
-    return fail(HV_ENOMEM, "sort scratch allocation failed");
   const Geom &g = c->g;
-  Soa &in = sp.buf[sp.cur];
-  int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 1024);
-  // keys in k[1]: the radix passes write k[0], k[1], ... so the input is
-  // consumed before it is overwritten
-  supercell_key_kernel<<<blocks, 256, 0, c->stream>>>(g, in.cell, sp.n, c->sort->k[1]);
-  c->launches++;
-  int32_t *perm = nullptr, *skeys = nullptr;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
-  cudaError_t e = radix_perm(c->sort->k[1], sp.n, nkeys, c->sort, c->stream, &perm, &c->launches,
-                             &skeys);
-  if (e != cudaSuccess) return cuda_fail(e, "sort passes");
+  const int64_t nb = bsum_len(nkeys);
+  if (!c->bucket) {
+    c->bucket_bytes = align256(sizeof(int32_t) * nkeys) + align256(sizeof(int32_t) * nb);
+    c->bucket = (int32_t *)dev_alloc(c->bucket_bytes, c->stream);
+    if (!c->bucket) return fail(HV_ENOMEM, "sort scratch allocation failed");
+  }
+  int32_t *cnt = c->bucket;
+  int32_t *bsum = (int32_t *)((char *)c->bucket + align256(sizeof(int32_t) * nkeys));
+  Soa &in = sp.buf[sp.cur];
   Soa &out = sp.buf[sp.cur ^ 1];
-  gather_kernel<<<blocks, 256, 0, c->stream>>>(in, out, perm, sp.n);
-  tile_offsets_kernel<<<(int)std::min<int64_t>((sp.n + 256) / 256, 8 * 1024), 256, 0,
-                        c->stream>>>(skeys, sp.n, g.tlog, g.ntiles, sp.tile_off);
-  c->launches += 2;
+  const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 16 * 1024);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sort counts");
+  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, in.cell, sp.n, cnt);
+  chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
+  scan_bsum_kernel<<<1, kThreads, 0, c->stream>>>(bsum, nb);
+  chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
+  tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, c->stream>>>(cnt, g.tlog, g.ntiles, sp.n,
+                                                                     sp.tile_off);
+  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(g, in, out, sp.n, cnt);
+  c->launches += 6;
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "sort gather");
+  if (e != cudaSuccess) return cuda_fail(e, "sort");
   sp.cur ^= 1;
   return HV_OK;
 }
@@ -393,6 +427,10 @@ void sort_release(hv_ctx *c) {
     dev_free(c->sort->base, c->sort->bytes, c->stream);
     delete c->sort;
     c->sort = nullptr;
+  }
+  if (c->bucket) {
+    dev_free(c->bucket, c->bucket_bytes, c->stream);
+    c->bucket = nullptr;
   }
 }
 

@@ -148,6 +148,34 @@ def _finish(cell, off, v, w, q=1.0, m=1.0) -> SpeciesInput:
                         w=np.ascontiguousarray(w.astype(np.float32)))
 
 
+def distinct_weights(w: np.ndarray) -> np.ndarray:
+    """The float32 weights moved up by the fewest ulps that make every value
+    distinct (ties broken in index order).  The library reorders ions as it
+    steps but copies each weight bit for bit, so a caller that loads
+    distinct weights can identify every ion afterwards."""
+    w = np.asarray(w, np.float32).copy()
+    order = np.argsort(w, kind="stable")
+    ws = w[order]
+    up = np.float32(np.inf)
+    for k in range(1, ws.shape[0]):
+        if ws[k] <= ws[k - 1]:
+            ws[k] = np.nextafter(ws[k - 1], up)
+    w[order] = ws
+    return w
+
+
+def with_distinct_weights(wl: "Workload") -> "Workload":
+    """The workload with distinct_weights applied across all its species."""
+    sizes = [s.n for s in wl.species]
+    allw = distinct_weights(np.concatenate([s.w for s in wl.species]))
+    o = 0
+    for k, s in enumerate(wl.species):
+        wl.species[k] = SpeciesInput(s.q, s.m, s.cell, s.off, s.v,
+                                     np.ascontiguousarray(allw[o:o + sizes[k]]))
+        o += sizes[k]
+    return wl
+
+
 # ----------------------------------------------------------------------------
 # workloads
 # ----------------------------------------------------------------------------
