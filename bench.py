@@ -5,7 +5,7 @@ Harris-sheet workload (1024x512 cells, dx = 0.25 d_i, 100 ions per cell,
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one pass of the whole hot path (sort every 20 steps, gather +
+One step = one pass of the whole hot path (sort every 4 steps, gather +
 Boris push + half-step deposit + move, moment post, 10 field subcycles of
 two Ohm/Faraday stages, final Ohm).  Under torchrun each rank runs an
 independent replica (the path is not sharded); rank 0 prints one JSON line.

@@ -340,7 +340,7 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&c->device);
   c->vc = p->dx * p->dy * p->dz;
-  c->push_blocks = c->g.ntiles;  // the push runs one block per supercell tile
+  c->push_blocks = c->g.ntiles * kPushSplit;  // push blocks (kPushSplit per supercell tile)
   c->grid_blocks = grid_reduce_blocks(c->device);
   const Geom &g = c->g;
   const size_t npad = (size_t)g.npad, nc = (size_t)g.ncell;

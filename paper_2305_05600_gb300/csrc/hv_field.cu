@@ -461,7 +461,9 @@ __device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, fl
     }
 }
 
-__global__ void __launch_bounds__(256) substep2d_kernel(SubArgs a) {
+constexpr int kSubThreads = 256;
+
+__global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
   using namespace sub2d;
   extern __shared__ float sm[];
   const Geom &g = a.g;
@@ -474,24 +476,44 @@ __global__ void __launch_bounds__(256) substep2d_kernel(SubArgs a) {
     const int kk = wrap_near(z0 + z, g.nz, SZ + SH);
     return ii + g.nx * kk;
   };
-  // load B on R6 and the moments on R5
-  for (int t_ = (int)threadIdx.x; t_ < N(6); t_ += blockDim.x) {
-      const int x = t_ % W(6) - 6, z = t_ / W(6) - 6;
-      const float4 b = a.B[gidx(x, z)];
-      const int i = at(6, x, z);
-      Bp[i] = b.x;
-      Bp[N(6) + i] = b.y;
-      Bp[2 * N(6) + i] = b.z;
+  // load B on R6 and the moments on R5: every thread issues all its loads
+  // before it stores any, so the L2 latencies overlap
+  {
+    constexpr int LB = (N(6) + kSubThreads - 1) / kSubThreads;
+    constexpr int LM = (N(5) + kSubThreads - 1) / kSubThreads;
+    float4 bv[LB], mv[LM];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t_ = (int)threadIdx.x + u * kSubThreads;
+      if (t_ < N(6)) bv[u] = a.B[gidx(t_ % W(6) - 6, t_ / W(6) - 6)];
     }
-  for (int t_ = (int)threadIdx.x; t_ < N(5); t_ += blockDim.x) {
-      const int x = t_ % W(5) - 5, z = t_ / W(5) - 5;
-      const float4 m = a.mom[gidx(x, z)];
-      const int i = at(5, x, z);
-      Mp[i] = m.x;
-      Mp[N(5) + i] = m.y;
-      Mp[2 * N(5) + i] = m.z;
-      Mp[3 * N(5) + i] = m.w;
+#pragma unroll
+    for (int u = 0; u < LM; ++u) {
+      const int t_ = (int)threadIdx.x + u * kSubThreads;
+      if (t_ < N(5)) mv[u] = a.mom[gidx(t_ % W(5) - 5, t_ / W(5) - 5)];
     }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t_ = (int)threadIdx.x + u * kSubThreads;
+      if (t_ < N(6)) {
+        const int i = at(6, t_ % W(6) - 6, t_ / W(6) - 6);
+        Bp[i] = bv[u].x;
+        Bp[N(6) + i] = bv[u].y;
+        Bp[2 * N(6) + i] = bv[u].z;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LM; ++u) {
+      const int t_ = (int)threadIdx.x + u * kSubThreads;
+      if (t_ < N(5)) {
+        const int i = at(5, t_ % W(5) - 5, t_ / W(5) - 5);
+        Mp[i] = mv[u].x;
+        Mp[N(5) + i] = mv[u].y;
+        Mp[2 * N(5) + i] = mv[u].z;
+        Mp[3 * N(5) + i] = mv[u].w;
+      }
+    }
+  }
   __syncthreads();
   // stage 1: J(B) on R5, E on R4, B* on R3
   curl2d<6, 5>(k, Bp, Jp);
@@ -747,7 +769,7 @@ cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) 
   const int ntx = (c->g.nx + sub2d::SX - 1) / sub2d::SX;
   const int ntz = (c->g.nz + sub2d::SZ - 1) / sub2d::SZ;
   c->launches++;
-  substep2d_kernel<<<ntx * ntz, 256, smem, c->stream>>>(a);
+  substep2d_kernel<<<ntx * ntz, kSubThreads, smem, c->stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,8 @@ struct Geom {
 // Tile extents of the supercell order: 16x16 cells in the x-z layout,
 // 8x8x8 cells in 3D (cells per tile a power of two).
 constexpr int kTile2X = 16, kTile2Z = 16, kTile3 = 8;
+// push blocks per supercell tile
+constexpr int kPushSplit = 4;
 
 // Supercell sort key of interior cell (i, j, k): tile index, then the cell
 // inside the tile, both x fastest.
@@ -88,6 +90,28 @@ __host__ __device__ __forceinline__ int supercell_key(const Geom &g, int i, int 
 
 __host__ __device__ __forceinline__ int voxel_of(const Geom &g, int i, int j, int k) {
   return (i + kGhost) + (g.dim2 ? 0 : (j + kGhost) * g.sy) + (k + kGhost) * g.sz;
+}
+
+// Supercell sort key of an ion from its voxel index (tile extents are
+// powers of two); a voxel outside the interior gets the last key, so a
+// corrupt index stays inside the arrays (the push reports it).
+__device__ __forceinline__ int ion_key(const Geom &g, int vox) {
+  if (vox < g.vlo || vox >= g.vhi) return (g.ntiles << g.tlog) - 1;
+  const uint32_t v = (uint32_t)vox;
+  const uint32_t q = fdiv(v, g.div_px);
+  const int i = (int)(v - q * (uint32_t)g.px) - kGhost;
+  int j = 0, k;
+  if (g.dim2) {
+    k = (int)q - kGhost;
+  } else {
+    const int kp = (int)fdiv(q, g.div_py);
+    j = (int)q - kp * g.py - kGhost;
+    k = kp - kGhost;
+  }
+  const int lx = __ffs(g.tx) - 1, ly = __ffs(g.ty) - 1, lz = __ffs(g.tz) - 1;
+  const int tile = (i >> lx) + g.ntx * ((j >> ly) + g.nty * (k >> lz));
+  const int local = (i & (g.tx - 1)) + ((j & (g.ty - 1)) << lx) + ((k & (g.tz - 1)) << (lx + ly));
+  return (tile << g.tlog) + local;
 }
 
 // Padded coordinates standing for interior coordinate i on an axis of n
@@ -114,6 +138,8 @@ struct Species {
   int64_t n, cap;
   int *tile_off;        // [ntiles + 1] first ion of each tile in the live
                         // buffer (valid ranges even before the first sort)
+  int32_t *bucket;      // step sort: key counts, then offsets / cursors, and
+  size_t bucket_bytes;  // scan sums
   Soa buf[2];
   int cur;              // index of the live buffer set
   void *base[2];        // allocation bases
@@ -176,8 +202,6 @@ struct hv_ctx {
   int started;
   // sort scratch (lazily sized to the largest species)
   hv::SortScratch *sort;
-  int32_t *bucket;      // step sort: key counts / cursors and scan sums
-  size_t bucket_bytes;
   // profiling
   int prof_on;
   hv_prof_t prof;

@@ -567,11 +567,13 @@ struct Run {
 // MODE 0: full step.  MODE 1: start-up deposit at the current position with
 // the stored velocity (no push, no move, no write-back).
 //
-// One block per supercell tile.  Ions are kept sorted tile-major, so the
-// block's ion range [tile_off[t], tile_off[t+1]) (rounded to whole quads)
-// lies in the tile, give or take the drift since the last sort.  The block
-// stages E and B of the tile and a halo in shared memory; ions that drifted
-// further gather from global memory.  Each warp streams tiles of kTile ions
+// kPushSplit blocks per supercell tile, each taking a contiguous part of the
+// tile's ion range (finer work units than whole tiles keep the last wave of
+// blocks short).  Ions are kept sorted tile-major, so the tile's ion range
+// [tile_off[t], tile_off[t+1]) (rounded to whole quads) lies in the tile,
+// give or take the drift since the last sort.  The block stages E and B of
+// the tile and a halo in shared memory; ions that drifted further gather
+// from global memory.  Each warp streams tiles of kTile ions
 // through shared memory with bulk copies; each lane takes kChunk consecutive
 // ions and sums their deposits in registers per run of equal deposit key,
 // flushing a run with vector reductions into the global accumulator.  The
@@ -596,8 +598,10 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   float4 *eb = reinterpret_cast<float4 *>(smem_raw + L::off_eb);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L::off_bar) + warp;
 
-  // tile origin and the block's range of quads
-  const int tile = blockIdx.x;
+  // tile origin and the block's range of quads: kPushSplit blocks share a
+  // tile, each taking a contiguous part of its staging tiles
+  const int tile = blockIdx.x / kPushSplit;
+  const int part = blockIdx.x % kPushSplit;
   const int ti = tile % g.ntx, tj = (tile / g.ntx) % g.nty, tk = tile / (g.ntx * g.nty);
   const int i0 = ti * W::TX, j0 = tj * W::TY, k0 = tk * W::TZ;
   const int64_t nq = (a.n + 3) >> 2;
@@ -626,9 +630,10 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};
   bool failed = false;
   int k = 0;
-  const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles
+  const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles of the tile
+  const int64_t st_lo = nst * part / kPushSplit, st_hi = nst * (part + 1) / kPushSplit;
 
-  for (int64_t st = warp; st < nst && !failed; st += nwarps, ++k) {
+  for (int64_t st = st_lo + warp; st < st_hi && !failed; st += nwarps, ++k) {
     const int64_t q0 = qa + st * TQ;
     const int nqt = (int)min((int64_t)TQ, qe - q0);
     if (lane == 0) {
@@ -788,7 +793,7 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.err = c->err;
   c->launches++;
   const int shape = c->p.shape;
-  const int blocks = c->g.ntiles;  // one block per supercell tile
+  const int blocks = c->push_blocks;  // kPushSplit blocks per supercell tile
   if (c->g.dim2) {
     return mode == 0 ? launch_shape<2, 0>(shape, a, blocks, c->stream)
                      : launch_shape<2, 1>(shape, a, blocks, c->stream);

@@ -300,72 +300,89 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
   return cudaSuccess;
 }
 
-// Supercell sort key of an ion from its voxel index (tile extents are
-// powers of two); a voxel outside the interior gets the last key, so a
-// corrupt index stays inside the arrays (the push reports it).
-__device__ __forceinline__ int ion_key(const Geom &g, int vox) {
-  if (vox < g.vlo || vox >= g.vhi) return (g.ntiles << g.tlog) - 1;
-  const uint32_t v = (uint32_t)vox;
-  const uint32_t q = fdiv(v, g.div_px);
-  const int i = (int)(v - q * (uint32_t)g.px) - kGhost;
-  int j = 0, k;
-  if (g.dim2) {
-    k = (int)q - kGhost;
-  } else {
-    const int kp = (int)fdiv(q, g.div_py);
-    j = (int)q - kp * g.py - kGhost;
-    k = kp - kGhost;
-  }
-  const int lx = __ffs(g.tx) - 1, ly = __ffs(g.ty) - 1, lz = __ffs(g.tz) - 1;
-  const int tile = (i >> lx) + g.ntx * ((j >> ly) + g.nty * (k >> lz));
-  const int local = (i & (g.tx - 1)) + ((j & (g.ty - 1)) << lx) + ((k & (g.tz - 1)) << (lx + ly));
-  return (tile << g.tlog) + local;
-}
-
 // The step's sort: a counting sort of the ions by supercell key.  Counts
 // (warp-aggregated atomics), an exclusive scan of the counts, then every
 // ion is copied once to the next free slot of its key (atomic cursors,
 // warp-aggregated).  Ions of one key keep no particular order among
 // themselves; the deposit sums them in any order.
+// Each warp takes kUnroll consecutive chunks of 32 ions per iteration and
+// issues all their loads (and, in the scatter, all their atomics) before it
+// needs a result, so memory latencies overlap.
+constexpr int kUnroll = 4;
+
 __global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt) {
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
-       base += stride) {
-    const int64_t i = base + lane;
-    const bool valid = i < n;
-    const unsigned act = __ballot_sync(kFull, valid);
-    if (!valid) continue;
-    const int key = ion_key(g, vox[i]);
-    const unsigned peers = __match_any_sync(act, key);
-    if (lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+  const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
+       base < n; base += wstride) {
+    int v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + 32 * u + lane;
+      v[u] = i < n ? vox[i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + 32 * u + lane;
+      const unsigned act = __ballot_sync(kFull, i < n);
+      if (i >= n) continue;
+      const int key = ion_key(g, v[u]);
+      const unsigned peers = __match_any_sync(act, key);
+      if (lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+    }
   }
 }
 
 __global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, int32_t *cursor) {
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
-       base += stride) {
-    const int64_t i = base + lane;
-    const bool valid = i < n;
-    const unsigned act = __ballot_sync(kFull, valid);
-    if (!valid) continue;
-    const int key = ion_key(g, in.cell[i]);
-    const unsigned peers = __match_any_sync(act, key);
-    const int leader = __ffs(peers) - 1;
-    int first = 0;
-    if (lane == leader) first = atomicAdd(&cursor[key], __popc(peers));
-    first = __shfl_sync(act, first, leader);
-    const int dst = first + __popc(peers & ((1u << lane) - 1u));
-    out.cell[dst] = in.cell[i];
-    out.ox[dst] = in.ox[i];
-    if (in.oy) out.oy[dst] = in.oy[i];
-    out.oz[dst] = in.oz[i];
-    out.vx[dst] = in.vx[i];
-    out.vy[dst] = in.vy[i];
-    out.vz[dst] = in.vz[i];
-    out.w[dst] = in.w[i];
+  const bool has_y = in.oy != nullptr;
+  const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
+       base < n; base += wstride) {
+    int c[kUnroll];
+    float x[kUnroll], y[kUnroll], z[kUnroll], vx[kUnroll], vy[kUnroll], vz[kUnroll], w[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + 32 * u + lane;
+      if (i < n) {
+        c[u] = in.cell[i];
+        x[u] = in.ox[i];
+        y[u] = has_y ? in.oy[i] : 0.f;
+        z[u] = in.oz[i];
+        vx[u] = in.vx[i];
+        vy[u] = in.vy[i];
+        vz[u] = in.vz[i];
+        w[u] = in.w[i];
+      }
+    }
+    int dst[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + 32 * u + lane;
+      const unsigned act = __ballot_sync(kFull, i < n);
+      dst[u] = -1;
+      if (i >= n) continue;
+      const int key = ion_key(g, c[u]);
+      const unsigned peers = __match_any_sync(act, key);
+      const int leader = __ffs(peers) - 1;
+      int first = 0;
+      if (lane == leader) first = atomicAdd(&cursor[key], __popc(peers));
+      first = __shfl_sync(act, first, leader);
+      dst[u] = first + __popc(peers & ((1u << lane) - 1u));
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int d = dst[u];
+      if (d < 0) continue;
+      out.cell[d] = c[u];
+      out.ox[d] = x[u];
+      if (has_y) out.oy[d] = y[u];
+      out.oz[d] = z[u];
+      out.vx[d] = vx[u];
+      out.vy[d] = vy[u];
+      out.vz[d] = vz[u];
+      out.w[d] = w[u];
+    }
   }
 }
 
@@ -382,32 +399,56 @@ __global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
 
 }  // namespace
 
-hv_status sort_species(hv_ctx *c, int sidx) {
-  Species &sp = c->sp[sidx];
-  if (sp.n <= 1) return HV_OK;
+namespace {
+
+// Per-species key counts and scan sums, allocated at the first sort.
+hv_status bucket_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum) {
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
-  if (!c->bucket) {
-    c->bucket_bytes = align256(sizeof(int32_t) * nkeys) + align256(sizeof(int32_t) * nb);
-    c->bucket = (int32_t *)dev_alloc(c->bucket_bytes, c->stream);
-    if (!c->bucket) return fail(HV_ENOMEM, "sort scratch allocation failed");
+  if (!sp.bucket) {
+    sp.bucket_bytes = align256(sizeof(int32_t) * nkeys) + align256(sizeof(int32_t) * nb);
+    sp.bucket = (int32_t *)dev_alloc(sp.bucket_bytes, c->stream);
+    if (!sp.bucket) return fail(HV_ENOMEM, "sort scratch allocation failed");
   }
-  int32_t *cnt = c->bucket;
-  int32_t *bsum = (int32_t *)((char *)c->bucket + align256(sizeof(int32_t) * nkeys));
-  Soa &in = sp.buf[sp.cur];
-  Soa &out = sp.buf[sp.cur ^ 1];
-  const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 16 * 1024);
+  *cnt = sp.bucket;
+  *bsum = (int32_t *)((char *)sp.bucket + align256(sizeof(int32_t) * nkeys));
+  return HV_OK;
+}
+
+// Counts of the live buffer's keys, scanned in place into offsets (the
+// scatter's cursors), and the tile starts taken from them into tile_off.
+cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int *tile_off) {
+  const Geom &g = c->g;
+  const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
+  const int64_t nb = bsum_len(nkeys);
+  const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "sort counts");
-  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, in.cell, sp.n, cnt);
+  if (e != cudaSuccess) return e;
+  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, sp.buf[sp.cur].cell, sp.n, cnt);
   chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
   scan_bsum_kernel<<<1, kThreads, 0, c->stream>>>(bsum, nb);
   chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
   tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, c->stream>>>(cnt, g.tlog, g.ntiles, sp.n,
-                                                                     sp.tile_off);
-  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(g, in, out, sp.n, cnt);
-  c->launches += 6;
+                                                                     tile_off);
+  c->launches += 5;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+hv_status sort_species(hv_ctx *c, int sidx) {
+  Species &sp = c->sp[sidx];
+  if (sp.n <= 1) return HV_OK;
+  int32_t *cnt, *bsum;
+  hv_status st = bucket_reserve(c, sp, &cnt, &bsum);
+  if (st != HV_OK) return st;
+  cudaError_t e = key_offsets(c, sp, cnt, bsum, sp.tile_off);
+  if (e != cudaSuccess) return cuda_fail(e, "sort counts");
+  const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
+  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
+                                                       sp.n, cnt);
+  c->launches++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sort");
   sp.cur ^= 1;
@@ -428,9 +469,10 @@ void sort_release(hv_ctx *c) {
     delete c->sort;
     c->sort = nullptr;
   }
-  if (c->bucket) {
-    dev_free(c->bucket, c->bucket_bytes, c->stream);
-    c->bucket = nullptr;
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    Species &sp = c->sp[s];
+    if (sp.bucket) dev_free(sp.bucket, sp.bucket_bytes, c->stream);
+    sp.bucket = nullptr;
   }
 }
 
