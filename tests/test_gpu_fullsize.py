@@ -1,0 +1,207 @@
+"""Parity at full size, in the launch configuration bench.py times, and on
+the 3D configurations at oracle-sized subdomains.
+
+Workload: the 2D Harris sheet of the benchmark, 1024x512 cells, 100 ions per
+cell (52,428,800 ions), QS shape, 10 field subcycles, sort every 4 steps.
+One GPU step is compared with one step of the FP64 oracle on the same
+input:
+  * the whole grids: deposited n, J, B (relative L2 <= 1e-6) and E
+    (relative L2 <= 1e-4).  The QS weights of Eq. 17 jump across a cell
+    face, and the GPU decides the half-step cell in FP32, the oracle in
+    FP64; at this size a few dozen ions land within FP32 rounding of a
+    face and may be deposited on different sides.  The oracle's own
+    half-step positions identify them: outside the cells their deposit
+    can reach, n and J must agree to relative L2 1e-5 (the step
+    tolerance of the small parity tests, E to 1e-4 one cell further out);
+    inside, the difference must stay within the weight jump those ions can
+    cause (at most 1/3 of q w / V_c per ion and cell, times |v| for J);
+  * 4096 sampled ions, found after the library's reorder by marker
+    weights: a sampled ion's weight is moved by a few ulps to a value no
+    other ion has, and the library copies weights bit for bit;
+  * the deposited charge against the sum of q w (charge conservation at
+    any size) and the FP64 diagnostics.
+The same check runs on the 3D Harris sheet (guide field, 32 ppc) on a
+periodic 64^3 subdomain and on the ion-ion beam on 64x32x32 cells.  The
+oracle step of the full 2D workload takes tens of seconds on one host
+core."""
+import numpy as np
+import pytest
+
+from paper_2305_05600_gb300 import inputs as I
+from tests.helpers import oracle_sim, periodic_delta, phys_pos
+
+pytestmark = pytest.mark.gpu
+
+NSAMPLE = 4096
+
+
+@pytest.fixture(scope="module")
+def hvmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_05600_gb300 import hv
+    hv.lib()
+    hv.hv_set_allocator(True)
+    return hv
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def mark_sample(w, rng, k):
+    """Indices of k sampled ions and weights in which each of them is moved
+    up by the fewest ulps that give it a value no other ion has."""
+    w = np.asarray(w, np.float32).copy()
+    idx = rng.choice(w.shape[0], k, replace=False)
+    taken = set(np.unique(w).tolist())
+    up = np.float32(np.inf)
+    for i in idx:
+        v = np.float32(w[i])
+        while True:
+            v = np.nextafter(v, up)
+            if float(v) not in taken:
+                break
+        taken.add(float(v))
+        w[i] = v
+    return idx, w
+
+
+def face_ambiguity(p, off0, cell0, v_half, w, band=2e-6):
+    """Ions whose half-step position lies within `band` of a cell face in the
+    oracle's FP64 arithmetic, the cells their deposit can reach, and per
+    cell the sums of q w / V_c and q w |v_a| / V_c of those ions.
+
+    The QS weights of Eq. 17 jump across a face by at most 1/3, and the GPU
+    decides the half-step cell in FP32 (`band` is about 20 FP32 ulps of an
+    offset), the oracle in FP64, so such an ion may be deposited on
+    different sides of the face."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    dims = (nx, ny, nz)
+    dl = (p["dx"], p["dy"], p["dz"])
+    amb = np.zeros(cell0.shape[0], bool)
+    for a in range(3):
+        if dims[a] > 1:
+            h = off0[a].astype(np.float64) + v_half[a] * (p["dt"] / dl[a])
+            amb |= np.abs(np.abs(h) - 1.0) < band
+    c = cell0[amb].astype(np.int64)
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    vc = dl[0] * dl[1] * dl[2]
+    sn = w[amb].astype(np.float64) / vc
+    sj = np.abs(v_half[:, amb]) * sn
+    ncell = nx * ny * nz
+    taint = np.zeros(ncell, bool)
+    bound_n = np.zeros(ncell)
+    bound_j = np.zeros((3, ncell))
+    # the half-step cell is within one cell of the start cell and the QS
+    # stencil reaches one cell further
+    span = [range(-2, 3) if d > 1 else range(1) for d in dims]
+    for di in span[0]:
+        for dj in span[1]:
+            for dk in span[2]:
+                cc = (i + di) % nx + nx * ((j + dj) % ny + ny * ((k + dk) % nz))
+                taint[cc] = True
+                np.add.at(bound_n, cc, sn)
+                for a in range(3):
+                    np.add.at(bound_j[a], cc, sj[a])
+    return amb, taint, bound_n, bound_j
+
+
+def dilate(p, mask):
+    """Cells within one cell (each axis with more than one cell) of mask."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    m = mask.reshape(nz, ny, nx)
+    out = m.copy()
+    for ax, n in ((0, nz), (1, ny), (2, nx)):
+        if n > 1:
+            out |= np.roll(m, 1, axis=ax) | np.roll(m, -1, axis=ax)
+    return out.reshape(-1)
+
+
+def one_step_check(hvmod, wl, nsample=NSAMPLE, seed=2024):
+    """One GPU step against one oracle step; grids, diagnostics and sampled
+    ions as described in the module docstring."""
+    p = wl.params
+    s = wl.species[0]
+    rng = np.random.default_rng(seed)
+    idx, w = mark_sample(s.w, rng, nsample)
+    wl.species[0] = I.SpeciesInput(s.q, s.m, s.cell, s.off, s.v, w)
+
+    ctx = hvmod.load_workload(wl)
+    hvmod.hv_step(ctx, 1)
+    m = hvmod.hv_moments(ctx)
+    d = hvmod.hv_diag(ctx)
+    g = hvmod.hv_get_ions(ctx, 0)
+    ctx.close()
+
+    sim = oracle_sim(wl)
+    sim.step(1)
+    od = sim.diags[-1]
+    sp = sim.species[0]
+
+    # cells that face-ambiguous half-step deposits can reach, and the most
+    # those deposits can change there (a QS weight jumps by at most 1/3)
+    amb, taint, bound_n, bound_j = face_ambiguity(p, s.off, s.cell, sp.v, w)
+    assert taint.mean() < 0.1, taint.mean()  # most cells keep the 1e-5 check
+    clean = ~taint
+
+    n = m["n"].reshape(-1).astype(np.float64)
+    J = m["J"].reshape(3, -1).astype(np.float64)
+    assert rel_l2(n[clean], sim.n_prev[clean]) < 1e-5
+    assert rel_l2(J[:, clean], sim.J_prev[:, clean]) < 1e-5
+    # element-wise everywhere: FP32 rounding plus what the ambiguous ions
+    # can move
+    slack = 1e-4 * np.abs(sim.n_prev).max()
+    assert (np.abs(n - sim.n_prev) <= bound_n / 3.0 + slack).all()
+    jslack = 1e-4 * np.abs(sim.J_prev).max()
+    assert (np.abs(J - sim.J_prev) <= bound_j / 3.0 + jslack).all()
+    assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+    clean_e = ~dilate(p, taint)
+    assert rel_l2(m["E"].reshape(3, -1)[:, clean_e], sim.E[:, clean_e]) < 1e-4
+    qw = float(np.sum(w.astype(np.float64))) * s.q
+    assert abs(d["charge"] - qw) < 1e-6 * qw
+    assert abs(d["charge"] - od["charge"]) < 1e-6 * od["charge"]
+    assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+    assert abs(d["W_B"] - od["W_B"]) < 1e-6 * od["W_B"]
+    print(f"face-ambiguous ions {int(amb.sum())}, cells they can reach {taint.mean():.2e}")
+
+    # the sampled ions, located on both sides by their marker weights
+    marks = w[idx]
+    order_g = np.argsort(g["w"], kind="stable")
+    gw_sorted = g["w"][order_g]
+    hit = np.searchsorted(gw_sorted, marks)
+    assert np.array_equal(gw_sorted[hit], marks)
+    gi = order_g[hit]
+    po = phys_pos(p, sp.cell[idx], sp.off[:, idx])
+    pg = phys_pos(p, g["cell"][gi], g["off"][:, gi].astype(np.float64))
+    dpos = periodic_delta(p, pg, po)
+    dl = np.array([p["dx"], p["dy"], p["dz"]])[:, None]
+    assert np.abs(dpos / dl).max() < 1e-5
+    vscale = float(np.sqrt(np.mean(s.v.astype(np.float64) ** 2)))
+    dv = np.abs(g["v"][:, gi].astype(np.float64) - sp.v[:, idx])
+    vmag = np.linalg.norm(sp.v[:, idx], axis=0)
+    assert (dv.max(axis=0) <= 1e-5 * (vmag + vscale)).all(), dv.max()
+
+
+def test_full_size_harris2d_one_step(hvmod):
+    """The benchmark workload itself: 1024x512 cells, 52,428,800 ions."""
+    wl = I.harris(shape="qs", seed=1000, sort_every=4)
+    assert (wl.params["nx"], wl.params["nz"], wl.n_particles) == (1024, 512, 52_428_800)
+    one_step_check(hvmod, wl)
+
+
+def test_harris3d_64cubed_subdomain_one_step(hvmod):
+    """The 3D Harris sheet with guide field 0.1 B0 and 32 ppc on a periodic
+    64^3 subdomain (8,388,608 ions), sorted every 20 steps."""
+    wl = I.harris3d(nx=64, ny=64, nz=64, ppc=32, dx=0.5, seed=3000, sort_every=20)
+    one_step_check(hvmod, wl)
+
+
+def test_beam3d_reduced_one_step(hvmod):
+    """The ion-ion beam workload (56 core + 8 beam ions per cell, beam at
+    10 v_A) on 64x32x32 cells (4,194,304 ions)."""
+    wl = I.beam3d(nx=64, ny=32, nz=32, seed=2000)
+    one_step_check(hvmod, wl)
