@@ -461,7 +461,11 @@ __device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, fl
     }
 }
 
-constexpr int kSubThreads = 256;
+// threads per block of the fused subcycle kernel
+#ifndef HV_SUB_THREADS
+#define HV_SUB_THREADS 384
+#endif
+constexpr int kSubThreads = HV_SUB_THREADS;
 
 __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
   using namespace sub2d;

@@ -301,16 +301,20 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 }
 
 // The step's sort: a counting sort of the ions by supercell key.  Counts
-// (warp-aggregated atomics), an exclusive scan of the counts, then every
-// ion is copied once to the next free slot of its key (atomic cursors,
-// warp-aggregated).  Ions of one key keep no particular order among
-// themselves; the deposit sums them in any order.
+// and ranks (warp-aggregated atomics), an exclusive scan of the counts,
+// then every ion is copied once to its key's offset plus its rank.  Ions
+// of one key keep no particular order among themselves (the atomics'
+// order); the deposit sums them in any order.
 // Each warp takes kUnroll consecutive chunks of 32 ions per iteration and
-// issues all their loads (and, in the scatter, all their atomics) before it
+// issues all their loads (and, in the count, all their atomics) before it
 // needs a result, so memory latencies overlap.
 constexpr int kUnroll = 4;
 
-__global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt) {
+// Key counts with warp-aggregated atomics; the value an atomic returns
+// gives every ion its rank among the ions of its key, which the scatter
+// uses to place it without atomics of its own.
+__global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt,
+                                    int32_t *rank) {
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
@@ -321,6 +325,7 @@ __global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32
       const int64_t i = base + 32 * u + lane;
       v[u] = i < n ? vox[i] : 0;
     }
+    int r[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t i = base + 32 * u + lane;
@@ -328,61 +333,40 @@ __global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32
       if (i >= n) continue;
       const int key = ion_key(g, v[u]);
       const unsigned peers = __match_any_sync(act, key);
-      if (lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+      const int leader = __ffs(peers) - 1;
+      int first = 0;
+      if (lane == leader) first = atomicAdd(&cnt[key], __popc(peers));
+      first = __shfl_sync(act, first, leader);
+      r[u] = first + __popc(peers & ((1u << lane) - 1u));
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + 32 * u + lane;
+      if (i < n) rank[i] = r[u];
     }
   }
 }
 
-__global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, int32_t *cursor) {
-  const int lane = threadIdx.x & 31;
+// Copy every ion to off[key] + rank.
+__global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, const int32_t *off,
+                                      const int32_t *rank) {
   const bool has_y = in.oy != nullptr;
-  const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
-  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
-       base < n; base += wstride) {
-    int c[kUnroll];
-    float x[kUnroll], y[kUnroll], z[kUnroll], vx[kUnroll], vy[kUnroll], vz[kUnroll], w[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t i = base + 32 * u + lane;
-      if (i < n) {
-        c[u] = in.cell[i];
-        x[u] = in.ox[i];
-        y[u] = has_y ? in.oy[i] : 0.f;
-        z[u] = in.oz[i];
-        vx[u] = in.vx[i];
-        vy[u] = in.vy[i];
-        vz[u] = in.vz[i];
-        w[u] = in.w[i];
-      }
-    }
-    int dst[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t i = base + 32 * u + lane;
-      const unsigned act = __ballot_sync(kFull, i < n);
-      dst[u] = -1;
-      if (i >= n) continue;
-      const int key = ion_key(g, c[u]);
-      const unsigned peers = __match_any_sync(act, key);
-      const int leader = __ffs(peers) - 1;
-      int first = 0;
-      if (lane == leader) first = atomicAdd(&cursor[key], __popc(peers));
-      first = __shfl_sync(act, first, leader);
-      dst[u] = first + __popc(peers & ((1u << lane) - 1u));
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int d = dst[u];
-      if (d < 0) continue;
-      out.cell[d] = c[u];
-      out.ox[d] = x[u];
-      if (has_y) out.oy[d] = y[u];
-      out.oz[d] = z[u];
-      out.vx[d] = vx[u];
-      out.vy[d] = vy[u];
-      out.vz[d] = vz[u];
-      out.w[d] = w[u];
-    }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int c = in.cell[i];
+    const float x = in.ox[i];
+    const float y = has_y ? in.oy[i] : 0.f;
+    const float z = in.oz[i];
+    const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
+    const int d = __ldg(off + ion_key(g, c)) + rank[i];
+    out.cell[d] = c;
+    out.ox[d] = x;
+    if (has_y) out.oy[d] = y;
+    out.oz[d] = z;
+    out.vx[d] = vx;
+    out.vy[d] = vy;
+    out.vz[d] = vz;
+    out.w[d] = w;
   }
 }
 
@@ -401,31 +385,37 @@ __global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
 
 namespace {
 
-// Per-species key counts and scan sums, allocated at the first sort.
-hv_status bucket_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum) {
+// Per-species key counts, scan sums and ion ranks, allocated at the first
+// sort.
+hv_status bucket_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum,
+                         int32_t **rank) {
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
+  const size_t kb = align256(sizeof(int32_t) * nkeys), bb = align256(sizeof(int32_t) * nb);
   if (!sp.bucket) {
-    sp.bucket_bytes = align256(sizeof(int32_t) * nkeys) + align256(sizeof(int32_t) * nb);
+    sp.bucket_bytes = kb + bb + align256(sizeof(int32_t) * std::max<int64_t>(sp.n, 1));
     sp.bucket = (int32_t *)dev_alloc(sp.bucket_bytes, c->stream);
     if (!sp.bucket) return fail(HV_ENOMEM, "sort scratch allocation failed");
   }
   *cnt = sp.bucket;
-  *bsum = (int32_t *)((char *)sp.bucket + align256(sizeof(int32_t) * nkeys));
+  *bsum = (int32_t *)((char *)sp.bucket + kb);
+  *rank = (int32_t *)((char *)sp.bucket + kb + bb);
   return HV_OK;
 }
 
-// Counts of the live buffer's keys, scanned in place into offsets (the
-// scatter's cursors), and the tile starts taken from them into tile_off.
-cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int *tile_off) {
+// Counts of the live buffer's keys and every ion's rank in its key, the
+// counts scanned in place into offsets, and the tile starts taken from them
+// into tile_off.
+cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int32_t *rank,
+                        int *tile_off) {
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
   const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, c->stream);
   if (e != cudaSuccess) return e;
-  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, sp.buf[sp.cur].cell, sp.n, cnt);
+  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
   chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
   scan_bsum_kernel<<<1, kThreads, 0, c->stream>>>(bsum, nb);
   chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
@@ -440,14 +430,14 @@ cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int
 hv_status sort_species(hv_ctx *c, int sidx) {
   Species &sp = c->sp[sidx];
   if (sp.n <= 1) return HV_OK;
-  int32_t *cnt, *bsum;
-  hv_status st = bucket_reserve(c, sp, &cnt, &bsum);
+  int32_t *cnt, *bsum, *rank;
+  hv_status st = bucket_reserve(c, sp, &cnt, &bsum, &rank);
   if (st != HV_OK) return st;
-  cudaError_t e = key_offsets(c, sp, cnt, bsum, sp.tile_off);
+  cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off);
   if (e != cudaSuccess) return cuda_fail(e, "sort counts");
-  const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
+  const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 64 * 1024);
   bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
-                                                       sp.n, cnt);
+                                                       sp.n, cnt, rank);
   c->launches++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sort");
