@@ -190,21 +190,6 @@ __global__ void load_check_kernel(Geom g, Soa s, int64_t n, int *bad) {
   }
 }
 
-// wrap table: voxel of the interior image of every padded voxel
-std::vector<int> wrap_table(const Geom &g) {
-  std::vector<int> w((size_t)g.npad);
-  const int ny_pad = g.dim2 ? 1 : g.py;
-  for (int Pz = 0; Pz < g.pz; ++Pz)
-    for (int Py = 0; Py < ny_pad; ++Py)
-      for (int Px = 0; Px < g.px; ++Px) {
-        const int i = ((Px - kGhost) % g.nx + g.nx) % g.nx;
-        const int j = g.dim2 ? 0 : ((Py - kGhost) % g.ny + g.ny) % g.ny;
-        const int k = ((Pz - kGhost) % g.nz + g.nz) % g.nz;
-        w[(size_t)Px + (size_t)Py * g.sy + (size_t)Pz * g.sz] = voxel_of(g, i, j, k);
-      }
-  return w;
-}
-
 // component-major [3][ncell] <-> interleaved float4 grids, and the padded
 // gather array's E part
 __global__ void unpack4_kernel(int ncell, const float4 *in, int ncomp, int first, float *out) {
@@ -356,12 +341,12 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->gridpart = (double *)ctx_alloc(c, sizeof(double) * c->grid_blocks * 4);
   c->diag_dev = (double *)ctx_alloc(c, sizeof(double) * 8);
   c->err = (int *)ctx_alloc(c, sizeof(int));
-  c->wrapvox = (int *)ctx_alloc(c, sizeof(int) * npad);
+  c->voxkey = (int *)ctx_alloc(c, sizeof(int) * npad);
   const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
   for (int b = 0; b < 2; ++b)
     c->accm[b] = rec ? (float *)ctx_alloc(c, sizeof(float) * kMono * npad) : nullptr;
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
-      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err || !c->wrapvox ||
+      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err || !c->voxkey ||
       (rec && (!c->accm[0] || !c->accm[1]))) {
     hv_destroy(c);
     return fail(HV_ENOMEM, "grid allocation failed");
@@ -375,8 +360,10 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
   for (int b = 0; b < 2; ++b)
     if (c->accm[b]) cudaMemsetAsync(c->accm[b], 0, sizeof(float) * kMono * npad, c->stream);
-  const std::vector<int> wt = wrap_table(c->g);
-  cudaMemcpyAsync(c->wrapvox, wt.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, c->stream);
+  if (build_voxkey(c) != cudaSuccess) {
+    hv_destroy(c);
+    return fail(HV_ECUDA, "key table");
+  }
   std::vector<float4> hb(nc);
   for (size_t i = 0; i < nc; ++i) {
     if (B0_host) {

@@ -386,6 +386,143 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// One field stage in 3D (Eq. 5 with E from Eqs. 2-4, 6), streamed along z:
+//   B_out = B_base - coef * curl E(B_in)
+// A block owns an S3X x S3Y column of output cells over S3Z planes and walks
+// up the column with a pipeline of planes in shared memory: at each step it
+// loads one plane of B (x-y halo 3), computes J = curl B and p_e one plane
+// behind (halo 2), E two planes behind (halo 1) and B_out three planes
+// behind.  Every plane of B is loaded once per column and the halos are
+// paid only in x and y.
+// ----------------------------------------------------------------------------
+namespace st3d {
+constexpr int X = 32, Y = 8, Z = 16;         // output cells per block
+constexpr int BX = X + 6, BY = Y + 6, NB = BX * BY;  // B plane, halo 3
+constexpr int JX = X + 4, JY = Y + 4, NJ = JX * JY;  // J, p_e plane, halo 2
+constexpr int EX = X + 2, EY = Y + 2, NE = EX * EY;  // E plane, halo 1
+constexpr int kThreads = 256;
+// ring buffers of three planes each
+constexpr int kB = 0;                  // [3][3][NB]
+constexpr int kJ = kB + 9 * NB;        // [3][3][NJ]
+constexpr int kP = kJ + 9 * NJ;        // [3][NJ]
+constexpr int kE = kP + 3 * NJ;        // [3][3][NE]
+constexpr int kFloats = kE + 9 * NE;
+__device__ __forceinline__ int slot(int z) { return ((z % 3) + 3) % 3; }
+}  // namespace st3d
+
+__global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
+  using namespace st3d;
+  extern __shared__ float sm[];
+  const Geom &g = a.g;
+  const FieldConsts &k = a.k;
+  const int ntx = (g.nx + X - 1) / X, nty = (g.ny + Y - 1) / Y;
+  const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
+  const int x0 = bx * X, y0 = by * Y, z0 = bz * Z;
+  auto gidx = [&](int lx, int ly, int z) {
+    const int ii = wrap_near(x0 + lx, g.nx, X + 3);
+    const int jj = wrap_near(y0 + ly, g.ny, Y + 3);
+    const int kk = wrap_near(z, g.nz, Z + 3);
+    return ii + g.nx * (jj + g.ny * kk);
+  };
+  float *Bs = sm + kB, *Js = sm + kJ, *Ps = sm + kP, *Es = sm + kE;
+
+  for (int p = 0; p < Z + 6; ++p) {
+    const int zb = z0 - 3 + p;  // B plane loaded now
+    {
+      float *b = Bs + slot(zb) * 3 * NB;
+      for (int r = threadIdx.x; r < NB; r += kThreads) {
+        const float4 v = a.Bin[gidx(r % BX - 3, r / BX - 3, zb)];
+        b[r] = v.x;
+        b[NB + r] = v.y;
+        b[2 * NB + r] = v.z;
+      }
+    }
+    __syncthreads();
+    const int zj = zb - 1;  // J and p_e plane
+    if (p >= 2) {
+      const float *bm = Bs + slot(zj - 1) * 3 * NB, *b0 = Bs + slot(zj) * 3 * NB,
+                  *bp = Bs + slot(zj + 1) * 3 * NB;
+      float *j = Js + slot(zj) * 3 * NJ;
+      float *pe = Ps + slot(zj) * NJ;
+      for (int r = threadIdx.x; r < NJ; r += kThreads) {
+        const int lx = r % JX - 2, ly = r / JX - 2;
+        const int c = (lx + 3) + (ly + 3) * BX;
+        const float dBz_dy = (b0[2 * NB + c + BX] - b0[2 * NB + c - BX]) * k.idy2;
+        const float dBx_dy = (b0[c + BX] - b0[c - BX]) * k.idy2;
+        const float dBy_dz = (bp[NB + c] - bm[NB + c]) * k.idz2;
+        const float dBx_dz = (bp[c] - bm[c]) * k.idz2;
+        const float dBz_dx = (b0[2 * NB + c + 1] - b0[2 * NB + c - 1]) * k.idx2;
+        const float dBy_dx = (b0[NB + c + 1] - b0[NB + c - 1]) * k.idx2;
+        j[r] = dBz_dy - dBy_dz;
+        j[NJ + r] = dBx_dz - dBz_dx;
+        j[2 * NJ + r] = dBy_dx - dBx_dy;
+        const float f = fmaxf(a.mom[gidx(lx, ly, zj)].x, k.n_floor);
+        pe[r] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
+      }
+    }
+    __syncthreads();
+    const int ze = zj - 1;  // E plane
+    if (p >= 4) {
+      const float *jm = Js + slot(ze - 1) * 3 * NJ, *j0 = Js + slot(ze) * 3 * NJ,
+                  *jp = Js + slot(ze + 1) * 3 * NJ;
+      const float *pm = Ps + slot(ze - 1) * NJ, *p0 = Ps + slot(ze) * NJ,
+                  *pp = Ps + slot(ze + 1) * NJ;
+      const float *b0 = Bs + slot(ze) * 3 * NB;
+      float *e = Es + slot(ze) * 3 * NE;
+      for (int r = threadIdx.x; r < NE; r += kThreads) {
+        const int lx = r % EX - 1, ly = r / EX - 1;
+        const int jc = (lx + 2) + (ly + 2) * JX;
+        const int bc = (lx + 3) + (ly + 3) * BX;
+        const float4 mi = a.mom[gidx(lx, ly, ze)];
+        const float inv = 1.f / fmaxf(mi.x, k.n_floor);
+        const float bxv = b0[bc], byv = b0[NB + bc], bzv = b0[2 * NB + bc];
+        const float jx = j0[jc], jy = j0[NJ + jc], jz = j0[2 * NJ + jc];
+        const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
+        const float gpx = (p0[jc + 1] - p0[jc - 1]) * k.idx2;
+        const float gpy = (p0[jc + JX] - p0[jc - JX]) * k.idy2;
+        const float gpz = (pp[jc] - pm[jc]) * k.idz2;
+        float l[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const float c0 = j0[m * NJ + jc];
+          l[m] = (j0[m * NJ + jc + 1] + j0[m * NJ + jc - 1] - 2.f * c0) * k.ilx +
+                 (j0[m * NJ + jc + JX] + j0[m * NJ + jc - JX] - 2.f * c0) * k.ily +
+                 (jp[m * NJ + jc] + jm[m * NJ + jc] - 2.f * c0) * k.ilz;
+        }
+        e[r] = ((uy * bzv - uz * byv) - gpx) * inv + k.eta * jx - k.eta_h * l[0];
+        e[NE + r] = ((uz * bxv - ux * bzv) - gpy) * inv + k.eta * jy - k.eta_h * l[1];
+        e[2 * NE + r] = ((ux * byv - uy * bxv) - gpz) * inv + k.eta * jz - k.eta_h * l[2];
+      }
+    }
+    __syncthreads();
+    const int zo = ze - 1;  // output plane
+    if (p >= 6) {
+      const float *em = Es + slot(zo - 1) * 3 * NE, *e0 = Es + slot(zo) * 3 * NE,
+                  *ep = Es + slot(zo + 1) * 3 * NE;
+      for (int r = threadIdx.x; r < X * Y; r += kThreads) {
+        const int lx = r % X, ly = r / X;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= g.nx || gy >= g.ny || zo >= g.nz) continue;
+        const int ec = (lx + 1) + (ly + 1) * EX;
+        const float dEz_dy = (e0[2 * NE + ec + EX] - e0[2 * NE + ec - EX]) * k.idy2;
+        const float dEx_dy = (e0[ec + EX] - e0[ec - EX]) * k.idy2;
+        const float dEy_dz = (ep[NE + ec] - em[NE + ec]) * k.idz2;
+        const float dEx_dz = (ep[ec] - em[ec]) * k.idz2;
+        const float dEz_dx = (e0[2 * NE + ec + 1] - e0[2 * NE + ec - 1]) * k.idx2;
+        const float dEy_dx = (e0[NE + ec + 1] - e0[NE + ec - 1]) * k.idx2;
+        const int c = gx + g.nx * (gy + g.ny * zo);
+        const float4 bb = a.Bbase[c];
+        a.Bout[c] = make_float4(bb.x - a.coef * (dEz_dy - dEy_dz),
+                                bb.y - a.coef * (dEx_dz - dEz_dx),
+                                bb.z - a.coef * (dEy_dx - dEx_dy), 0.f);
+      }
+    }
+    // the next step's load overwrites the oldest B plane, last read above
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
 // One whole explicit-midpoint substep in the x-z layout, fused:
 //   B* = B - (h/2) curl E(B),  B_out = B - h curl E(B*)
 // A 32x16 tile of outputs needs B on a halo of 6 cells: each Ohm evaluation
@@ -749,7 +886,20 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   a.coef = coef;
   a.EB = nullptr;
   c->launches++;
-  return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
+  if (c->g.dim2) return launch_stage_t<2, 0>(c, a);
+  const size_t smem = st3d::kFloats * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(stage3d_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const Geom &g = c->g;
+  const int blocks = ((g.nx + st3d::X - 1) / st3d::X) * ((g.ny + st3d::Y - 1) / st3d::Y) *
+                     ((g.nz + st3d::Z - 1) / st3d::Z);
+  stage3d_kernel<<<blocks, st3d::kThreads, smem, c->stream>>>(a);
+  return cudaGetLastError();
 }
 
 bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0; }

@@ -180,7 +180,8 @@ struct hv_ctx {
   float *accm[2];       // padded [npad][kMono] per-cell moment records
                         // (QS in the x-z layout), used alternately
   int accpar;           // record buffer the next deposit writes
-  int *wrapvox;         // padded [npad]: voxel of the interior image
+  int *voxkey;          // padded [npad]: supercell key of each interior voxel
+                        // (the last key for ghost voxels)
   int filter_on;        // learned filter replaces the binomial smoothing
   hv::FilterParams filt;
   // filter training state: FP32 master parameters, Adam moments, gradient,
@@ -249,6 +250,8 @@ int grid_reduce_blocks(int device);
 
 // sort: sorts species `s` of the context by cell (stable), swapping buffers
 hv_status sort_species(hv_ctx *c, int s);
+// Fill c->voxkey.
+cudaError_t build_voxkey(hv_ctx *c);
 // equal split of species s into tile ranges (used before the first sort)
 cudaError_t tile_ranges_even(hv_ctx *c, int s);
 void sort_release(hv_ctx *c);

@@ -55,7 +55,6 @@ struct PushArgs {
   const float4 *EB;
   float4 *acc;       // per-target accumulator
   float *accm;       // per-cell moment records (QS in the x-z layout)
-  const int *wrapvox;
   Geom g;
   PushConsts k;
   double *part;      // [gridDim.x][4]
@@ -781,7 +780,6 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.EB = c->EB;
   a.acc = c->acc;
   a.accm = c->accm[c->accpar];
-  a.wrapvox = c->wrapvox;
   a.g = c->g;
   a.k.qmdt2 = (float)(0.5 * sp.q / sp.m * c->p.dt);
   a.k.cx = c->g.nx > 1 ? (float)(c->p.dt / c->p.dx) : 0.f;
