@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="harris2d",
                     choices=["harris2d", "harris2d_small", "alfven2d", "beam3d_small", "beam3d",
-                             "harris3d", "harris3d_quarter"])
+                             "beam3d_2ppc", "harris3d", "harris3d_quarter"])
     ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
     ap.add_argument("--sort-every", type=int, default=None,
                     help="override the workload's sort interval")
@@ -67,6 +67,8 @@ def make_workload(name, shape, seed_offset=0):
         return I.beam3d(nx=64, ny=64, nz=64, shape=shape, seed=2000 + seed_offset)
     if name == "beam3d":  # 256x128x128 cells, 64 ppc, 268M ions
         return I.beam3d(shape=shape, seed=2000 + seed_offset)
+    if name == "beam3d_2ppc":  # the beam grid with 1 core + 1 beam ion per cell (field kernels)
+        return I.beam3d(n_core=1, n_beam=1, shape=shape, seed=2000 + seed_offset)
     if name == "harris3d":  # 512x256x256 cells, 32 ppc, 1.07e9 ions (slow to generate)
         return I.harris3d(shape=shape, seed=3000 + seed_offset)
     if name == "harris3d_quarter":  # 256x128x128 cells, 32 ppc, 134M ions

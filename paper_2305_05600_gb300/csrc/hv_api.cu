@@ -341,12 +341,11 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->gridpart = (double *)ctx_alloc(c, sizeof(double) * c->grid_blocks * 4);
   c->diag_dev = (double *)ctx_alloc(c, sizeof(double) * 8);
   c->err = (int *)ctx_alloc(c, sizeof(int));
-  c->voxkey = (int *)ctx_alloc(c, sizeof(int) * npad);
   const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
   for (int b = 0; b < 2; ++b)
     c->accm[b] = rec ? (float *)ctx_alloc(c, sizeof(float) * kMono * npad) : nullptr;
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
-      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err || !c->voxkey ||
+      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err ||
       (rec && (!c->accm[0] || !c->accm[1]))) {
     hv_destroy(c);
     return fail(HV_ENOMEM, "grid allocation failed");
@@ -360,10 +359,6 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
   for (int b = 0; b < 2; ++b)
     if (c->accm[b]) cudaMemsetAsync(c->accm[b], 0, sizeof(float) * kMono * npad, c->stream);
-  if (build_voxkey(c) != cudaSuccess) {
-    hv_destroy(c);
-    return fail(HV_ECUDA, "key table");
-  }
   std::vector<float4> hb(nc);
   for (size_t i = 0; i < nc; ++i) {
     if (B0_host) {

@@ -93,10 +93,11 @@ __host__ __device__ __forceinline__ int voxel_of(const Geom &g, int i, int j, in
 }
 
 // Supercell sort key of an ion from its voxel index (tile extents are
-// powers of two); a voxel outside the interior gets the last key, so a
-// corrupt index stays inside the arrays (the push reports it).
+// powers of two).  A voxel that is not an interior cell gets the last key,
+// so a corrupt index stays inside the count arrays (the push reports it).
 __device__ __forceinline__ int ion_key(const Geom &g, int vox) {
-  if (vox < g.vlo || vox >= g.vhi) return (g.ntiles << g.tlog) - 1;
+  const int last = (g.ntiles << g.tlog) - 1;
+  if (vox < g.vlo || vox >= g.vhi) return last;
   const uint32_t v = (uint32_t)vox;
   const uint32_t q = fdiv(v, g.div_px);
   const int i = (int)(v - q * (uint32_t)g.px) - kGhost;
@@ -108,6 +109,9 @@ __device__ __forceinline__ int ion_key(const Geom &g, int vox) {
     j = (int)q - kp * g.py - kGhost;
     k = kp - kGhost;
   }
+  if ((unsigned)i >= (unsigned)g.nx || (unsigned)j >= (unsigned)g.ny ||
+      (unsigned)k >= (unsigned)g.nz)
+    return last;
   const int lx = __ffs(g.tx) - 1, ly = __ffs(g.ty) - 1, lz = __ffs(g.tz) - 1;
   const int tile = (i >> lx) + g.ntx * ((j >> ly) + g.nty * (k >> lz));
   const int local = (i & (g.tx - 1)) + ((j & (g.ty - 1)) << lx) + ((k & (g.tz - 1)) << (lx + ly));
@@ -180,8 +184,6 @@ struct hv_ctx {
   float *accm[2];       // padded [npad][kMono] per-cell moment records
                         // (QS in the x-z layout), used alternately
   int accpar;           // record buffer the next deposit writes
-  int *voxkey;          // padded [npad]: supercell key of each interior voxel
-                        // (the last key for ghost voxels)
   int filter_on;        // learned filter replaces the binomial smoothing
   hv::FilterParams filt;
   // filter training state: FP32 master parameters, Adam moments, gradient,
@@ -250,8 +252,6 @@ int grid_reduce_blocks(int device);
 
 // sort: sorts species `s` of the context by cell (stable), swapping buffers
 hv_status sort_species(hv_ctx *c, int s);
-// Fill c->voxkey.
-cudaError_t build_voxkey(hv_ctx *c);
 // equal split of species s into tile ranges (used before the first sort)
 cudaError_t tile_ranges_even(hv_ctx *c, int s);
 void sort_release(hv_ctx *c);

@@ -305,33 +305,6 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 // then every ion is copied once to its key's offset plus its rank.  Ions
 // of one key keep no particular order among themselves (the atomics'
 // order); the deposit sums them in any order.
-// Supercell key of every padded voxel: interior voxels get their key, ghost
-// voxels (never an ion's cell) the last key, so a corrupt index stays
-// inside the count arrays.
-__global__ void voxkey_kernel(Geom g, int *voxkey) {
-  const int last = (g.ntiles << g.tlog) - 1;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.npad; v += gridDim.x * blockDim.x) {
-    int ip, jp, kp;
-    const int q = v / g.px;
-    ip = v - q * g.px;
-    if (g.dim2) {
-      jp = kGhost;
-      kp = q;
-    } else {
-      kp = q / g.py;
-      jp = q - kp * g.py;
-    }
-    const bool in = ip >= kGhost && ip < kGhost + g.nx && kp >= kGhost && kp < kGhost + g.nz &&
-                    (g.dim2 || (jp >= kGhost && jp < kGhost + g.ny));
-    voxkey[v] = in ? ion_key(g, v) : last;
-  }
-}
-
-// Key of an ion from its stored voxel index through the table.
-__device__ __forceinline__ int key_of(const Geom &g, const int *voxkey, int vox) {
-  return (unsigned)vox < (unsigned)g.npad ? __ldg(voxkey + vox) : (g.ntiles << g.tlog) - 1;
-}
-
 // Each warp takes kUnroll consecutive chunks of 32 ions per iteration and
 // issues all their loads (and, in the count, all their atomics) before it
 // needs a result, so memory latencies overlap.
@@ -340,8 +313,8 @@ constexpr int kUnroll = 4;
 // Key counts with warp-aggregated atomics; the value an atomic returns
 // gives every ion its rank among the ions of its key, which the scatter
 // uses to place it without atomics of its own.
-__global__ void bucket_count_kernel(Geom g, const int *voxkey, const int32_t *vox, int64_t n,
-                                    int32_t *cnt, int32_t *rank) {
+__global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt,
+                                    int32_t *rank) {
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
@@ -350,7 +323,7 @@ __global__ void bucket_count_kernel(Geom g, const int *voxkey, const int32_t *vo
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t i = base + 32 * u + lane;
-      v[u] = i < n ? key_of(g, voxkey, vox[i]) : 0;
+      v[u] = i < n ? vox[i] : 0;
     }
     int r[kUnroll];
 #pragma unroll
@@ -358,7 +331,7 @@ __global__ void bucket_count_kernel(Geom g, const int *voxkey, const int32_t *vo
       const int64_t i = base + 32 * u + lane;
       const unsigned act = __ballot_sync(kFull, i < n);
       if (i >= n) continue;
-      const int key = v[u];
+      const int key = ion_key(g, v[u]);
       const unsigned peers = __match_any_sync(act, key);
       const int leader = __ffs(peers) - 1;
       int first = 0;
@@ -377,8 +350,8 @@ __global__ void bucket_count_kernel(Geom g, const int *voxkey, const int32_t *vo
 // Copy every ion to off[key] + rank.  (Issuing several ions' loads per
 // thread measured no faster: at a sort every few steps the drifted ions
 // make short store segments, and those, not load latency, set the pace.)
-__global__ void bucket_scatter_kernel(Geom g, const int *voxkey, Soa in, Soa out, int64_t n,
-                                      const int32_t *off, const int32_t *rank) {
+__global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, const int32_t *off,
+                                      const int32_t *rank) {
   const bool has_y = in.oy != nullptr;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -387,7 +360,7 @@ __global__ void bucket_scatter_kernel(Geom g, const int *voxkey, Soa in, Soa out
     const float y = has_y ? in.oy[i] : 0.f;
     const float z = in.oz[i];
     const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
-    const int d = __ldg(off + key_of(g, voxkey, c)) + rank[i];
+    const int d = __ldg(off + ion_key(g, c)) + rank[i];
     out.cell[d] = c;
     out.ox[d] = x;
     if (has_y) out.oy[d] = y;
@@ -444,8 +417,7 @@ cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int
   const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, c->stream);
   if (e != cudaSuccess) return e;
-  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, c->voxkey, sp.buf[sp.cur].cell, sp.n,
-                                                     cnt, rank);
+  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
   chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
   scan_bsum_kernel<<<1, kThreads, 0, c->stream>>>(bsum, nb);
   chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
@@ -466,20 +438,13 @@ hv_status sort_species(hv_ctx *c, int sidx) {
   cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off);
   if (e != cudaSuccess) return cuda_fail(e, "sort counts");
   const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 64 * 1024);
-  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(c->g, c->voxkey, sp.buf[sp.cur],
-                                                       sp.buf[sp.cur ^ 1], sp.n, cnt, rank);
+  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
+                                                       sp.n, cnt, rank);
   c->launches++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sort");
   sp.cur ^= 1;
   return HV_OK;
-}
-
-cudaError_t build_voxkey(hv_ctx *c) {
-  voxkey_kernel<<<(int)std::min<int64_t>(((int64_t)c->g.npad + 255) / 256, 16 * 1024), 256, 0,
-                  c->stream>>>(c->g, c->voxkey);
-  c->launches++;
-  return cudaGetLastError();
 }
 
 cudaError_t tile_ranges_even(hv_ctx *c, int s) {
