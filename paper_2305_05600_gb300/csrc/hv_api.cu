@@ -470,6 +470,17 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
   return HV_OK;
 }
 
+// Side stream and events for sorts issued ahead of their step, created on
+// first use.
+static hv_status side_stream(hv_ctx *c) {
+  if (c->side) return HV_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "side stream");
+  return HV_OK;
+}
+
 hv_status hv_step(hv_ctx *c, int32_t nsteps) {
   if (!c) return fail(HV_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(HV_EINVAL, "nsteps must be >= 0");
@@ -486,9 +497,14 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       for (int i = 0; i < 6; ++i) ev.e[i] = prof_event(ps);
       cudaEventRecord(ev.e[0], c->stream);
     }
-    if (c->p.sort_every > 0 && c->step % c->p.sort_every == 0) {
+    const bool sort_now = c->p.sort_every > 0 && c->step % c->p.sort_every == 0;
+    if (c->presorted) {
+      // issued during the previous step's field advance
+      cudaStreamWaitEvent(c->stream, c->ev_sort, 0);
+      c->presorted = 0;
+    } else if (sort_now) {
       for (int sp = 0; sp < c->nspecies; ++sp) {
-        hv_status st = sort_species(c, sp);
+        hv_status st = sort_species(c, sp, c->stream);
         if (st != HV_OK) return st;
       }
     }
@@ -500,6 +516,21 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
     for (int sp = 0; sp < c->nspecies; ++sp) {
       cudaError_t e = launch_push(c, sp, 0);
       if (e != cudaSuccess) return cuda_fail(e, "push");
+    }
+    // The next step's sort needs only the pushed ions, not the fields: when
+    // it is due and runs in this call, issue it now on the side stream so
+    // that it overlaps this step's moment post and field advance.
+    if (s + 1 < nsteps && c->p.sort_every > 0 && (c->step + 1) % c->p.sort_every == 0) {
+      hv_status st = side_stream(c);
+      if (st != HV_OK) return st;
+      cudaEventRecord(c->ev_push, c->stream);
+      cudaStreamWaitEvent(c->side, c->ev_push, 0);
+      for (int sp = 0; sp < c->nspecies; ++sp) {
+        st = sort_species(c, sp, c->side);
+        if (st != HV_OK) return st;
+      }
+      cudaEventRecord(c->ev_sort, c->side);
+      c->presorted = 1;
     }
     if (ps) {
       cudaEventRecord(ev.e[2], c->stream);
@@ -878,6 +909,12 @@ hv_status hv_profile_read(hv_ctx *c, hv_prof_t *out) {
 void hv_destroy(hv_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaEventDestroy(c->ev_push);
+    cudaEventDestroy(c->ev_sort);
+    cudaStreamDestroy(c->side);
+  }
   prof_destroy(c);
   for (int s = 0; s < c->nspecies; ++s) {
     for (int b = 0; b < 2; ++b) dev_free(c->sp[s].base[b], c->sp[s].bytes[b], c->stream);

@@ -176,6 +176,10 @@ struct hv_ctx {
   hv_params p;
   hv::Geom g;
   cudaStream_t stream;
+  cudaStream_t side;    // a sort issued ahead of its step runs here, beside
+                        // the previous step's field advance
+  cudaEvent_t ev_push, ev_sort;
+  int presorted;        // the current step's sort was issued on `side`
   int device;
   double vc;
   // grids (device)
@@ -251,7 +255,9 @@ cudaError_t launch_diag(hv_ctx *c);
 int grid_reduce_blocks(int device);
 
 // sort: sorts species `s` of the context by cell (stable), swapping buffers
-hv_status sort_species(hv_ctx *c, int s);
+// Counting sort of species s on stream st (the scratch is allocated on the
+// first call).
+hv_status sort_species(hv_ctx *c, int s, cudaStream_t st);
 // equal split of species s into tile ranges (used before the first sort)
 cudaError_t tile_ranges_even(hv_ctx *c, int s);
 void sort_release(hv_ctx *c);

@@ -557,8 +557,27 @@ struct Run {
       flush_direct<DIM, SHAPE>(a, pk, cv);
     }
   }
+  // End of a staging tile, called by all 32 lanes: lanes whose open runs
+  // share a key (neighbouring lanes of a sorted tile) sum them with a
+  // segmented shuffle reduction, and one lane per key flushes.
   __device__ __forceinline__ void finish(const PushArgs &a) {
-    if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
+    const int lane = threadIdx.x & 31;
+    const int knext = __shfl_down_sync(kFull, key, 1);
+    const int kprev = __shfl_up_sync(kFull, key, 1);
+    bool cut = lane == 31 || knext != key;  // a segment ends at this lane
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool cut_o = __shfl_down_sync(kFull, cut, o);
+      const bool take = !cut && lane + o < 32;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const float v = __shfl_down_sync(kFull, acc[j], o);
+        if (take) acc[j] += v;
+      }
+      cut = cut || cut_o;
+    }
+    const bool head = lane == 0 || kprev != key;
+    if (head && key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
     key = INT_MIN;
   }
 };
@@ -643,7 +662,8 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
       for (int f = 0; f < NA; ++f)
         bulk_load(T[f], field_ptr<DIM>(a.s, f) + q0 * 16, bytes, bar);
     }
-    if (!mbar_wait_bounded(bar, (uint32_t)(k & 1))) {
+    // the warp gives up together if any lane's bounded wait ran out
+    if (__any_sync(kFull, !mbar_wait_bounded(bar, (uint32_t)(k & 1)))) {
       failed = true;
       mbar_wait_bounded(bar, (uint32_t)(k & 1));  // one more bounded chance
       break;

@@ -410,18 +410,18 @@ hv_status bucket_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum,
 // counts scanned in place into offsets, and the tile starts taken from them
 // into tile_off.
 cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int32_t *rank,
-                        int *tile_off) {
+                        int *tile_off, cudaStream_t st) {
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
   const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, c->stream);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, st);
   if (e != cudaSuccess) return e;
-  bucket_count_kernel<<<blocks, 256, 0, c->stream>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
-  chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
-  scan_bsum_kernel<<<1, kThreads, 0, c->stream>>>(bsum, nb);
-  chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, c->stream>>>(cnt, nkeys, bsum);
-  tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, c->stream>>>(cnt, g.tlog, g.ntiles, sp.n,
+  bucket_count_kernel<<<blocks, 256, 0, st>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
+  chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
+  scan_bsum_kernel<<<1, kThreads, 0, st>>>(bsum, nb);
+  chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
+  tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(cnt, g.tlog, g.ntiles, sp.n,
                                                                      tile_off);
   c->launches += 5;
   return cudaGetLastError();
@@ -429,17 +429,17 @@ cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int
 
 }  // namespace
 
-hv_status sort_species(hv_ctx *c, int sidx) {
+hv_status sort_species(hv_ctx *c, int sidx, cudaStream_t stream) {
   Species &sp = c->sp[sidx];
   if (sp.n <= 1) return HV_OK;
   int32_t *cnt, *bsum, *rank;
   hv_status st = bucket_reserve(c, sp, &cnt, &bsum, &rank);
   if (st != HV_OK) return st;
-  cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off);
+  cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off, stream);
   if (e != cudaSuccess) return cuda_fail(e, "sort counts");
   const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 64 * 1024);
-  bucket_scatter_kernel<<<blocks, 256, 0, c->stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
-                                                       sp.n, cnt, rank);
+  bucket_scatter_kernel<<<blocks, 256, 0, stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
+                                                           sp.n, cnt, rank);
   c->launches++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sort");
