@@ -517,9 +517,16 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       cudaError_t e = launch_push(c, sp, 0);
       if (e != cudaSuccess) return cuda_fail(e, "push");
     }
+    if (ps) {
+      cudaEventRecord(ev.e[2], c->stream);
+      ev.launches[1] = c->launches - l0;
+      l0 = c->launches;
+    }
     // The next step's sort needs only the pushed ions, not the fields: when
     // it is due and runs in this call, issue it now on the side stream so
-    // that it overlaps this step's moment post and field advance.
+    // that it overlaps this step's moment post and field advance.  (Its
+    // launches count as sort launches; its time shows as the slowdown of the
+    // phases it overlaps.)
     if (s + 1 < nsteps && c->p.sort_every > 0 && (c->step + 1) % c->p.sort_every == 0) {
       hv_status st = side_stream(c);
       if (st != HV_OK) return st;
@@ -531,11 +538,10 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       }
       cudaEventRecord(c->ev_sort, c->side);
       c->presorted = 1;
-    }
-    if (ps) {
-      cudaEventRecord(ev.e[2], c->stream);
-      ev.launches[1] = c->launches - l0;
-      l0 = c->launches;
+      if (ps) {
+        ev.launches[0] += c->launches - l0;
+        l0 = c->launches;
+      }
     }
     cudaError_t e = launch_moments(c, 0);
     if (e != cudaSuccess) return cuda_fail(e, "moments");
