@@ -134,10 +134,13 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
  * already loaded; up to 8) with charge q and mass m (q_s = Z_s e, m_s; Sec.
  * 2.1) and n macro-particles: cell[n] int32 in [0, ncell), off3 [3][n]
  * relative coordinates in [-1, 1) (ignored along single-cell axes),
- * v3 [3][n] velocities v^{-1/2}, w[n] weights (Sec. 2.2).  Every value is
- * checked on the host (HV_EINVAL on a bad index, offset or non-finite value);
- * device inputs are copied to the host for the check.  Only before the first
- * step (HV_ESTATE afterwards). */
+ * v3 [3][n] velocities v^{-1/2}, w[n] weights (Sec. 2.2).  The arrays are
+ * copied to the device (on_device != 0: they are device pointers) and every
+ * value is checked there before the call returns (HV_EINVAL on a bad index,
+ * offset or non-finite value; nothing of the species is kept then).  The
+ * library reorders ions as it steps (sorted by cell, any order within a
+ * cell) and copies weights bit for bit.  Only before the first step
+ * (HV_ESTATE afterwards). */
 hv_status hv_load_ions(hv_ctx *ctx, int32_t species, double q, double m, int64_t n,
                        const int32_t *cell, const float *off3, const float *v3,
                        const float *w, int on_device);
