@@ -525,13 +525,13 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int
 }
 
 // A lane's register run: the deposit values summed over consecutive ions
-// with the same deposit key.  For QS and NGP (keys are cells) an ion that
-// left the run's cell is flushed on its own while the run continues; a new
-// run starts only with an ion whose key is its own cell.
+// with the same deposit key.  An ion with another key flushes the run and
+// starts a new one.  (Keeping the run across a single ion that left its
+// cell saves a flush, but the third branch it needs makes the warp issue
+// all three paths on almost every ion.)
 template <int DIM, int SHAPE>
 struct Run {
   static constexpr int NV = Shape<DIM, SHAPE>::NV;
-  static constexpr bool CELLKEY = SHAPE != 2;
   int key;
   float acc[NV];
 
@@ -540,22 +540,15 @@ struct Run {
 #pragma unroll
     for (int j = 0; j < NV; ++j) acc[j] = 0.f;
   }
-  __device__ __forceinline__ void add(const PushArgs &a, int pk, int own,
-                                      const Dep<DIM, SHAPE> &d) {
-    if (pk == key) {
-#pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] = d.fma_into(j, acc[j]);
-    } else if (!CELLKEY || pk == own || key == INT_MIN) {
+  __device__ __forceinline__ void add(const PushArgs &a, int pk, const Dep<DIM, SHAPE> &d) {
+    if (pk != key) {
       if (key != INT_MIN) flush_direct<DIM, SHAPE>(a, key, acc);
       key = pk;
 #pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] = d.value(j);
-    } else {
-      float cv[NV];
-#pragma unroll
-      for (int j = 0; j < NV; ++j) cv[j] = d.value(j);
-      flush_direct<DIM, SHAPE>(a, pk, cv);
+      for (int j = 0; j < NV; ++j) acc[j] = 0.f;
     }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = d.fma_into(j, acc[j]);
   }
   // End of a staging tile, called by all 32 lanes: lanes whose open runs
   // share a key (neighbouring lanes of a sorted tile) sum them with a
@@ -695,12 +688,11 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
 #pragma unroll
       for (int p = 0; p < kGroup; ++p) {
         if (p >= nvalid) continue;
-        const int own = cc[p];
         Dep<DIM, SHAPE> dep;
         const int pk = push_ion<DIM, SHAPE, MODE>(a, eb, i0, j0, k0, cc[p], ox[p], oy[p], oz[p],
                                                   vx[p], vy[p], vz[p], ww[p], dep, rk);
         if (pk == INT_MIN) continue;
-        run.add(a, pk, own, dep);
+        run.add(a, pk, dep);
       }
       if (MODE == 0) {
         stv<kGroup>(&TC[SL::CELL][e0], cc);
