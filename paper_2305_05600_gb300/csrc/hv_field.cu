@@ -535,8 +535,8 @@ constexpr int SX = 32, SZ = 16, SH = 6;
 __host__ __device__ constexpr int W(int r) { return SX + 2 * r; }
 __host__ __device__ constexpr int N(int r) { return (SX + 2 * r) * (SZ + 2 * r); }
 constexpr int kB = 0;                          // B on R6 (3 planes)
-constexpr int kM = kB + 3 * N(6);              // moments on R5 (4 planes: n, Jix, Jiy, Jiz)
-constexpr int kJ = kM + 4 * N(5);              // J on R5 (stage 1) / R2 (stage 2)
+constexpr int kM = kB + 3 * N(6);              // on R5: p_e, 1/n_f, Jix, Jiy, Jiz
+constexpr int kJ = kM + 5 * N(5);              // J on R5 (stage 1) / R2 (stage 2)
 constexpr int kE = kJ + 3 * N(5);              // E on R4 (stage 1) / R1 (stage 2)
 constexpr int kS = kE + 3 * N(4);              // B* on R3
 constexpr int kFloats = kS + 3 * N(3);
@@ -552,21 +552,17 @@ struct SubArgs {
   float h;
 };
 
-// E from Ohm's law at tile point (x, z), with B, J on their own regions.
+// E from Ohm's law at tile point (x, z), with B, J on their own regions and
+// p_e, 1/n_f and J_i per cell on R5 (computed once per cell at load).
 __device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int x, int z,
                                       const float *Bp, int rb, const float *Jp, int rj,
                                       float &ex, float &ey, float &ez) {
   using namespace sub2d;
   const int nb = N(rb), nj = N(rj), nm = N(5);
-  const float *mn = sm + kM, *mjx = mn + nm, *mjy = mjx + nm, *mjz = mjy + nm;
+  const float *pe = sm + kM, *invn = pe + nm, *mjx = invn + nm, *mjy = mjx + nm, *mjz = mjy + nm;
   const int im = at(5, x, z);
-  const float n0 = fmaxf(mn[im], k.n_floor);
-  auto pe = [&](int i) {
-    const float f = fmaxf(mn[i], k.n_floor);
-    return k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
-  };
-  const float gpx = (pe(im + 1) - pe(im - 1)) * k.idx2;
-  const float gpz = (pe(im + W(5)) - pe(im - W(5))) * k.idz2;
+  const float gpx = (pe[im + 1] - pe[im - 1]) * k.idx2;
+  const float gpz = (pe[im + W(5)] - pe[im - W(5)]) * k.idz2;
   const int ij = at(rj, x, z), wj = W(rj);
   const float *Jx = Jp, *Jy = Jp + nj, *Jz = Jp + 2 * nj;
   const float jx = Jx[ij], jy = Jy[ij], jz = Jz[ij];
@@ -576,7 +572,7 @@ __device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int
   const int ib = at(rb, x, z);
   const float bx = Bp[ib], by = Bp[nb + ib], bz = Bp[2 * nb + ib];
   const float ux = jx - mjx[im], uy = jy - mjy[im], uz = jz - mjz[im];
-  const float inv = 1.f / n0;
+  const float inv = invn[im];
   ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx;
   ey = (uz * bx - ux * bz) * inv + k.eta * jy - k.eta_h * ly;
   ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz;
@@ -647,11 +643,13 @@ __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
     for (int u = 0; u < LM; ++u) {
       const int t_ = (int)threadIdx.x + u * kSubThreads;
       if (t_ < N(5)) {
-        const int i = at(5, t_ % W(5) - 5, t_ / W(5) - 5);
-        Mp[i] = mv[u].x;
-        Mp[N(5) + i] = mv[u].y;
-        Mp[2 * N(5) + i] = mv[u].z;
-        Mp[3 * N(5) + i] = mv[u].w;
+        // p_e and 1/n_f once per cell (the floor enters both, Sec. 2.1)
+        const float f = fmaxf(mv[u].x, k.n_floor);
+        Mp[t_] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
+        Mp[N(5) + t_] = __frcp_rn(f);
+        Mp[2 * N(5) + t_] = mv[u].y;
+        Mp[3 * N(5) + t_] = mv[u].z;
+        Mp[4 * N(5) + t_] = mv[u].w;
       }
     }
   }
