@@ -412,26 +412,58 @@ __device__ __forceinline__ int slot(int z) { return ((z % 3) + 3) % 3; }
 
 __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
   using namespace st3d;
+  // cells per thread in each plane region; a thread keeps the x-y part of
+  // its cells' global offsets, so a plane adds only its z offset
+  constexpr int LB = (NB + kThreads - 1) / kThreads;
+  constexpr int LJ = (NJ + kThreads - 1) / kThreads;
+  constexpr int LE = (NE + kThreads - 1) / kThreads;
+  constexpr int LO = (X * Y + kThreads - 1) / kThreads;
   extern __shared__ float sm[];
   const Geom &g = a.g;
   const FieldConsts &k = a.k;
   const int ntx = (g.nx + X - 1) / X, nty = (g.ny + Y - 1) / Y;
   const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
   const int x0 = bx * X, y0 = by * Y, z0 = bz * Z;
-  auto gidx = [&](int lx, int ly, int z) {
-    const int ii = wrap_near(x0 + lx, g.nx, X + 3);
-    const int jj = wrap_near(y0 + ly, g.ny, Y + 3);
-    const int kk = wrap_near(z, g.nz, Z + 3);
-    return ii + g.nx * (jj + g.ny * kk);
+  const int t = threadIdx.x;
+  const int sxy = g.nx * g.ny;
+  auto xy = [&](int lx, int ly) {
+    return wrap_near(x0 + lx, g.nx, X + 3) + g.nx * wrap_near(y0 + ly, g.ny, Y + 3);
   };
+  auto zoff = [&](int z) { return sxy * wrap_near(z, g.nz, Z + 3); };
+  int xb[LB], xj[LJ], xe[LE], xo[LO];
+#pragma unroll
+  for (int u = 0; u < LB; ++u) {
+    const int r = t + u * kThreads;
+    xb[u] = r < NB ? xy(r % BX - 3, r / BX - 3) : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < LJ; ++u) {
+    const int r = t + u * kThreads;
+    xj[u] = r < NJ ? xy(r % JX - 2, r / JX - 2) : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < LE; ++u) {
+    const int r = t + u * kThreads;
+    xe[u] = r < NE ? xy(r % EX - 1, r / EX - 1) : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < LO; ++u) {
+    const int r = t + u * kThreads;
+    const int gx = x0 + r % X, gy = y0 + r / X;
+    xo[u] = (r < X * Y && gx < g.nx && gy < g.ny) ? gx + g.nx * gy : -1;
+  }
   float *Bs = sm + kB, *Js = sm + kJ, *Ps = sm + kP, *Es = sm + kE;
 
   for (int p = 0; p < Z + 6; ++p) {
     const int zb = z0 - 3 + p;  // B plane loaded now
     {
       float *b = Bs + slot(zb) * 3 * NB;
-      for (int r = threadIdx.x; r < NB; r += kThreads) {
-        const float4 v = a.Bin[gidx(r % BX - 3, r / BX - 3, zb)];
+      const int zo_ = zoff(zb);
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int r = t + u * kThreads;
+        if (r >= NB) continue;
+        const float4 v = a.Bin[xb[u] + zo_];
         b[r] = v.x;
         b[NB + r] = v.y;
         b[2 * NB + r] = v.z;
@@ -444,9 +476,12 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
                   *bp = Bs + slot(zj + 1) * 3 * NB;
       float *j = Js + slot(zj) * 3 * NJ;
       float *pe = Ps + slot(zj) * NJ;
-      for (int r = threadIdx.x; r < NJ; r += kThreads) {
-        const int lx = r % JX - 2, ly = r / JX - 2;
-        const int c = (lx + 3) + (ly + 3) * BX;
+      const int zo_ = zoff(zj);
+#pragma unroll
+      for (int u = 0; u < LJ; ++u) {
+        const int r = t + u * kThreads;
+        if (r >= NJ) continue;
+        const int c = (r % JX + 1) + (r / JX + 1) * BX;
         const float dBz_dy = (b0[2 * NB + c + BX] - b0[2 * NB + c - BX]) * k.idy2;
         const float dBx_dy = (b0[c + BX] - b0[c - BX]) * k.idy2;
         const float dBy_dz = (bp[NB + c] - bm[NB + c]) * k.idz2;
@@ -456,7 +491,7 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
         j[r] = dBz_dy - dBy_dz;
         j[NJ + r] = dBx_dz - dBz_dx;
         j[2 * NJ + r] = dBy_dx - dBx_dy;
-        const float f = fmaxf(a.mom[gidx(lx, ly, zj)].x, k.n_floor);
+        const float f = fmaxf(a.mom[xj[u] + zo_].x, k.n_floor);
         pe[r] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
       }
     }
@@ -469,12 +504,16 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
                   *pp = Ps + slot(ze + 1) * NJ;
       const float *b0 = Bs + slot(ze) * 3 * NB;
       float *e = Es + slot(ze) * 3 * NE;
-      for (int r = threadIdx.x; r < NE; r += kThreads) {
-        const int lx = r % EX - 1, ly = r / EX - 1;
-        const int jc = (lx + 2) + (ly + 2) * JX;
-        const int bc = (lx + 3) + (ly + 3) * BX;
-        const float4 mi = a.mom[gidx(lx, ly, ze)];
-        const float inv = 1.f / fmaxf(mi.x, k.n_floor);
+      const int zo_ = zoff(ze);
+#pragma unroll
+      for (int u = 0; u < LE; ++u) {
+        const int r = t + u * kThreads;
+        if (r >= NE) continue;
+        const int rx = r % EX, ry = r / EX;
+        const int jc = (rx + 1) + (ry + 1) * JX;
+        const int bc = (rx + 2) + (ry + 2) * BX;
+        const float4 mi = a.mom[xe[u] + zo_];
+        const float inv = __frcp_rn(fmaxf(mi.x, k.n_floor));
         const float bxv = b0[bc], byv = b0[NB + bc], bzv = b0[2 * NB + bc];
         const float jx = j0[jc], jy = j0[NJ + jc], jz = j0[2 * NJ + jc];
         const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
@@ -496,24 +535,24 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
     }
     __syncthreads();
     const int zo = ze - 1;  // output plane
-    if (p >= 6) {
+    if (p >= 6 && zo < g.nz) {
       const float *em = Es + slot(zo - 1) * 3 * NE, *e0 = Es + slot(zo) * 3 * NE,
                   *ep = Es + slot(zo + 1) * 3 * NE;
-      for (int r = threadIdx.x; r < X * Y; r += kThreads) {
-        const int lx = r % X, ly = r / X;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= g.nx || gy >= g.ny || zo >= g.nz) continue;
-        const int ec = (lx + 1) + (ly + 1) * EX;
+      const int zo_ = sxy * zo;
+#pragma unroll
+      for (int u = 0; u < LO; ++u) {
+        const int r = t + u * kThreads;
+        if (xo[u] < 0) continue;
+        const int ec = (r % X + 1) + (r / X + 1) * EX;
         const float dEz_dy = (e0[2 * NE + ec + EX] - e0[2 * NE + ec - EX]) * k.idy2;
         const float dEx_dy = (e0[ec + EX] - e0[ec - EX]) * k.idy2;
         const float dEy_dz = (ep[NE + ec] - em[NE + ec]) * k.idz2;
         const float dEx_dz = (ep[ec] - em[ec]) * k.idz2;
         const float dEz_dx = (e0[2 * NE + ec + 1] - e0[2 * NE + ec - 1]) * k.idx2;
         const float dEy_dx = (e0[NE + ec + 1] - e0[NE + ec - 1]) * k.idx2;
-        const int c = gx + g.nx * (gy + g.ny * zo);
+        const int c = xo[u] + zo_;
         const float4 bb = a.Bbase[c];
-        a.Bout[c] = make_float4(bb.x - a.coef * (dEz_dy - dEy_dz),
-                                bb.y - a.coef * (dEx_dz - dEz_dx),
+        a.Bout[c] = make_float4(bb.x - a.coef * (dEz_dy - dEy_dz), bb.y - a.coef * (dEx_dz - dEz_dx),
                                 bb.z - a.coef * (dEy_dx - dEx_dy), 0.f);
       }
     }
