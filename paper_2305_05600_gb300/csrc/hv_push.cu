@@ -298,6 +298,41 @@ static_assert(kGroup == 4 || kGroup == 2, "ion group: 4 or 2");
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// One window cell of E and B in shared memory.  The x-z layout keeps the
+// gather array's two float4 ({Ex,Ey,Ez,Bx}, {By,Bz,-,-}); 3D packs the six
+// values into three float2 so that the larger 3D window leaves room for a
+// third block per SM.
+template <int DIM>
+struct WinCell {
+  static constexpr int kBytes = DIM == 2 ? 32 : 24;
+  __device__ __forceinline__ static void store(void *win, int c, float4 e0, float4 e1) {
+    if (DIM == 2) {
+      float4 *w = reinterpret_cast<float4 *>(win);
+      w[2 * c] = e0;
+      w[2 * c + 1] = e1;
+    } else {
+      float2 *w = reinterpret_cast<float2 *>(win);
+      w[3 * c] = make_float2(e0.x, e0.y);
+      w[3 * c + 1] = make_float2(e0.z, e0.w);
+      w[3 * c + 2] = make_float2(e1.x, e1.y);
+    }
+  }
+  // E and B of cell c: {Ex, Ey, Ez, Bx} and {By, Bz}
+  __device__ __forceinline__ static void load(const void *win, int c, float4 &e0, float2 &e1) {
+    if (DIM == 2) {
+      const float4 *w = reinterpret_cast<const float4 *>(win);
+      e0 = w[2 * c];
+      const float4 b = w[2 * c + 1];
+      e1 = make_float2(b.x, b.y);
+    } else {
+      const float2 *w = reinterpret_cast<const float2 *>(win);
+      const float2 a = w[3 * c], b = w[3 * c + 1];
+      e0 = make_float4(a.x, a.y, b.x, b.y);
+      e1 = w[3 * c + 2];
+    }
+  }
+};
+
 // Shared-memory layout of one push block (one supercell tile).
 //   stage: one kTile-ion staging buffer per warp (bulk-copied in and out)
 //   eb:    E, B of the window, 2 float4 per cell
@@ -307,7 +342,7 @@ struct Layout {
   static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
   static constexpr size_t stage_bytes = (size_t)NA * kTile * 4;
   static constexpr size_t off_eb = align_up(stage_bytes * NW, 16);
-  static constexpr size_t off_bar = off_eb + (size_t)Win<DIM>::NEB * 32;
+  static constexpr size_t off_bar = off_eb + (size_t)Win<DIM>::NEB * WinCell<DIM>::kBytes;
   static constexpr size_t bytes = off_bar + 8 * NW;
 };
 
@@ -381,7 +416,7 @@ __device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, in
 // position.  Returns the voxel of the deposit key, or INT_MIN for a corrupt
 // cell index (latched in the error word; the ion is left as it is).
 template <int DIM, int SHAPE, int MODE>
-__device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int i0, int j0,
+__device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i0, int j0,
                                         int k0, int &vox, float &ox, float &oy, float &oz,
                                         float &vx, float &vy, float &vz, float w,
                                         Dep<DIM, SHAPE> &dep, float *rk) {
@@ -430,8 +465,9 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const float4 *eb, int
         else
           wo = DIM == 2 ? (t & 1) + ((t >> 1) & 1) * W::EX
                         : (t & 1) + ((t >> 1) & 1) * W::EX + ((t >> 2) & 1) * W::EX * W::EY;
-        const float4 f0 = eb[2 * (eb0 + wo)];
-        const float4 f1 = eb[2 * (eb0 + wo) + 1];
+        float4 f0;
+        float2 f1;
+        WinCell<DIM>::load(eb, eb0 + wo, f0, f1);
         ex = fmaf(wt[t], f0.x, ex);
         ey = fmaf(wt[t], f0.y, ey);
         ez = fmaf(wt[t], f0.z, ez);
@@ -606,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   constexpr int nwarps = kThreads / 32;
   float(&T)[NA][kTile] = *reinterpret_cast<float(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
   int(&TC)[NA][kTile] = *reinterpret_cast<int(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
-  float4 *eb = reinterpret_cast<float4 *>(smem_raw + L::off_eb);
+  void *eb = smem_raw + L::off_eb;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L::off_bar) + warp;
 
   // tile origin and the block's range of quads: kPushSplit blocks share a
@@ -628,8 +664,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
       if (ip < 0 || ip >= g.px || kp < 0 || kp >= g.pz || (DIM == 3 && (jp < 0 || jp >= g.py)))
         continue;  // outside the padded grid: never read by an in-window ion
       const int v = ip + (DIM == 2 ? 0 : jp * g.sy) + kp * g.sz;
-      eb[2 * c] = __ldg(a.EB + 2 * v);
-      eb[2 * c + 1] = __ldg(a.EB + 2 * v + 1);
+      WinCell<DIM>::store(eb, c, __ldg(a.EB + 2 * v), __ldg(a.EB + 2 * v + 1));
     }
   }
   if (lane == 0) {
