@@ -388,29 +388,57 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
 // ----------------------------------------------------------------------------
 // One field stage in 3D (Eq. 5 with E from Eqs. 2-4, 6), streamed along z:
 //   B_out = B_base - coef * curl E(B_in)
-// A block owns an S3X x S3Y column of output cells over S3Z planes and walks
-// up the column with a pipeline of planes in shared memory: at each step it
-// loads one plane of B (x-y halo 3), computes J = curl B and p_e one plane
-// behind (halo 2), E two planes behind (halo 1) and B_out three planes
-// behind.  Every plane of B is loaded once per column and the halos are
-// paid only in x and y.
+// A block owns an X x Y column of output cells over Z planes and walks up
+// the column.  At step q it computes J = curl B on plane zj = z0 - 2 + q
+// (x-y halo 2), E two planes behind (halo 1) and B_out two planes behind
+// that, so every plane a step reads was written in an earlier step: one
+// barrier per step suffices.  The planes of B (halo 3) and of the ion
+// moments are fetched one step ahead with asynchronous copies into ring
+// buffers, so no global load waits inside a step; only B_base is read from
+// global memory, issued before the barrier.  Every plane of B is loaded
+// once per column and the halos are paid only in x and y.
 // ----------------------------------------------------------------------------
+#ifndef HV_ST3D_Z
+#define HV_ST3D_Z 16
+#endif
+#ifndef HV_ST3D_THREADS
+#define HV_ST3D_THREADS 384
+#endif
 namespace st3d {
-constexpr int X = 32, Y = 8, Z = 16;         // output cells per block
+constexpr int X = 32, Y = 8, Z = HV_ST3D_Z;  // output cells per block
 constexpr int BX = X + 6, BY = Y + 6, NB = BX * BY;  // B plane, halo 3
-constexpr int JX = X + 4, JY = Y + 4, NJ = JX * JY;  // J, p_e plane, halo 2
+constexpr int JX = X + 4, JY = Y + 4, NJ = JX * JY;  // J and n plane, halo 2
 constexpr int EX = X + 2, EY = Y + 2, NE = EX * EY;  // E plane, halo 1
-constexpr int kThreads = 256;
-// ring buffers of three planes each
-constexpr int kB = 0;                  // [3][3][NB]
-constexpr int kJ = kB + 9 * NB;        // [3][3][NJ]
-constexpr int kP = kJ + 9 * NJ;        // [3][NJ]
-constexpr int kE = kP + 3 * NJ;        // [3][3][NE]
-constexpr int kFloats = kE + 9 * NE;
-__device__ __forceinline__ int slot(int z) { return ((z % 3) + 3) % 3; }
+constexpr int kThreads = HV_ST3D_THREADS;
+// ring depths: B planes zj-2..zj+2 (E reads zj-2, J zj-1..zj+1, the copy
+// fills zj+2); J, n and E each hold three planes being read and one being
+// written; the moment float4 at E cells one read and one in flight
+constexpr int kRB = 5, kRJ = 4, kRN = 4, kRM = 2, kRE = 4;
+constexpr int kB = 0;                    // [kRB][3][NB]
+constexpr int kJ = kB + kRB * 3 * NB;    // [kRJ][3][NJ]
+constexpr int kN = kJ + kRJ * 3 * NJ;    // [kRN][NJ]   ion density n
+constexpr int kM = kN + kRN * NJ;        // [kRM][NE]   {n, Jix, Jiy, Jiz} as float4
+constexpr int kE = kM + kRM * 4 * NE;    // [kRE][3][NE]
+constexpr int kFloats = kE + kRE * 3 * NE;
+static_assert(kM % 4 == 0, "moment ring must be 16-byte aligned");
 }  // namespace st3d
 
-__global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a) {
   using namespace st3d;
   // cells per thread in each plane region; a thread keeps the x-y part of
   // its cells' global offsets, so a plane adds only its z offset
@@ -418,7 +446,7 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
   constexpr int LJ = (NJ + kThreads - 1) / kThreads;
   constexpr int LE = (NE + kThreads - 1) / kThreads;
   constexpr int LO = (X * Y + kThreads - 1) / kThreads;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const Geom &g = a.g;
   const FieldConsts &k = a.k;
   const int ntx = (g.nx + X - 1) / X, nty = (g.ny + Y - 1) / Y;
@@ -429,7 +457,9 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
   auto xy = [&](int lx, int ly) {
     return wrap_near(x0 + lx, g.nx, X + 3) + g.nx * wrap_near(y0 + ly, g.ny, Y + 3);
   };
-  auto zoff = [&](int z) { return sxy * wrap_near(z, g.nz, Z + 3); };
+  auto zoff = [&](int z) { return sxy * wrap_near(z, g.nz, Z + 6); };
+  // ring slot of plane z (planes start at z0 - 5, so the index is >= 0)
+  auto slot = [&](int z, int depth) { return (z - z0 + 8) % depth; };
   int xb[LB], xj[LJ], xe[LE], xo[LO];
 #pragma unroll
   for (int u = 0; u < LB; ++u) {
@@ -452,31 +482,70 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
     const int gx = x0 + r % X, gy = y0 + r / X;
     xo[u] = (r < X * Y && gx < g.nx && gy < g.ny) ? gx + g.nx * gy : -1;
   }
-  float *Bs = sm + kB, *Js = sm + kJ, *Ps = sm + kP, *Es = sm + kE;
-
-  for (int p = 0; p < Z + 6; ++p) {
-    const int zb = z0 - 3 + p;  // B plane loaded now
-    {
-      float *b = Bs + slot(zb) * 3 * NB;
-      const int zo_ = zoff(zb);
+  auto copy_B = [&](int z) {
+    float *b = sm + kB + slot(z, kRB) * 3 * NB;
+    const int zo_ = zoff(z);
 #pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int r = t + u * kThreads;
-        if (r >= NB) continue;
-        const float4 v = a.Bin[xb[u] + zo_];
-        b[r] = v.x;
-        b[NB + r] = v.y;
-        b[2 * NB + r] = v.z;
-      }
+    for (int u = 0; u < LB; ++u) {
+      const int r = t + u * kThreads;
+      if (r >= NB) continue;
+      const float *src = reinterpret_cast<const float *>(a.Bin + (xb[u] + zo_));
+      cp_async4(b + r, src);
+      cp_async4(b + NB + r, src + 1);
+      cp_async4(b + 2 * NB + r, src + 2);
     }
+  };
+  auto copy_n = [&](int z) {
+    float *nn = sm + kN + slot(z, kRN) * NJ;
+    const int zo_ = zoff(z);
+#pragma unroll
+    for (int u = 0; u < LJ; ++u) {
+      const int r = t + u * kThreads;
+      if (r < NJ) cp_async4(nn + r, reinterpret_cast<const float *>(a.mom + (xj[u] + zo_)));
+    }
+  };
+  auto copy_m = [&](int z) {
+    float4 *m = reinterpret_cast<float4 *>(sm + kM) + slot(z, kRM) * NE;
+    const int zo_ = zoff(z);
+#pragma unroll
+    for (int u = 0; u < LE; ++u) {
+      const int r = t + u * kThreads;
+      if (r < NE) cp_async16(m + r, a.mom + (xe[u] + zo_));
+    }
+  };
+  // electron pressure p_e(n) with the density floor (Eq. 4)
+  auto pe = [&](float n) {
+    const float f = fmaxf(n, k.n_floor);
+    return k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
+  };
+
+  copy_B(z0 - 3);
+  copy_B(z0 - 2);
+  copy_B(z0 - 1);
+  cp_async_commit();
+  for (int q = 0; q < Z + 6; ++q) {
+    const int zj = z0 - 2 + q, ze = zj - 2, zo = ze - 2;
+    const bool out_on = q >= 6 && zo < g.nz;
+    // B_base of the output plane: only this thread reads or writes these
+    // cells, so the load may precede the barrier even when B_out == B_base
+    float4 bb[LO];
+#pragma unroll
+    for (int u = 0; u < LO; ++u)
+      bb[u] = (out_on && xo[u] >= 0) ? a.Bbase[xo[u] + sxy * zo] : make_float4(0.f, 0.f, 0.f, 0.f);
+    cp_async_wait_all();
     __syncthreads();
-    const int zj = zb - 1;  // J and p_e plane
-    if (p >= 2) {
-      const float *bm = Bs + slot(zj - 1) * 3 * NB, *b0 = Bs + slot(zj) * 3 * NB,
-                  *bp = Bs + slot(zj + 1) * 3 * NB;
-      float *j = Js + slot(zj) * 3 * NJ;
-      float *pe = Ps + slot(zj) * NJ;
-      const int zo_ = zoff(zj);
+    // one step ahead: B for the next J plane, n and the moments for the
+    // next E plane
+    if (q <= Z + 2) copy_B(zj + 2);
+    if (q <= Z + 3) copy_n(zj);
+    if (q >= 2 && q <= Z + 3) copy_m(ze + 1);
+    cp_async_commit();
+
+    if (q <= Z + 3) {  // J = curl B on plane zj
+      const float *bm = sm + kB + slot(zj - 1, kRB) * 3 * NB;
+      const float *b0 = sm + kB + slot(zj, kRB) * 3 * NB;
+      const float *bp = sm + kB + slot(zj + 1, kRB) * 3 * NB;
+      float *j = sm + kJ + slot(zj, kRJ) * 3 * NJ;
 #pragma unroll
       for (int u = 0; u < LJ; ++u) {
         const int r = t + u * kThreads;
@@ -491,20 +560,18 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
         j[r] = dBz_dy - dBy_dz;
         j[NJ + r] = dBx_dz - dBz_dx;
         j[2 * NJ + r] = dBy_dx - dBx_dy;
-        const float f = fmaxf(a.mom[xj[u] + zo_].x, k.n_floor);
-        pe[r] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
       }
     }
-    __syncthreads();
-    const int ze = zj - 1;  // E plane
-    if (p >= 4) {
-      const float *jm = Js + slot(ze - 1) * 3 * NJ, *j0 = Js + slot(ze) * 3 * NJ,
-                  *jp = Js + slot(ze + 1) * 3 * NJ;
-      const float *pm = Ps + slot(ze - 1) * NJ, *p0 = Ps + slot(ze) * NJ,
-                  *pp = Ps + slot(ze + 1) * NJ;
-      const float *b0 = Bs + slot(ze) * 3 * NB;
-      float *e = Es + slot(ze) * 3 * NE;
-      const int zo_ = zoff(ze);
+    if (q >= 3 && q <= Z + 4) {  // E from Ohm's law on plane ze
+      const float *jm = sm + kJ + slot(ze - 1, kRJ) * 3 * NJ;
+      const float *j0 = sm + kJ + slot(ze, kRJ) * 3 * NJ;
+      const float *jp = sm + kJ + slot(ze + 1, kRJ) * 3 * NJ;
+      const float *nm = sm + kN + slot(ze - 1, kRN) * NJ;
+      const float *n0 = sm + kN + slot(ze, kRN) * NJ;
+      const float *np = sm + kN + slot(ze + 1, kRN) * NJ;
+      const float4 *m0 = reinterpret_cast<const float4 *>(sm + kM) + slot(ze, kRM) * NE;
+      const float *b0 = sm + kB + slot(ze, kRB) * 3 * NB;
+      float *e = sm + kE + slot(ze, kRE) * 3 * NE;
 #pragma unroll
       for (int u = 0; u < LE; ++u) {
         const int r = t + u * kThreads;
@@ -512,14 +579,14 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
         const int rx = r % EX, ry = r / EX;
         const int jc = (rx + 1) + (ry + 1) * JX;
         const int bc = (rx + 2) + (ry + 2) * BX;
-        const float4 mi = a.mom[xe[u] + zo_];
+        const float4 mi = m0[r];
         const float inv = __frcp_rn(fmaxf(mi.x, k.n_floor));
         const float bxv = b0[bc], byv = b0[NB + bc], bzv = b0[2 * NB + bc];
         const float jx = j0[jc], jy = j0[NJ + jc], jz = j0[2 * NJ + jc];
         const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
-        const float gpx = (p0[jc + 1] - p0[jc - 1]) * k.idx2;
-        const float gpy = (p0[jc + JX] - p0[jc - JX]) * k.idy2;
-        const float gpz = (pp[jc] - pm[jc]) * k.idz2;
+        const float gpx = (pe(n0[jc + 1]) - pe(n0[jc - 1])) * k.idx2;
+        const float gpy = (pe(n0[jc + JX]) - pe(n0[jc - JX])) * k.idy2;
+        const float gpz = (pe(np[jc]) - pe(nm[jc])) * k.idz2;
         float l[3];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
@@ -533,11 +600,10 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
         e[2 * NE + r] = ((ux * byv - uy * bxv) - gpz) * inv + k.eta * jz - k.eta_h * l[2];
       }
     }
-    __syncthreads();
-    const int zo = ze - 1;  // output plane
-    if (p >= 6 && zo < g.nz) {
-      const float *em = Es + slot(zo - 1) * 3 * NE, *e0 = Es + slot(zo) * 3 * NE,
-                  *ep = Es + slot(zo + 1) * 3 * NE;
+    if (out_on) {  // B_out = B_base - coef * curl E on plane zo
+      const float *em = sm + kE + slot(zo - 1, kRE) * 3 * NE;
+      const float *e0 = sm + kE + slot(zo, kRE) * 3 * NE;
+      const float *ep = sm + kE + slot(zo + 1, kRE) * 3 * NE;
       const int zo_ = sxy * zo;
 #pragma unroll
       for (int u = 0; u < LO; ++u) {
@@ -550,14 +616,11 @@ __global__ void __launch_bounds__(st3d::kThreads) stage3d_kernel(StageArgs a) {
         const float dEx_dz = (ep[ec] - em[ec]) * k.idz2;
         const float dEz_dx = (e0[2 * NE + ec + 1] - e0[2 * NE + ec - 1]) * k.idx2;
         const float dEy_dx = (e0[NE + ec + 1] - e0[NE + ec - 1]) * k.idx2;
-        const int c = xo[u] + zo_;
-        const float4 bb = a.Bbase[c];
-        a.Bout[c] = make_float4(bb.x - a.coef * (dEz_dy - dEy_dz), bb.y - a.coef * (dEx_dz - dEz_dx),
-                                bb.z - a.coef * (dEy_dx - dEx_dy), 0.f);
+        a.Bout[xo[u] + zo_] =
+            make_float4(bb[u].x - a.coef * (dEz_dy - dEy_dz), bb[u].y - a.coef * (dEx_dz - dEz_dx),
+                        bb[u].z - a.coef * (dEy_dx - dEx_dy), 0.f);
       }
     }
-    // the next step's load overwrites the oldest B plane, last read above
-    __syncthreads();
   }
 }
 

@@ -654,6 +654,24 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   const int64_t nq = (a.n + 3) >> 2;
   const int64_t qa = tile == 0 ? 0 : (int64_t)a.tile_off[tile] >> 2;
   const int64_t qe = tile == g.ntiles - 1 ? nq : (int64_t)a.tile_off[tile + 1] >> 2;
+  const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles of the tile
+  const int64_t st_lo = nst * part / kPushSplit, st_hi = nst * (part + 1) / kPushSplit;
+
+  // bulk loads of staging tile st into the warp's buffer
+  auto issue = [&](int64_t st) {
+    const int64_t q0 = qa + st * TQ;
+    const uint32_t bytes = (uint32_t)min((int64_t)TQ, qe - q0) * 16u;
+    mbar_expect_tx(bar, bytes * NA);
+#pragma unroll
+    for (int f = 0; f < NA; ++f) bulk_load(T[f], field_ptr<DIM>(a.s, f) + q0 * 16, bytes, bar);
+  };
+  // the warp's first staging tile is requested before the window is staged,
+  // so that the two loads overlap
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (st_lo + warp < st_hi) issue(st_lo + warp);
+  }
 
   // stage E, B of the window
   if (MODE == 0) {
@@ -667,28 +685,18 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
       WinCell<DIM>::store(eb, c, __ldg(a.EB + 2 * v), __ldg(a.EB + 2 * v + 1));
     }
   }
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   __syncthreads();
 
   float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};
   bool failed = false;
   int k = 0;
-  const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles of the tile
-  const int64_t st_lo = nst * part / kPushSplit, st_hi = nst * (part + 1) / kPushSplit;
 
   for (int64_t st = st_lo + warp; st < st_hi && !failed; st += nwarps, ++k) {
     const int64_t q0 = qa + st * TQ;
     const int nqt = (int)min((int64_t)TQ, qe - q0);
-    if (lane == 0) {
+    if (lane == 0 && k > 0) {
       bulk_wait_read_all();  // the previous store has read the buffer
-      const uint32_t bytes = (uint32_t)nqt * 16u;
-      mbar_expect_tx(bar, bytes * NA);
-#pragma unroll
-      for (int f = 0; f < NA; ++f)
-        bulk_load(T[f], field_ptr<DIM>(a.s, f) + q0 * 16, bytes, bar);
+      issue(st);
     }
     // the warp gives up together if any lane's bounded wait ran out
     if (__any_sync(kFull, !mbar_wait_bounded(bar, (uint32_t)(k & 1)))) {
