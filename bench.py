@@ -236,7 +236,7 @@ def oracle_strip_rate(wl, rows: int, steps: int):
     B = wl.B0[:, k0:k0 + rows].astype(np.float64).reshape(3, -1)
     g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
                     p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
-                    p["smooth_passes"])
+                    p["smooth_passes"], p.get("field_smooth_passes", 0))
     sim = O.Sim(g, [sp], B)
     times = []
     for i in range(steps):

@@ -47,7 +47,7 @@ class Grid(ctypes.Structure):
                 ("Te", ctypes.c_double), ("gamma_e", ctypes.c_double),
                 ("eta", ctypes.c_double), ("eta_h", ctypes.c_double),
                 ("n_floor", ctypes.c_double), ("shape", ctypes.c_int64),
-                ("smooth_passes", ctypes.c_int64)]
+                ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64)]
 
 
 class _Species(ctypes.Structure):
@@ -111,10 +111,11 @@ def _f64(a) -> np.ndarray:
 
 
 def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
-              eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0) -> Grid:
+              eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0,
+              field_smooth_passes=0) -> Grid:
     s = SHAPES[shape] if isinstance(shape, str) else int(shape)
     return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
-                smooth_passes)
+                smooth_passes, field_smooth_passes)
 
 
 def ncell(g: Grid) -> int:

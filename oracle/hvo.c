@@ -29,7 +29,13 @@
  *      is used for every shape and for both n and J.
  *   R3 n is extrapolated like J (Eq. 11 states it for J only).
  *   R4 smoothing is the separable (1/4,1/2,1/4) binomial filter applied to
- *      the deposited moments only.
+ *      the deposited moments.
+ *   R15 the optional field smoothing (Sec. 2.2: a self-consistent field and
+ *      moment smoother) applies the same operator S, field_smooth_passes
+ *      times, to copies of E^n and B^n that the ions gather in the push;
+ *      the field state is not smoothed.  S is symmetric, so with as many
+ *      field passes as moment passes the smoothed gather is the transpose
+ *      of the smoothed deposit and an ion exerts no force on itself.
  *   R5 the floor n_f = max(n, n_floor) is applied wherever n enters Ohm's
  *      law (pressure, ion flow and Hall term).
  *   R6 the Laplacian in the hyper-resistive term is the 3-point-per-axis
@@ -58,6 +64,7 @@ typedef struct {
   double Te, gamma_e, eta, eta_h, n_floor;
   int64_t shape; /* 0 NGP (Eq. 13), 1 QS (Eq. 17), 2 CIC (tensor-linear) */
   int64_t smooth_passes;
+  int64_t field_smooth_passes; /* R15 */
 } hvo_grid;
 
 typedef struct {
@@ -459,6 +466,7 @@ void hvo_init(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const doubl
 }
 
 /* One full step n -> n+1 in the paper's order (Sec. 2.2):
+ *   [field smoothing of the gathered copies of E, B (R15)],
  *   push + half-step deposit,  smoothing,  extrapolation (Eq. 11),
  *   subcycled field advance B^n -> B^{n+1} with the half-step moments,
  *   E^{n+1} = Ohm(B^{n+1}, n^{n+1}, J^{n+1}),  prev := half-step moments.
@@ -472,7 +480,19 @@ void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double
   double *ne = (double *)malloc(sizeof(double) * nce);
   double *Je = (double *)malloc(sizeof(double) * 3 * nce);
   double kin[4];
-  hvo_push_deposit(g, sp, nsp, E, B, nh, Jh, kin);
+  if (g->field_smooth_passes > 0) {
+    double *Eg = (double *)malloc(sizeof(double) * 3 * nce);
+    double *Bg = (double *)malloc(sizeof(double) * 3 * nce);
+    memcpy(Eg, E, sizeof(double) * 3 * nce);
+    memcpy(Bg, B, sizeof(double) * 3 * nce);
+    hvo_smooth(g, Eg, 3, g->field_smooth_passes);
+    hvo_smooth(g, Bg, 3, g->field_smooth_passes);
+    hvo_push_deposit(g, sp, nsp, Eg, Bg, nh, Jh, kin);
+    free(Eg);
+    free(Bg);
+  } else {
+    hvo_push_deposit(g, sp, nsp, E, B, nh, Jh, kin);
+  }
   double charge_raw = 0.0, vc = g->dx * g->dy * g->dz;
   for (int64_t c = 0; c < nce; ++c) charge_raw += nh[c] * vc;
   hvo_smooth(g, nh, 1, g->smooth_passes);
