@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
     ap.add_argument("--sort-every", type=int, default=None,
                     help="override the workload's sort interval")
+    ap.add_argument("--smooth", type=int, default=0,
+                    help="binomial passes on the moments and on the gathered E, B "
+                         "(self-consistent smoothing, Sec. 2.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -74,6 +77,15 @@ def make_workload(name, shape, seed_offset=0):
     if name == "harris3d_quarter":  # 256x128x128 cells, 32 ppc, 134M ions
         return I.harris3d(nx=256, ny=128, nz=128, shape=shape, seed=3000 + seed_offset)
     raise ValueError(name)
+
+
+def apply_overrides(wl, args):
+    if args.sort_every is not None:
+        wl.params["sort_every"] = args.sort_every
+    if args.smooth:
+        wl.params["smooth_passes"] = args.smooth
+        wl.params["field_smooth_passes"] = args.smooth
+    return wl
 
 
 # ----------------------------------------------------------------------------
@@ -250,7 +262,7 @@ def oracle_strip_rate(wl, rows: int, steps: int):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    wl = make_workload(args.workload, args.shape)
+    wl = apply_overrides(make_workload(args.workload, args.shape), args)
     p = wl.params
     n_full = wl.n_particles
     # bound the whole run to ~2 minutes: rows per step from a two-row probe
@@ -291,9 +303,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     hv.lib()
     hv.hv_set_allocator(True)
-    wl = make_workload(args.workload, args.shape, seed_offset=rank)
-    if args.sort_every is not None:
-        wl.params["sort_every"] = args.sort_every
+    wl = apply_overrides(make_workload(args.workload, args.shape, seed_offset=rank), args)
     n_ions = wl.n_particles
     stream = torch.cuda.current_stream(dev)
     ctx = hv.load_workload(wl, stream=stream)
@@ -349,7 +359,9 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {p['nx']}x{p['ny']}x{p['nz']} cells, "
                                    f"dx={p['dx']}, {n_ions} ions/GPU, shape {args.shape}, "
-                                   f"nsub={p['nsub']}, sort every {p['sort_every']}",
+                                   f"nsub={p['nsub']}, sort every {p['sort_every']}"
+                                   + (f", {p['smooth_passes']} smoothing passes on the moments "
+                                      f"and the gathered fields" if args.smooth else ""),
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (ions %.2f GB/GPU)" % (
                            n_ions * (28 if p['ny'] == 1 else 32) / 1e9)},

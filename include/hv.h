@@ -74,7 +74,10 @@ typedef struct {
   int32_t shape;        /* hv_shape */
   int32_t smooth_passes;/* binomial passes applied to deposited moments */
   int32_t sort_every;   /* sort ions by cell every this many steps; 0 never */
-  int32_t flags;        /* reserved, must be 0 */
+  int32_t field_smooth_passes; /* binomial passes applied to copies of E^n and
+                           B^n that the push gathers (the self-consistent
+                           field smoothing of Sec. 2.2); the field state is
+                           not smoothed; 0 off, at most 64 */
   uint64_t seed;        /* reserved for stochastic extensions */
 } hv_params;
 

@@ -98,7 +98,8 @@ hv_status check_params(const hv_params *p) {
   if (p->shape < 0 || p->shape > 2) return fail(HV_EINVAL, "shape must be 0 (NGP), 1 (QS) or 2 (CIC)");
   if (p->smooth_passes < 0 || p->smooth_passes > 64) return fail(HV_EINVAL, "smooth_passes in [0, 64]");
   if (p->sort_every < 0) return fail(HV_EINVAL, "sort_every must be >= 0");
-  if (p->flags != 0) return fail(HV_EINVAL, "flags must be 0");
+  if (p->field_smooth_passes < 0 || p->field_smooth_passes > 64)
+    return fail(HV_EINVAL, "field_smooth_passes in [0, 64]");
   // whistler limit Omega_ci h < Delta^2 / pi (Sec. 2.1) for the field step h
   double dmin = 1e300;
   if (p->nx > 1) dmin = std::fmin(dmin, p->dx);
@@ -344,13 +345,20 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
   for (int b = 0; b < 2; ++b)
     c->accm[b] = rec ? (float *)ctx_alloc(c, sizeof(float) * kMono * npad) : nullptr;
+  const bool fsm = p->field_smooth_passes > 0;
+  if (fsm) {
+    c->EBs = (float4 *)ctx_alloc(c, sizeof(float4) * 2 * npad);
+    for (int b = 0; b < 4; ++b) c->fsm[b] = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  }
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
       !c->pushpart || !c->gridpart || !c->diag_dev || !c->err ||
-      (rec && (!c->accm[0] || !c->accm[1]))) {
+      (rec && (!c->accm[0] || !c->accm[1])) ||
+      (fsm && (!c->EBs || !c->fsm[0] || !c->fsm[1] || !c->fsm[2] || !c->fsm[3]))) {
     hv_destroy(c);
     return fail(HV_ENOMEM, "grid allocation failed");
   }
   cudaMemsetAsync(c->EB, 0, sizeof(float4) * 2 * npad, c->stream);
+  if (fsm) cudaMemsetAsync(c->EBs, 0, sizeof(float4) * 2 * npad, c->stream);
   cudaMemsetAsync(c->acc, 0, sizeof(float4) * npad, c->stream);
   cudaMemsetAsync(c->mprev, 0, sizeof(float4) * nc, c->stream);
   cudaMemsetAsync(c->mext, 0, sizeof(float4) * nc, c->stream);

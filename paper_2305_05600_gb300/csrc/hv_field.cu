@@ -11,6 +11,8 @@
 //    array;
 //  * diagnostics: FP64 block partials of sum |B|^2/2 V_c, sum n V_c and
 //    max |div B|, reduced in a fixed order with the particle partials.
+#include <utility>
+
 #include "hv_internal.cuh"
 
 namespace hv {
@@ -1027,6 +1029,64 @@ cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) 
   return cudaGetLastError();
 }
 
+// Self-consistent field smoothing (Sec. 2.2): the push gathers S^p E and
+// S^p B, S being the binomial pass the moments are smoothed with, from a
+// second padded array; E and B themselves stay unsmoothed.  The interior of
+// the gather array is unpacked, smoothed p times and packed back with its
+// ghost images.
+__global__ void __launch_bounds__(256) eb_unpad_kernel(Geom g, const float4 *EB, float4 *ea,
+                                                       float4 *eb) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, c, i, j, k);
+    const int p = voxel_of(g, i, j, k);
+    ea[c] = EB[2 * p];
+    eb[c] = EB[2 * p + 1];
+  }
+}
+
+__global__ void __launch_bounds__(256) eb_pad_kernel(Geom g, const float4 *ea, const float4 *eb,
+                                                     float4 *EB) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode(g, c, i, j, k);
+    int xs[5], ys[5], zs[5];
+    const int nxs = axis_images(i, g.nx, xs);
+    const int nys = g.dim2 ? 1 : axis_images(j, g.ny, ys);
+    if (g.dim2) ys[0] = 0;
+    const int nzs = axis_images(k, g.nz, zs);
+    const float4 va = ea[c], vb = eb[c];
+    for (int a3 = 0; a3 < nzs; ++a3)
+      for (int a2 = 0; a2 < nys; ++a2)
+        for (int a1 = 0; a1 < nxs; ++a1) {
+          const int p = xs[a1] + ys[a2] * g.sy + zs[a3] * g.sz;
+          EB[2 * p] = va;
+          EB[2 * p + 1] = vb;
+        }
+  }
+}
+
+static cudaError_t launch_field_smoothing(hv_ctx *c) {
+  const int passes = c->p.field_smooth_passes;
+  if (passes <= 0) return cudaSuccess;
+  const int nb = elem_blocks(c->g.ncell);
+  float4 *a0 = c->fsm[0], *a1 = c->fsm[1], *b0 = c->fsm[2], *b1 = c->fsm[3];
+  eb_unpad_kernel<<<nb, 256, 0, c->stream>>>(c->g, c->EB, a0, b0);
+  for (int p = 0; p < passes; ++p) {
+    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, a0, a1);
+    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, b0, b1);
+    std::swap(a0, a1);
+    std::swap(b0, b1);
+  }
+  eb_pad_kernel<<<nb, 256, 0, c->stream>>>(c->g, a0, b0, c->EBs);
+  c->launches += 2 + 2 * passes;
+  return cudaGetLastError();
+}
+
+const float4 *gather_array(const hv_ctx *c) {
+  return c->p.field_smooth_passes > 0 ? c->EBs : c->EB;
+}
+
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
   StageArgs a;
   a.g = c->g;
@@ -1038,7 +1098,9 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
   a.coef = 0.f;
   a.EB = c->EB;
   c->launches++;
-  return c->g.dim2 ? launch_stage_t<2, 1>(c, a) : launch_stage_t<3, 1>(c, a);
+  cudaError_t e = c->g.dim2 ? launch_stage_t<2, 1>(c, a) : launch_stage_t<3, 1>(c, a);
+  if (e != cudaSuccess) return e;
+  return launch_field_smoothing(c);
 }
 
 cudaError_t launch_diag(hv_ctx *c) {

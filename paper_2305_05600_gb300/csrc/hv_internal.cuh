@@ -184,6 +184,9 @@ struct hv_ctx {
   double vc;
   // grids (device)
   float4 *EB;           // padded [npad][2]: {Ex,Ey,Ez,Bx},{By,Bz,0,0}
+  float4 *EBs;          // the same, field-smoothed, gathered by the push when
+                        // field_smooth_passes > 0 (else null)
+  float4 *fsm[4];       // interior [ncell] scratch of the field smoothing
   float4 *acc;          // padded [npad] per-cell deposit {n,Jx,Jy,Jz}
   float *accm[2];       // padded [npad][kMono] per-cell moment records
                         // (QS in the x-z layout), used alternately
@@ -236,6 +239,7 @@ bool uses_records(const hv_ctx *c);
 cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                float coef);
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
+const float4 *gather_array(const hv_ctx *c);
 // learned moment filter (x-z layout)
 cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out);
 void pack_filter(const float *P, std::vector<__nv_bfloat16> &w, std::vector<float> &bias);

@@ -832,7 +832,7 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.s = sp.buf[sp.cur];
   a.n = sp.n;
   a.tile_off = sp.tile_off;
-  a.EB = c->EB;
+  a.EB = gather_array(c);
   a.acc = c->acc;
   a.accm = c->accm[c->accpar];
   a.g = c->g;

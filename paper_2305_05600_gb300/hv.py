@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
                 ("gamma_e", ctypes.c_double), ("eta", ctypes.c_double),
                 ("eta_h", ctypes.c_double), ("n_floor", ctypes.c_double),
                 ("shape", ctypes.c_int32), ("smooth_passes", ctypes.c_int32),
-                ("sort_every", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("sort_every", ctypes.c_int32), ("field_smooth_passes", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -171,7 +171,8 @@ def params_from(d: dict) -> Params:
                   float(d["dx"]), float(d.get("dy", 1.0)), float(d["dz"]), float(d["dt"]),
                   float(d.get("Te", 0.0)), float(d.get("gamma_e", 1.0)), float(d.get("eta", 0.0)),
                   float(d.get("eta_h", 0.0)), float(d.get("n_floor", 0.05)), shape,
-                  int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)), 0,
+                  int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)),
+                  int(d.get("field_smooth_passes", 0)),
                   int(d.get("seed", 0)))
 
 

@@ -159,6 +159,33 @@ def test_smoothing_parity(hvmod):
     ctx.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("shape", ["qs", "ngp"])
+def test_field_smoothing_parity(hvmod, dim, shape):
+    """Self-consistent smoothing: moments and the gathered E, B both get two
+    binomial passes; E and B themselves stay unsmoothed."""
+    wl = small_workload(dim, shape)
+    wl.params["smooth_passes"] = 2
+    wl.params["field_smooth_passes"] = 2
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+        assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+        assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
+        d = hvmod.hv_diag(ctx)
+        od = sim.diags[-1]
+        assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+    ctx.close()
+
+
 def test_quasi_1d_and_multispecies(hvmod):
     """nz = 1 (one-cell z axis) and two species with different q/m."""
     wl = I.whistler1d(nx=64, ppc=32, steps=1)
