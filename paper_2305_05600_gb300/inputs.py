@@ -329,10 +329,69 @@ def whistler1d(nx=128, ppc=256, dx=0.25, dt=0.05, nsub=5, Ti=0.005, Te=0.005, am
                     notes=f"{nx} cells, {ppc} ppc, k={k:.4f}")
 
 
+def explosion2d(nx=512, nz=512, length=1000.0, ppc=200, n_debris=1 << 20, mach=15.0,
+                r_m=150.0, sigma=None, beta=0.1, seed=6000, steps=3000, shape="ngp",
+                smooth_passes=0, dt=0.01, nsub=1, eta=0.0, eta_h=0.01, n_floor=0.05,
+                sort_every=20) -> Workload:
+    """Expanding debris cloud in a magnetised background (the astrophysical
+    explosion of Sec. 3.2), x-z plane, periodic.
+
+    Background: n0 = 1, B0 = x^ (in the plane), beta_i = beta_e = beta, so
+    T_i = T_e = beta / 2, isothermal electrons, `ppc` ions per cell.  Debris:
+    `n_debris` ions of the same charge and mass in a Gaussian cloud of width
+    `sigma` (default r_m / 10) at the box centre, each moving radially in the
+    plane at `mach` v_A plus the background's thermal spread.  The debris
+    holds as many ions as a disc of radius r_m of the background (the
+    equal-mass radius; in the x-z plane a disc per unit length in y).
+    `smooth_passes` binomial passes are applied both to the moments and to
+    the gathered fields (the self-consistent smoothing)."""
+    dx = length / nx
+    p = base_params(nx, 1, nz, dx, 1.0, dx, dt, nsub, Te=0.5 * beta, eta=eta, eta_h=eta_h,
+                    n_floor=n_floor, shape=shape, smooth_passes=smooth_passes,
+                    sort_every=sort_every, field_smooth_passes=smooth_passes)
+    rng = _rng(seed)
+    ncell = nx * nz
+    Ti = 0.5 * beta
+    B = np.zeros((3, nz, 1, nx))
+    B[0] = 1.0
+    cell, off = load_cells(p, np.full(ncell, ppc), rng, (nx, 1, nz))
+    nb = cell.shape[0]
+    v = math.sqrt(Ti) * _box_muller(rng, (3, nb))
+    w = np.full(nb, dx * dx / ppc)
+    # debris: Gaussian positions about the centre, radial velocities
+    sig = 0.1 * r_m if sigma is None else sigma
+    Lx, Lz = nx * dx, nz * dx
+    rx = sig * _box_muller(rng, n_debris)
+    rz = sig * _box_muller(rng, n_debris)
+    x = np.mod(0.5 * Lx + rx, Lx)
+    z = np.mod(0.5 * Lz + rz, Lz)
+    r = np.maximum(np.hypot(rx, rz), 1e-12)
+    vd = math.sqrt(Ti) * _box_muller(rng, (3, n_debris))
+    vd[0] += mach * rx / r
+    vd[2] += mach * rz / r
+    fx, fz = x / dx, z / dx
+    i = np.minimum(np.floor(fx).astype(np.int64), nx - 1)
+    k = np.minimum(np.floor(fz).astype(np.int64), nz - 1)
+    offd = np.zeros((3, n_debris))
+    offd[0] = np.clip(2.0 * (fx - i) - 1.0, -1.0, 1.0)
+    offd[2] = np.clip(2.0 * (fz - k) - 1.0, -1.0, 1.0)
+    celld = i + nx * k
+    wd = np.full(n_debris, math.pi * r_m * r_m / n_debris)
+    cell = np.concatenate([cell, celld])
+    order = np.argsort(cell, kind="stable")
+    sp = _finish(cell[order], np.concatenate([off, offd], axis=1)[:, order],
+                 np.concatenate([v, vd], axis=1)[:, order], np.concatenate([w, wd])[order])
+    return Workload("explosion2d", p, B.astype(np.float32), [sp], steps,
+                    notes=f"{nx}x{nz} cells, dx={dx:.4f}, {ppc} ppc + {n_debris} debris ions, "
+                          f"M_A={mach}, R_m={r_m}, sigma={sig}, {shape}, "
+                          f"{smooth_passes} smoothing passes")
+
+
 WORKLOADS = {
     "alfven2d": alfven2d,
     "harris2d": harris2d,
     "beam3d": beam3d,
     "harris3d": harris3d,
     "whistler1d": whistler1d,
+    "explosion2d": explosion2d,
 }
