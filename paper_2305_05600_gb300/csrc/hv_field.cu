@@ -74,12 +74,23 @@ __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, k;
     decode(g, c, i, j, k);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (single_image(g, i, j, k)) {
+      const int p = voxel_of(g, i, j, k);
+      const float4 v = a.acc[p];
+      m.x += v.x;
+      m.y += v.y;
+      m.z += v.z;
+      m.w += v.w;
+      a.acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      finish_moment(a, c, m);
+      continue;
+    }
     int xs[5], ys[5], zs[5];
     const int nxs = axis_images(i, g.nx, xs);
     const int nys = g.dim2 ? 1 : axis_images(j, g.ny, ys);
     if (g.dim2) ys[0] = 0;
     const int nzs = axis_images(k, g.nz, zs);
-    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int a3 = 0; a3 < nzs; ++a3)
       for (int a2 = 0; a2 < nys; ++a2)
         for (int a1 = 0; a1 < nxs; ++a1) {
@@ -341,13 +352,19 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       // at the cell and at each of its ghost images
       const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
       if (gx < g.nx && (DIM == 2 || gy < g.ny) && gz < g.nz) {
+        const float4 e0 = make_float4(ex, ey, ez, bx);
+        const float4 e1 = make_float4(by, bz, 0.f, 0.f);
+        if (single_image(g, gx, gy, gz)) {
+          const int p = voxel_of(g, gx, gy, gz);
+          a.EB[2 * p] = e0;
+          a.EB[2 * p + 1] = e1;
+          continue;
+        }
         int xs[5], ys[5], zs[5];
         const int nxs = axis_images(gx, g.nx, xs);
         const int nys = DIM == 2 ? 1 : axis_images(gy, g.ny, ys);
         if (DIM == 2) ys[0] = 0;
         const int nzs = axis_images(gz, g.nz, zs);
-        const float4 e0 = make_float4(ex, ey, ez, bx);
-        const float4 e1 = make_float4(by, bz, 0.f, 0.f);
         for (int a3 = 0; a3 < nzs; ++a3)
           for (int a2 = 0; a2 < nys; ++a2)
             for (int a1 = 0; a1 < nxs; ++a1) {
@@ -391,14 +408,20 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
 // One field stage in 3D (Eq. 5 with E from Eqs. 2-4, 6), streamed along z:
 //   B_out = B_base - coef * curl E(B_in)
 // A block owns an X x Y column of output cells over Z planes and walks up
-// the column.  At step q it computes J = curl B on plane zj = z0 - 2 + q
-// (x-y halo 2), E two planes behind (halo 1) and B_out two planes behind
-// that, so every plane a step reads was written in an earlier step: one
-// barrier per step suffices.  The planes of B (halo 3) and of the ion
-// moments are fetched one step ahead with asynchronous copies into ring
-// buffers, so no global load waits inside a step; only B_base is read from
-// global memory, issued before the barrier.  Every plane of B is loaded
-// once per column and the halos are paid only in x and y.
+// the column.  At step q it computes J = curl B on plane zj = z0 - 2 + q, E
+// two planes behind and B_out two planes behind that, so every plane a step
+// reads was written in an earlier step: one barrier per step suffices.  The
+// planes of B and of the ion moments are fetched one step ahead with
+// asynchronous copies into ring buffers, so no global load waits inside a
+// step; only B_base is read from global memory, issued before the barrier.
+// Every plane of B is loaded once per column and the halos are paid only in
+// x and y.
+//
+// All planes share one layout: rows of P = X + 6 cells (the B halo of 3)
+// and Y + 6 rows.  J (and n) is computed on rows 1..Y+4, E on rows 2..Y+3,
+// over whole rows, so that the lanes of a warp touch consecutive words of
+// shared memory; the values in the outer columns of those rows are never
+// used.
 // ----------------------------------------------------------------------------
 #ifndef HV_ST3D_Z
 #define HV_ST3D_Z 16
@@ -408,20 +431,20 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
 #endif
 namespace st3d {
 constexpr int X = 32, Y = 8, Z = HV_ST3D_Z;  // output cells per block
-constexpr int BX = X + 6, BY = Y + 6, NB = BX * BY;  // B plane, halo 3
-constexpr int JX = X + 4, JY = Y + 4, NJ = JX * JY;  // J and n plane, halo 2
-constexpr int EX = X + 2, EY = Y + 2, NE = EX * EY;  // E plane, halo 1
+constexpr int P = X + 6, R = Y + 6, NP = P * R;  // plane layout (B halo 3)
+constexpr int J0 = P, NJ = P * (Y + 4);          // J, n: rows 1 .. Y+4
+constexpr int E0 = 2 * P, NE = P * (Y + 2);      // E, moments: rows 2 .. Y+3
 constexpr int kThreads = HV_ST3D_THREADS;
 // ring depths: B planes zj-2..zj+2 (E reads zj-2, J zj-1..zj+1, the copy
 // fills zj+2); J, n and E each hold three planes being read and one being
 // written; the moment float4 at E cells one read and one in flight
 constexpr int kRB = 5, kRJ = 4, kRN = 4, kRM = 2, kRE = 4;
-constexpr int kB = 0;                    // [kRB][3][NB]
-constexpr int kJ = kB + kRB * 3 * NB;    // [kRJ][3][NJ]
-constexpr int kN = kJ + kRJ * 3 * NJ;    // [kRN][NJ]   ion density n
-constexpr int kM = kN + kRN * NJ;        // [kRM][NE]   {n, Jix, Jiy, Jiz} as float4
-constexpr int kE = kM + kRM * 4 * NE;    // [kRE][3][NE]
-constexpr int kFloats = kE + kRE * 3 * NE;
+constexpr int kB = 0;                    // [kRB][3][NP]
+constexpr int kJ = kB + kRB * 3 * NP;    // [kRJ][3][NP]
+constexpr int kN = kJ + kRJ * 3 * NP;    // [kRN][NP]   ion density n
+constexpr int kM = kN + kRN * NP;        // [kRM][NP]   {n, Jix, Jiy, Jiz} as float4
+constexpr int kE = kM + kRM * 4 * NP;    // [kRE][3][NP]
+constexpr int kFloats = kE + kRE * 3 * NP;
 static_assert(kM % 4 == 0, "moment ring must be 16-byte aligned");
 }  // namespace st3d
 
@@ -444,7 +467,7 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
   using namespace st3d;
   // cells per thread in each plane region; a thread keeps the x-y part of
   // its cells' global offsets, so a plane adds only its z offset
-  constexpr int LB = (NB + kThreads - 1) / kThreads;
+  constexpr int LB = (NP + kThreads - 1) / kThreads;
   constexpr int LJ = (NJ + kThreads - 1) / kThreads;
   constexpr int LE = (NE + kThreads - 1) / kThreads;
   constexpr int LO = (X * Y + kThreads - 1) / kThreads;
@@ -456,27 +479,28 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
   const int x0 = bx * X, y0 = by * Y, z0 = bz * Z;
   const int t = threadIdx.x;
   const int sxy = g.nx * g.ny;
-  auto xy = [&](int lx, int ly) {
-    return wrap_near(x0 + lx, g.nx, X + 3) + g.nx * wrap_near(y0 + ly, g.ny, Y + 3);
+  // x-y part of the global offset of plane cell c (column c % P, row c / P)
+  auto xy = [&](int c) {
+    return wrap_near(x0 + c % P - 3, g.nx, X + 3) + g.nx * wrap_near(y0 + c / P - 3, g.ny, Y + 3);
   };
   auto zoff = [&](int z) { return sxy * wrap_near(z, g.nz, Z + 6); };
-  // ring slot of plane z (planes start at z0 - 5, so the index is >= 0)
+  // ring slot of plane z (planes start at z0 - 3, so the index is >= 0)
   auto slot = [&](int z, int depth) { return (z - z0 + 8) % depth; };
   int xb[LB], xj[LJ], xe[LE], xo[LO];
 #pragma unroll
   for (int u = 0; u < LB; ++u) {
     const int r = t + u * kThreads;
-    xb[u] = r < NB ? xy(r % BX - 3, r / BX - 3) : 0;
+    xb[u] = r < NP ? xy(r) : 0;
   }
 #pragma unroll
   for (int u = 0; u < LJ; ++u) {
     const int r = t + u * kThreads;
-    xj[u] = r < NJ ? xy(r % JX - 2, r / JX - 2) : 0;
+    xj[u] = r < NJ ? xy(J0 + r) : 0;
   }
 #pragma unroll
   for (int u = 0; u < LE; ++u) {
     const int r = t + u * kThreads;
-    xe[u] = r < NE ? xy(r % EX - 1, r / EX - 1) : 0;
+    xe[u] = r < NE ? xy(E0 + r) : 0;
   }
 #pragma unroll
   for (int u = 0; u < LO; ++u) {
@@ -485,20 +509,20 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
     xo[u] = (r < X * Y && gx < g.nx && gy < g.ny) ? gx + g.nx * gy : -1;
   }
   auto copy_B = [&](int z) {
-    float *b = sm + kB + slot(z, kRB) * 3 * NB;
+    float *b = sm + kB + slot(z, kRB) * 3 * NP;
     const int zo_ = zoff(z);
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int r = t + u * kThreads;
-      if (r >= NB) continue;
+      if (r >= NP) continue;
       const float *src = reinterpret_cast<const float *>(a.Bin + (xb[u] + zo_));
       cp_async4(b + r, src);
-      cp_async4(b + NB + r, src + 1);
-      cp_async4(b + 2 * NB + r, src + 2);
+      cp_async4(b + NP + r, src + 1);
+      cp_async4(b + 2 * NP + r, src + 2);
     }
   };
   auto copy_n = [&](int z) {
-    float *nn = sm + kN + slot(z, kRN) * NJ;
+    float *nn = sm + kN + slot(z, kRN) * NP + J0;
     const int zo_ = zoff(z);
 #pragma unroll
     for (int u = 0; u < LJ; ++u) {
@@ -507,7 +531,7 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
     }
   };
   auto copy_m = [&](int z) {
-    float4 *m = reinterpret_cast<float4 *>(sm + kM) + slot(z, kRM) * NE;
+    float4 *m = reinterpret_cast<float4 *>(sm + kM) + slot(z, kRM) * NP + E0;
     const int zo_ = zoff(z);
 #pragma unroll
     for (int u = 0; u < LE; ++u) {
@@ -544,80 +568,78 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
     cp_async_commit();
 
     if (q <= Z + 3) {  // J = curl B on plane zj
-      const float *bm = sm + kB + slot(zj - 1, kRB) * 3 * NB;
-      const float *b0 = sm + kB + slot(zj, kRB) * 3 * NB;
-      const float *bp = sm + kB + slot(zj + 1, kRB) * 3 * NB;
-      float *j = sm + kJ + slot(zj, kRJ) * 3 * NJ;
+      const float *bm = sm + kB + slot(zj - 1, kRB) * 3 * NP;
+      const float *b0 = sm + kB + slot(zj, kRB) * 3 * NP;
+      const float *bp = sm + kB + slot(zj + 1, kRB) * 3 * NP;
+      float *j = sm + kJ + slot(zj, kRJ) * 3 * NP;
 #pragma unroll
       for (int u = 0; u < LJ; ++u) {
         const int r = t + u * kThreads;
         if (r >= NJ) continue;
-        const int c = (r % JX + 1) + (r / JX + 1) * BX;
-        const float dBz_dy = (b0[2 * NB + c + BX] - b0[2 * NB + c - BX]) * k.idy2;
-        const float dBx_dy = (b0[c + BX] - b0[c - BX]) * k.idy2;
-        const float dBy_dz = (bp[NB + c] - bm[NB + c]) * k.idz2;
+        const int c = J0 + r;
+        const float dBz_dy = (b0[2 * NP + c + P] - b0[2 * NP + c - P]) * k.idy2;
+        const float dBx_dy = (b0[c + P] - b0[c - P]) * k.idy2;
+        const float dBy_dz = (bp[NP + c] - bm[NP + c]) * k.idz2;
         const float dBx_dz = (bp[c] - bm[c]) * k.idz2;
-        const float dBz_dx = (b0[2 * NB + c + 1] - b0[2 * NB + c - 1]) * k.idx2;
-        const float dBy_dx = (b0[NB + c + 1] - b0[NB + c - 1]) * k.idx2;
-        j[r] = dBz_dy - dBy_dz;
-        j[NJ + r] = dBx_dz - dBz_dx;
-        j[2 * NJ + r] = dBy_dx - dBx_dy;
+        const float dBz_dx = (b0[2 * NP + c + 1] - b0[2 * NP + c - 1]) * k.idx2;
+        const float dBy_dx = (b0[NP + c + 1] - b0[NP + c - 1]) * k.idx2;
+        j[c] = dBz_dy - dBy_dz;
+        j[NP + c] = dBx_dz - dBz_dx;
+        j[2 * NP + c] = dBy_dx - dBx_dy;
       }
     }
     if (q >= 3 && q <= Z + 4) {  // E from Ohm's law on plane ze
-      const float *jm = sm + kJ + slot(ze - 1, kRJ) * 3 * NJ;
-      const float *j0 = sm + kJ + slot(ze, kRJ) * 3 * NJ;
-      const float *jp = sm + kJ + slot(ze + 1, kRJ) * 3 * NJ;
-      const float *nm = sm + kN + slot(ze - 1, kRN) * NJ;
-      const float *n0 = sm + kN + slot(ze, kRN) * NJ;
-      const float *np = sm + kN + slot(ze + 1, kRN) * NJ;
-      const float4 *m0 = reinterpret_cast<const float4 *>(sm + kM) + slot(ze, kRM) * NE;
-      const float *b0 = sm + kB + slot(ze, kRB) * 3 * NB;
-      float *e = sm + kE + slot(ze, kRE) * 3 * NE;
+      const float *jm = sm + kJ + slot(ze - 1, kRJ) * 3 * NP;
+      const float *j0 = sm + kJ + slot(ze, kRJ) * 3 * NP;
+      const float *jp = sm + kJ + slot(ze + 1, kRJ) * 3 * NP;
+      const float *nm = sm + kN + slot(ze - 1, kRN) * NP;
+      const float *n0 = sm + kN + slot(ze, kRN) * NP;
+      const float *np = sm + kN + slot(ze + 1, kRN) * NP;
+      const float4 *m0 = reinterpret_cast<const float4 *>(sm + kM) + slot(ze, kRM) * NP;
+      const float *b0 = sm + kB + slot(ze, kRB) * 3 * NP;
+      float *e = sm + kE + slot(ze, kRE) * 3 * NP;
 #pragma unroll
       for (int u = 0; u < LE; ++u) {
         const int r = t + u * kThreads;
         if (r >= NE) continue;
-        const int rx = r % EX, ry = r / EX;
-        const int jc = (rx + 1) + (ry + 1) * JX;
-        const int bc = (rx + 2) + (ry + 2) * BX;
-        const float4 mi = m0[r];
+        const int c = E0 + r;
+        const float4 mi = m0[c];
         const float inv = __frcp_rn(fmaxf(mi.x, k.n_floor));
-        const float bxv = b0[bc], byv = b0[NB + bc], bzv = b0[2 * NB + bc];
-        const float jx = j0[jc], jy = j0[NJ + jc], jz = j0[2 * NJ + jc];
+        const float bxv = b0[c], byv = b0[NP + c], bzv = b0[2 * NP + c];
+        const float jx = j0[c], jy = j0[NP + c], jz = j0[2 * NP + c];
         const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
-        const float gpx = (pe(n0[jc + 1]) - pe(n0[jc - 1])) * k.idx2;
-        const float gpy = (pe(n0[jc + JX]) - pe(n0[jc - JX])) * k.idy2;
-        const float gpz = (pe(np[jc]) - pe(nm[jc])) * k.idz2;
+        const float gpx = (pe(n0[c + 1]) - pe(n0[c - 1])) * k.idx2;
+        const float gpy = (pe(n0[c + P]) - pe(n0[c - P])) * k.idy2;
+        const float gpz = (pe(np[c]) - pe(nm[c])) * k.idz2;
         float l[3];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const float c0 = j0[m * NJ + jc];
-          l[m] = (j0[m * NJ + jc + 1] + j0[m * NJ + jc - 1] - 2.f * c0) * k.ilx +
-                 (j0[m * NJ + jc + JX] + j0[m * NJ + jc - JX] - 2.f * c0) * k.ily +
-                 (jp[m * NJ + jc] + jm[m * NJ + jc] - 2.f * c0) * k.ilz;
+          const float c0 = j0[m * NP + c];
+          l[m] = (j0[m * NP + c + 1] + j0[m * NP + c - 1] - 2.f * c0) * k.ilx +
+                 (j0[m * NP + c + P] + j0[m * NP + c - P] - 2.f * c0) * k.ily +
+                 (jp[m * NP + c] + jm[m * NP + c] - 2.f * c0) * k.ilz;
         }
-        e[r] = ((uy * bzv - uz * byv) - gpx) * inv + k.eta * jx - k.eta_h * l[0];
-        e[NE + r] = ((uz * bxv - ux * bzv) - gpy) * inv + k.eta * jy - k.eta_h * l[1];
-        e[2 * NE + r] = ((ux * byv - uy * bxv) - gpz) * inv + k.eta * jz - k.eta_h * l[2];
+        e[c] = ((uy * bzv - uz * byv) - gpx) * inv + k.eta * jx - k.eta_h * l[0];
+        e[NP + c] = ((uz * bxv - ux * bzv) - gpy) * inv + k.eta * jy - k.eta_h * l[1];
+        e[2 * NP + c] = ((ux * byv - uy * bxv) - gpz) * inv + k.eta * jz - k.eta_h * l[2];
       }
     }
     if (out_on) {  // B_out = B_base - coef * curl E on plane zo
-      const float *em = sm + kE + slot(zo - 1, kRE) * 3 * NE;
-      const float *e0 = sm + kE + slot(zo, kRE) * 3 * NE;
-      const float *ep = sm + kE + slot(zo + 1, kRE) * 3 * NE;
+      const float *em = sm + kE + slot(zo - 1, kRE) * 3 * NP;
+      const float *e0 = sm + kE + slot(zo, kRE) * 3 * NP;
+      const float *ep = sm + kE + slot(zo + 1, kRE) * 3 * NP;
       const int zo_ = sxy * zo;
 #pragma unroll
       for (int u = 0; u < LO; ++u) {
         const int r = t + u * kThreads;
         if (xo[u] < 0) continue;
-        const int ec = (r % X + 1) + (r / X + 1) * EX;
-        const float dEz_dy = (e0[2 * NE + ec + EX] - e0[2 * NE + ec - EX]) * k.idy2;
-        const float dEx_dy = (e0[ec + EX] - e0[ec - EX]) * k.idy2;
-        const float dEy_dz = (ep[NE + ec] - em[NE + ec]) * k.idz2;
-        const float dEx_dz = (ep[ec] - em[ec]) * k.idz2;
-        const float dEz_dx = (e0[2 * NE + ec + 1] - e0[2 * NE + ec - 1]) * k.idx2;
-        const float dEy_dx = (e0[NE + ec + 1] - e0[NE + ec - 1]) * k.idx2;
+        const int c = (r % X + 3) + (r / X + 3) * P;
+        const float dEz_dy = (e0[2 * NP + c + P] - e0[2 * NP + c - P]) * k.idy2;
+        const float dEx_dy = (e0[c + P] - e0[c - P]) * k.idy2;
+        const float dEy_dz = (ep[NP + c] - em[NP + c]) * k.idz2;
+        const float dEx_dz = (ep[c] - em[c]) * k.idz2;
+        const float dEz_dx = (e0[2 * NP + c + 1] - e0[2 * NP + c - 1]) * k.idx2;
+        const float dEy_dx = (e0[NP + c + 1] - e0[NP + c - 1]) * k.idx2;
         a.Bout[xo[u] + zo_] =
             make_float4(bb[u].x - a.coef * (dEz_dy - dEy_dz), bb[u].y - a.coef * (dEx_dz - dEz_dx),
                         bb[u].z - a.coef * (dEy_dx - dEx_dy), 0.f);
@@ -1050,12 +1072,18 @@ __global__ void __launch_bounds__(256) eb_pad_kernel(Geom g, const float4 *ea, c
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, k;
     decode(g, c, i, j, k);
+    const float4 va = ea[c], vb = eb[c];
+    if (single_image(g, i, j, k)) {
+      const int p = voxel_of(g, i, j, k);
+      EB[2 * p] = va;
+      EB[2 * p + 1] = vb;
+      continue;
+    }
     int xs[5], ys[5], zs[5];
     const int nxs = axis_images(i, g.nx, xs);
     const int nys = g.dim2 ? 1 : axis_images(j, g.ny, ys);
     if (g.dim2) ys[0] = 0;
     const int nzs = axis_images(k, g.nz, zs);
-    const float4 va = ea[c], vb = eb[c];
     for (int a3 = 0; a3 < nzs; ++a3)
       for (int a2 = 0; a2 < nys; ++a2)
         for (int a1 = 0; a1 < nxs; ++a1) {

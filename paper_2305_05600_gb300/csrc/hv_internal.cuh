@@ -120,6 +120,13 @@ __device__ __forceinline__ int ion_key(const Geom &g, int vox) {
 
 // Padded coordinates standing for interior coordinate i on an axis of n
 // cells: P in [0, n + 2*kGhost) with (P - kGhost) mod n == i.  At most 5.
+// True when interior cell (i, j, k) has no ghost image: it lies at least
+// kGhost cells from every face (2D: along x and z).
+__host__ __device__ __forceinline__ bool single_image(const Geom &g, int i, int j, int k) {
+  return i >= kGhost && i < g.nx - kGhost && k >= kGhost && k < g.nz - kGhost &&
+         (g.dim2 || (j >= kGhost && j < g.ny - kGhost));
+}
+
 __host__ __device__ __forceinline__ int axis_images(int i, int n, int *out) {
   int c = 0;
   const int hi = n + 2 * kGhost;
