@@ -47,7 +47,8 @@ class Grid(ctypes.Structure):
                 ("Te", ctypes.c_double), ("gamma_e", ctypes.c_double),
                 ("eta", ctypes.c_double), ("eta_h", ctypes.c_double),
                 ("n_floor", ctypes.c_double), ("shape", ctypes.c_int64),
-                ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64)]
+                ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64),
+                ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double)]
 
 
 class _Species(ctypes.Structure):
@@ -87,6 +88,11 @@ def lib():
             L.hvo_lap.argtypes = [P, P, I64, P]
             L.hvo_ohm.argtypes = [P, P, P, P, P]
             L.hvo_field_advance.argtypes = [P, P, P, P]
+            L.hvo_ohm_pe.argtypes = [P, P, P, P, P, P]
+            L.hvo_dpdt.argtypes = [P, P, P, P, P, P]
+            L.hvo_field_advance_pe.argtypes = [P, P, P, P, P]
+            L.hvo_init_pe.argtypes = [P, P, I64, P, P, P, P, P]
+            L.hvo_step_pe.argtypes = [P, P, I64, P, P, P, P, P, P, P, P]
             L.hvo_smooth.argtypes = [P, P, I64, I64]
             L.hvo_extrapolate.argtypes = [I64, P, P, P]
             L.hvo_diag_grid.argtypes = [P, P, P, P, P, P]
@@ -112,10 +118,10 @@ def _f64(a) -> np.ndarray:
 
 def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
               eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0,
-              field_smooth_passes=0) -> Grid:
+              field_smooth_passes=0, pe_eq=0, kappa=0.0) -> Grid:
     s = SHAPES[shape] if isinstance(shape, str) else int(shape)
     return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
-                smooth_passes, field_smooth_passes)
+                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa))
 
 
 def ncell(g: Grid) -> int:
@@ -261,6 +267,35 @@ def field_advance(g, B, n, Ji):
     return B
 
 
+def ohm_pe(g, B, n, Ji, pe):
+    B = _f64(B).reshape(3, -1)
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    pe = _f64(pe).reshape(-1)
+    E = np.zeros(3 * ncell(g))
+    lib().hvo_ohm_pe(ctypes.byref(g), _p(B), _p(n), _p(Ji), _p(pe), _p(E))
+    return E.reshape(3, -1)
+
+
+def dpdt(g, B, pe, n, Ji):
+    B = _f64(B).reshape(3, -1)
+    pe = _f64(pe).reshape(-1)
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    out = np.zeros(ncell(g))
+    lib().hvo_dpdt(ctypes.byref(g), _p(B), _p(pe), _p(n), _p(Ji), _p(out))
+    return out
+
+
+def field_advance_pe(g, B, pe, n, Ji):
+    B = _f64(B).reshape(3, -1).copy()
+    pe = _f64(pe).reshape(-1).copy()
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    lib().hvo_field_advance_pe(ctypes.byref(g), _p(B), _p(pe), _p(n), _p(Ji))
+    return B, pe
+
+
 def smooth(g, q, passes):
     q = _f64(q).copy()
     nc = q.size // ncell(g)
@@ -362,8 +397,13 @@ class Sim:
         self.step_count = 0
         self.diags: list[dict] = []
         arr = _species_array(self.species)
-        lib().hvo_init(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
-                       _p(self.n_prev), _p(self.J_prev))
+        self.pe = np.zeros(nce) if g.pe_eq else None
+        if g.pe_eq:
+            lib().hvo_init_pe(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
+                              _p(self.pe), _p(self.n_prev), _p(self.J_prev))
+        else:
+            lib().hvo_init(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
+                           _p(self.n_prev), _p(self.J_prev))
 
     def sort(self, key_fn=None):
         """Apply the stable counting sort to every species, by cell or by
@@ -383,9 +423,14 @@ class Sim:
                 self.sort(key_fn)
             arr = _species_array(self.species)
             d = Diag()
-            lib().hvo_step(ctypes.byref(self.g), arr, len(self.species), _p(self.B), _p(self.E),
-                           _p(self.n_prev), _p(self.J_prev), _p(self.n_ext), _p(self.J_ext),
-                           ctypes.byref(d))
+            if self.pe is not None:
+                lib().hvo_step_pe(ctypes.byref(self.g), arr, len(self.species), _p(self.B),
+                                  _p(self.E), _p(self.pe), _p(self.n_prev), _p(self.J_prev),
+                                  _p(self.n_ext), _p(self.J_ext), ctypes.byref(d))
+            else:
+                lib().hvo_step(ctypes.byref(self.g), arr, len(self.species), _p(self.B),
+                               _p(self.E), _p(self.n_prev), _p(self.J_prev), _p(self.n_ext),
+                               _p(self.J_ext), ctypes.byref(d))
             self.step_count += 1
             self.diags.append(d.as_dict())
         return self.diags[-1] if self.diags else None

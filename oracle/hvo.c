@@ -30,6 +30,15 @@
  *   R3 n is extrapolated like J (Eq. 11 states it for J only).
  *   R4 smoothing is the separable (1/4,1/2,1/4) binomial filter applied to
  *      the deposited moments.
+ *   R16 the optional electron energy equation (Sec. 2.1, Eq. dpdt) makes
+ *      p_e a field: dp_e/dt = -gamma div(p_e u_e) + (gamma - 1) u_e . grad p_e
+ *      + (gamma - 1) div(kappa grad T_e), with u_e = -(J - J_i) / n_f,
+ *      T_e = p_e / n_f, a constant kappa, H_ei = 0 (no collisions) and the
+ *      centred operators of Eq. 12 (the Laplacian of R6 for the heat flux).
+ *      It is advanced with B in each explicit-midpoint subcycle (R7), with
+ *      the moments held at their half-step values; Ohm's law takes grad p_e
+ *      from the field.  At start-up p_e = Te n_f^gamma of the start-up
+ *      moments (Eq. 6).
  *   R15 the optional field smoothing (Sec. 2.2: a self-consistent field and
  *      moment smoother) applies the same operator S, field_smooth_passes
  *      times, to copies of E^n and B^n that the ions gather in the push;
@@ -65,6 +74,8 @@ typedef struct {
   int64_t shape; /* 0 NGP (Eq. 13), 1 QS (Eq. 17), 2 CIC (tensor-linear) */
   int64_t smooth_passes;
   int64_t field_smooth_passes; /* R15 */
+  int64_t pe_eq;                /* R16: 1 = electron energy equation */
+  double kappa;                 /* R16: heat conductivity */
 } hvo_grid;
 
 typedef struct {
@@ -348,7 +359,8 @@ void hvo_lap(const hvo_grid *g, const double *A, int64_t nc, double *out) {
  * Te, n_0 = 1) and the density floor n_f = max(n, n_floor) (Sec. 2.1):
  *   E = -grad p_e / n_f - (J_i / n_f) x B + (J x B) / n_f + eta J - eta_H lap J
  * Inputs: B [3][ncell], n [ncell], Ji [3][ncell]; output E [3][ncell]. */
-void hvo_ohm(const hvo_grid *g, const double *B, const double *n, const double *Ji, double *E) {
+static void ohm_with(const hvo_grid *g, const double *B, const double *n, const double *Ji,
+                     const double *pe_field, double *E) {
   int64_t nce = ncell_of(g);
   double *J = (double *)malloc(sizeof(double) * 3 * nce);
   double *LJ = (double *)malloc(sizeof(double) * 3 * nce);
@@ -359,7 +371,7 @@ void hvo_ohm(const hvo_grid *g, const double *B, const double *n, const double *
   hvo_lap(g, J, 3, LJ);
   for (int64_t c = 0; c < nce; ++c) {
     nf[c] = n[c] > g->n_floor ? n[c] : g->n_floor;
-    pe[c] = g->Te * pow(nf[c], g->gamma_e);
+    pe[c] = pe_field ? pe_field[c] : g->Te * pow(nf[c], g->gamma_e);
   }
   hvo_grad(g, pe, gp);
   for (int64_t c = 0; c < nce; ++c) {
@@ -378,6 +390,56 @@ void hvo_ohm(const hvo_grid *g, const double *B, const double *n, const double *
   free(nf);
   free(pe);
   free(gp);
+}
+
+void hvo_ohm(const hvo_grid *g, const double *B, const double *n, const double *Ji, double *E) {
+  ohm_with(g, B, n, Ji, NULL, E);
+}
+
+/* Ohm's law with p_e taken from the field pe [ncell] (R16). */
+void hvo_ohm_pe(const hvo_grid *g, const double *B, const double *n, const double *Ji,
+                const double *pe, double *E) {
+  ohm_with(g, B, n, Ji, pe, E);
+}
+
+/* Electron energy equation (Sec. 2.1, Eq. dpdt; reading R16):
+ *   out = -gamma div(p_e u_e) + (gamma - 1) u_e . grad p_e
+ *         + (gamma - 1) kappa lap(T_e),
+ *   u_e = -(curl B - J_i) / n_f,  T_e = p_e / n_f. */
+void hvo_dpdt(const hvo_grid *g, const double *B, const double *pe, const double *n,
+              const double *Ji, double *out) {
+  int64_t nce = ncell_of(g);
+  double gam = g->gamma_e;
+  double *J = (double *)malloc(sizeof(double) * 3 * nce);
+  double *ue = (double *)malloc(sizeof(double) * 3 * nce);
+  double *pu = (double *)malloc(sizeof(double) * 3 * nce);
+  double *T = (double *)malloc(sizeof(double) * nce);
+  double *divpu = (double *)malloc(sizeof(double) * nce);
+  double *gp = (double *)malloc(sizeof(double) * 3 * nce);
+  double *lT = (double *)malloc(sizeof(double) * nce);
+  hvo_curl(g, B, J);
+  for (int64_t c = 0; c < nce; ++c) {
+    double nf = n[c] > g->n_floor ? n[c] : g->n_floor;
+    for (int a = 0; a < 3; ++a) {
+      ue[a * nce + c] = -(J[a * nce + c] - Ji[a * nce + c]) / nf;
+      pu[a * nce + c] = pe[c] * ue[a * nce + c];
+    }
+    T[c] = pe[c] / nf;
+  }
+  hvo_div(g, pu, divpu);
+  hvo_grad(g, pe, gp);
+  hvo_lap(g, T, 1, lT);
+  for (int64_t c = 0; c < nce; ++c) {
+    double ugp = ue[c] * gp[c] + ue[nce + c] * gp[nce + c] + ue[2 * nce + c] * gp[2 * nce + c];
+    out[c] = -gam * divpu[c] + (gam - 1.0) * ugp + (gam - 1.0) * g->kappa * lT[c];
+  }
+  free(J);
+  free(ue);
+  free(pu);
+  free(T);
+  free(divpu);
+  free(gp);
+  free(lT);
 }
 
 /* Faraday's law (Eq. 5) subcycled nsub times per particle step (Sec. 2.1),
@@ -401,6 +463,38 @@ void hvo_field_advance(const hvo_grid *g, double *B, const double *n, const doub
   free(E);
   free(cE);
   free(Bs);
+}
+
+/* The same subcycles with the electron energy equation (R16): B and p_e
+ * advance together,
+ *   B* = B - (h/2) curl E(B, p_e),  p_e* = p_e + (h/2) dpdt(B, p_e),
+ *   B <- B - h curl E(B*, p_e*),    p_e <- p_e + h dpdt(B*, p_e*). */
+void hvo_field_advance_pe(const hvo_grid *g, double *B, double *pe, const double *n,
+                          const double *Ji) {
+  int64_t nce = ncell_of(g);
+  double h = g->dt / (double)g->nsub;
+  double *E = (double *)malloc(sizeof(double) * 3 * nce);
+  double *cE = (double *)malloc(sizeof(double) * 3 * nce);
+  double *Bs = (double *)malloc(sizeof(double) * 3 * nce);
+  double *dp = (double *)malloc(sizeof(double) * nce);
+  double *ps = (double *)malloc(sizeof(double) * nce);
+  for (int64_t s = 0; s < g->nsub; ++s) {
+    hvo_ohm_pe(g, B, n, Ji, pe, E);
+    hvo_curl(g, E, cE);
+    hvo_dpdt(g, B, pe, n, Ji, dp);
+    for (int64_t c = 0; c < 3 * nce; ++c) Bs[c] = B[c] - 0.5 * h * cE[c];
+    for (int64_t c = 0; c < nce; ++c) ps[c] = pe[c] + 0.5 * h * dp[c];
+    hvo_ohm_pe(g, Bs, n, Ji, ps, E);
+    hvo_curl(g, E, cE);
+    hvo_dpdt(g, Bs, ps, n, Ji, dp);
+    for (int64_t c = 0; c < 3 * nce; ++c) B[c] = B[c] - h * cE[c];
+    for (int64_t c = 0; c < nce; ++c) pe[c] = pe[c] + h * dp[c];
+  }
+  free(E);
+  free(cE);
+  free(Bs);
+  free(dp);
+  free(ps);
 }
 
 /* Separable binomial (1/4, 1/2, 1/4) smoothing, `passes` times, of nc
@@ -465,6 +559,19 @@ void hvo_init(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const doubl
   hvo_ohm(g, B, n_prev, J_prev, E);
 }
 
+/* Start-up with the electron energy equation (R16): as hvo_init, and
+ * p_e = Te n_f^gamma of the start-up moments (Eq. 6). */
+void hvo_init_pe(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const double *B,
+                 double *E, double *pe, double *n_prev, double *J_prev) {
+  int64_t nce = ncell_of(g);
+  hvo_init(g, sp, nsp, B, E, n_prev, J_prev);
+  for (int64_t c = 0; c < nce; ++c) {
+    double nf = n_prev[c] > g->n_floor ? n_prev[c] : g->n_floor;
+    pe[c] = g->Te * pow(nf, g->gamma_e);
+  }
+  hvo_ohm_pe(g, B, n_prev, J_prev, pe, E);
+}
+
 /* One full step n -> n+1 in the paper's order (Sec. 2.2):
  *   [field smoothing of the gathered copies of E, B (R15)],
  *   push + half-step deposit,  smoothing,  extrapolation (Eq. 11),
@@ -472,8 +579,9 @@ void hvo_init(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const doubl
  *   E^{n+1} = Ohm(B^{n+1}, n^{n+1}, J^{n+1}),  prev := half-step moments.
  * On return n_prev, J_prev hold n^{n+1/2}, J^{n+1/2}.  n_ext, J_ext (may be
  * NULL) receive the extrapolated n^{n+1}, J^{n+1}. */
-void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double *E,
-              double *n_prev, double *J_prev, double *n_ext, double *J_ext, hvo_diag *dg) {
+static void step_impl(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double *E,
+                      double *pe, double *n_prev, double *J_prev, double *n_ext, double *J_ext,
+                      hvo_diag *dg) {
   int64_t nce = ncell_of(g);
   double *nh = (double *)calloc((size_t)nce, sizeof(double));
   double *Jh = (double *)calloc((size_t)(3 * nce), sizeof(double));
@@ -499,8 +607,13 @@ void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double
   hvo_smooth(g, Jh, 3, g->smooth_passes);
   hvo_extrapolate(nce, nh, n_prev, ne);
   hvo_extrapolate(3 * nce, Jh, J_prev, Je);
-  hvo_field_advance(g, B, nh, Jh);
-  hvo_ohm(g, B, ne, Je, E);
+  if (pe) {
+    hvo_field_advance_pe(g, B, pe, nh, Jh);
+    hvo_ohm_pe(g, B, ne, Je, pe, E);
+  } else {
+    hvo_field_advance(g, B, nh, Jh);
+    hvo_ohm(g, B, ne, Je, E);
+  }
   memcpy(n_prev, nh, sizeof(double) * nce);
   memcpy(J_prev, Jh, sizeof(double) * 3 * nce);
   if (n_ext) memcpy(n_ext, ne, sizeof(double) * nce);
@@ -520,6 +633,19 @@ void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double
   free(Jh);
   free(ne);
   free(Je);
+}
+
+void hvo_step(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double *E,
+              double *n_prev, double *J_prev, double *n_ext, double *J_ext, hvo_diag *dg) {
+  step_impl(g, sp, nsp, B, E, NULL, n_prev, J_prev, n_ext, J_ext, dg);
+}
+
+/* One step with the electron energy equation (R16): p_e [ncell] is advanced
+ * with B and enters Ohm's law. */
+void hvo_step_pe(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B, double *E,
+                 double *pe, double *n_prev, double *J_prev, double *n_ext, double *J_ext,
+                 hvo_diag *dg) {
+  step_impl(g, sp, nsp, B, E, pe, n_prev, J_prev, n_ext, J_ext, dg);
 }
 
 /* Stable counting sort of keys in [0, nkeys): counts[k], exclusive offsets
