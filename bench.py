@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--smooth", type=int, default=0,
                     help="binomial passes on the moments and on the gathered E, B "
                          "(self-consistent smoothing, Sec. 2.2)")
+    ap.add_argument("--pe-eq", action="store_true",
+                    help="electron energy equation (Sec. 2.1) with gamma_e = 5/3 and "
+                         "kappa = 0.01 instead of the equation of state")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -85,6 +88,8 @@ def apply_overrides(wl, args):
     if args.smooth:
         wl.params["smooth_passes"] = args.smooth
         wl.params["field_smooth_passes"] = args.smooth
+    if args.pe_eq:
+        wl.params.update(pe_eq=1, kappa=0.01, gamma_e=5.0 / 3.0)
     return wl
 
 
@@ -248,7 +253,8 @@ def oracle_strip_rate(wl, rows: int, steps: int):
     B = wl.B0[:, k0:k0 + rows].astype(np.float64).reshape(3, -1)
     g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
                     p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
-                    p["smooth_passes"], p.get("field_smooth_passes", 0))
+                    p["smooth_passes"], p.get("field_smooth_passes", 0), p.get("pe_eq", 0),
+                    p.get("kappa", 0.0))
     sim = O.Sim(g, [sp], B)
     times = []
     for i in range(steps):
@@ -361,7 +367,9 @@ def run_ours(args, world, rank, local):
                                    f"dx={p['dx']}, {n_ions} ions/GPU, shape {args.shape}, "
                                    f"nsub={p['nsub']}, sort every {p['sort_every']}"
                                    + (f", {p['smooth_passes']} smoothing passes on the moments "
-                                      f"and the gathered fields" if args.smooth else ""),
+                                      f"and the gathered fields" if args.smooth else "")
+                                   + (", electron energy equation (gamma_e 5/3, kappa 0.01)"
+                                      if args.pe_eq else ""),
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (ions %.2f GB/GPU)" % (
                            n_ions * (28 if p['ny'] == 1 else 32) / 1e9)},

@@ -61,7 +61,7 @@ typedef enum {
 
 typedef enum { HV_SHAPE_NGP = 0, HV_SHAPE_QS = 1, HV_SHAPE_CIC = 2 } hv_shape;
 
-/* Simulation parameters (Secs. 2.1-2.2).  Layout is fixed (112 bytes). */
+/* Simulation parameters (Secs. 2.1-2.2).  Layout is fixed (128 bytes). */
 typedef struct {
   int32_t nx, ny, nz;   /* cells per axis, each >= 1, nx*ny*nz < 2^31 */
   int32_t nsub;         /* field subcycles per particle step (Sec. 2.1), >= 1 */
@@ -79,6 +79,11 @@ typedef struct {
                            field smoothing of Sec. 2.2); the field state is
                            not smoothed; 0 off, at most 64 */
   uint64_t seed;        /* reserved for stochastic extensions */
+  int32_t pe_eq;        /* 1: the electron pressure is a field advanced with
+                           the electron energy equation (Sec. 2.1, Eq. dpdt)
+                           in the field subcycles; 0: p_e = Te n^gamma_e */
+  int32_t reserved;     /* must be 0 */
+  double kappa;         /* heat conductivity of that equation (>= 0) */
 } hv_params;
 
 /* FP64 diagnostics of the last completed step (or of the start-up state). */
@@ -161,6 +166,12 @@ hv_status hv_step(hv_ctx *ctx, int32_t nsteps);
  * the stream and reports latched device errors. */
 hv_status hv_moments(hv_ctx *ctx, float *n_out, float *J_out, float *E_out, float *B_out,
                      int on_device);
+
+/* Copy the electron pressure field p_e^n [nz][ny][nx] out (Sec. 2.1, Eq.
+ * dpdt), when the context was created with pe_eq = 1 (HV_EINVAL otherwise;
+ * HV_EINVAL also for a NULL pe_out).  on_device: pe_out is device memory.
+ * Synchronises the stream and reports latched device errors. */
+hv_status hv_electron_pressure(hv_ctx *ctx, float *pe_out, int on_device);
 
 /* FP64 diagnostics of the state after the last step (Secs. 2.1-2.2).
  * Synchronises; returns HV_ECFL / HV_ENAN when the error word or a

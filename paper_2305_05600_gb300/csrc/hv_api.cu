@@ -100,6 +100,24 @@ hv_status check_params(const hv_params *p) {
   if (p->sort_every < 0) return fail(HV_EINVAL, "sort_every must be >= 0");
   if (p->field_smooth_passes < 0 || p->field_smooth_passes > 64)
     return fail(HV_EINVAL, "field_smooth_passes in [0, 64]");
+  if (p->pe_eq != 0 && p->pe_eq != 1) return fail(HV_EINVAL, "pe_eq must be 0 or 1");
+  if (p->reserved != 0) return fail(HV_EINVAL, "reserved must be 0");
+  if (!std::isfinite(p->kappa) || p->kappa < 0) return fail(HV_EINVAL, "kappa must be finite and >= 0");
+  if (p->pe_eq && p->kappa > 0) {
+    // explicit heat conduction at the density floor: the explicit-midpoint
+    // step is stable for h (gamma - 1) kappa / n_floor * sum 4 / Delta^2 <= 2
+    double s2 = 0;
+    if (p->nx > 1) s2 += 4.0 / (p->dx * p->dx);
+    if (p->ny > 1) s2 += 4.0 / (p->dy * p->dy);
+    if (p->nz > 1) s2 += 4.0 / (p->dz * p->dz);
+    const double r = p->dt / p->nsub * (p->gamma_e - 1.0) * p->kappa / p->n_floor * s2;
+    if (r > 2.0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "heat-conduction limit violated: h (gamma-1) kappa / n_floor * "
+               "sum 4/dx^2 = %g > 2", r);
+      return fail(HV_ECFL, buf);
+    }
+  }
   // whistler limit Omega_ci h < Delta^2 / pi (Sec. 2.1) for the field step h
   double dmin = 1e300;
   if (p->nx > 1) dmin = std::fmin(dmin, p->dx);
@@ -238,6 +256,10 @@ hv_status startup(hv_ctx *c) {
   }
   cudaError_t e = launch_moments(c, 1);
   if (e != cudaSuccess) return cuda_fail(e, "start-up moments");
+  if (c->p.pe_eq) {
+    e = launch_pe_init(c);
+    if (e != cudaSuccess) return cuda_fail(e, "start-up electron pressure");
+  }
   e = launch_ohm_final(c, c->mext);
   if (e != cudaSuccess) return cuda_fail(e, "start-up Ohm");
   c->started = 1;
@@ -345,6 +367,10 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
   for (int b = 0; b < 2; ++b)
     c->accm[b] = rec ? (float *)ctx_alloc(c, sizeof(float) * kMono * npad) : nullptr;
+  if (p->pe_eq) {
+    c->pe = (float *)ctx_alloc(c, sizeof(float) * nc);
+    c->pes = (float *)ctx_alloc(c, sizeof(float) * nc);
+  }
   const bool fsm = p->field_smooth_passes > 0;
   if (fsm) {
     c->EBs = (float4 *)ctx_alloc(c, sizeof(float4) * 2 * npad);
@@ -353,7 +379,8 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
       !c->pushpart || !c->gridpart || !c->diag_dev || !c->err ||
       (rec && (!c->accm[0] || !c->accm[1])) ||
-      (fsm && (!c->EBs || !c->fsm[0] || !c->fsm[1] || !c->fsm[2] || !c->fsm[3]))) {
+      (fsm && (!c->EBs || !c->fsm[0] || !c->fsm[1] || !c->fsm[2] || !c->fsm[3])) ||
+      (p->pe_eq && (!c->pe || !c->pes))) {
     hv_destroy(c);
     return fail(HV_ENOMEM, "grid allocation failed");
   }
@@ -559,7 +586,13 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       l0 = c->launches;
     }
     for (int k = 0; k < c->p.nsub; ++k) {
-      if (fused_substeps(c)) {
+      if (c->p.pe_eq) {
+        // B and p_e together (electron energy equation); stage 2 writes in
+        // place over its own base cells only
+        e = launch_field_stage_pe(c, c->B, c->B, c->Bs, c->pe, c->pe, c->pes, 0.5f * h);
+        if (e == cudaSuccess)
+          e = launch_field_stage_pe(c, c->Bs, c->B, c->B, c->pes, c->pe, c->pe, h);
+      } else if (fused_substeps(c)) {
         // B and B* alternate so that a substep never writes what it reads
         e = launch_substep(c, (k & 1) ? c->Bs : c->B, (k & 1) ? c->B : c->Bs, h);
       } else {
@@ -568,7 +601,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       }
       if (e != cudaSuccess) return cuda_fail(e, "field stage");
     }
-    if (fused_substeps(c) && (c->p.nsub & 1)) {
+    if (!c->p.pe_eq && fused_substeps(c) && (c->p.nsub & 1)) {
       // an odd number of fused substeps leaves B^{n+1} in B*: copy it back
       e = cudaMemcpyAsync(c->B, c->Bs, sizeof(float4) * c->g.ncell, cudaMemcpyDeviceToDevice,
                           c->stream);
@@ -621,6 +654,20 @@ hv_status hv_moments(hv_ctx *c, float *n_out, float *J_out, float *E_out, float 
   }
   dev_free(tmp, sizeof(float) * 4 * nc, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "hv_moments");
+  return latched(c, nullptr);
+}
+
+hv_status hv_electron_pressure(hv_ctx *c, float *pe_out, int on_device) {
+  if (!c || !pe_out) return fail(HV_EINVAL, "ctx or pe_out is NULL");
+  if (!c->p.pe_eq) return fail(HV_EINVAL, "the context has no electron pressure field (pe_eq = 0)");
+  if (!c->started) {
+    hv_status st = startup(c);
+    if (st != HV_OK) return st;
+  }
+  cudaError_t e = cudaMemcpyAsync(pe_out, c->pe, sizeof(float) * (size_t)c->g.ncell,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_electron_pressure");
   return latched(c, nullptr);
 }
 

@@ -207,6 +207,8 @@ struct hv_ctx {
   double *tr_loss;
   int tr_step;
   float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}
+  float *pe, *pes;      // interior [ncell] electron pressure and its stage
+                        // value (pe_eq = 1 only, else null)
   float4 *mhalf, *mext, *mprev, *mtmp;  // interior moments {n,Jx,Jy,Jz}
   double *pushpart;     // [kMaxSpecies][push_blocks][4]
   double *gridpart;     // [grid_blocks][4]
@@ -246,6 +248,9 @@ bool uses_records(const hv_ctx *c);
 cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                float coef);
 cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
+cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
+                                  const float *pin, const float *pbase, float *pout, float coef);
+cudaError_t launch_pe_init(hv_ctx *c);
 const float4 *gather_array(const hv_ctx *c);
 // learned moment filter (x-z layout)
 cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out);

@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("eta_h", ctypes.c_double), ("n_floor", ctypes.c_double),
                 ("shape", ctypes.c_int32), ("smooth_passes", ctypes.c_int32),
                 ("sort_every", ctypes.c_int32), ("field_smooth_passes", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("pe_eq", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("kappa", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -68,7 +69,7 @@ class Info(ctypes.Structure):
                 ("n", ctypes.c_int64 * 8), ("step", ctypes.c_int64)]
 
 
-assert ctypes.sizeof(Params) == 112, ctypes.sizeof(Params)
+assert ctypes.sizeof(Params) == 128, ctypes.sizeof(Params)
 
 _lib = None
 _lock = threading.Lock()
@@ -82,7 +83,7 @@ EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_mo
            "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
            "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
-           "hv_filter_get_params",
+           "hv_filter_get_params", "hv_electron_pressure",
            "hv_last_error"]
 
 
@@ -107,6 +108,7 @@ def lib():
         L.hv_step.argtypes = [P, I32]
         L.hv_moments.argtypes = [P, P, P, P, P, ctypes.c_int]
         L.hv_diag.argtypes = [P, ctypes.POINTER(Diag)]
+        L.hv_electron_pressure.argtypes = [P, P, ctypes.c_int]
         L.hv_get_ions.argtypes = [P, I32, ctypes.POINTER(I64), P, P, P, P, ctypes.c_int]
         L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
         L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
@@ -173,7 +175,8 @@ def params_from(d: dict) -> Params:
                   float(d.get("eta_h", 0.0)), float(d.get("n_floor", 0.05)), shape,
                   int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)),
                   int(d.get("field_smooth_passes", 0)),
-                  int(d.get("seed", 0)))
+                  int(d.get("seed", 0)), int(d.get("pe_eq", 0)), 0,
+                  float(d.get("kappa", 0.0)))
 
 
 def _ptr(a):
@@ -263,6 +266,18 @@ def hv_moments(ctx: Ctx, n_out=None, J_out=None, E_out=None, B_out=None, host: b
     on_dev = max(devs)
     _check(lib().hv_moments(ctx.handle, *ptrs, on_dev))
     return {"n": n_out, "J": J_out, "E": E_out, "B": B_out}
+
+
+def hv_electron_pressure(ctx: Ctx, pe_out=None, host: bool = True):
+    """Copy the electron pressure field p_e [nz,ny,nx] out (contexts created
+    with pe_eq = 1).  With host=True and no output given, returns a numpy
+    array."""
+    p = ctx.params
+    if host and pe_out is None:
+        pe_out = np.zeros((p.nz, p.ny, p.nx), np.float32)
+    ptr, dev = _ptr(pe_out)
+    _check(lib().hv_electron_pressure(ctx.handle, ptr, dev))
+    return pe_out
 
 
 def hv_diag(ctx: Ctx, check: bool = True) -> dict:

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_function():
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(hv.Params) == 112
+    assert ctypes.sizeof(hv.Params) == 128
     assert ctypes.sizeof(hv.Diag) == 8 * 9 + 8
     assert ctypes.sizeof(hv.Prof) == 8 * 14
 
@@ -51,11 +51,19 @@ def _init_status(p):
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(nsub=0), dict(dx=-1.0), dict(dt=math.nan),
                                  dict(shape=5), dict(n_floor=0.0), dict(smooth_passes=-1),
                                  dict(Te=-1.0), dict(eta=-1e-3), dict(field_smooth_passes=-1),
-                                 dict(field_smooth_passes=65)])
+                                 dict(field_smooth_passes=65), dict(pe_eq=2),
+                                 dict(pe_eq=1, kappa=-1.0), dict(kappa=math.inf)])
 def test_init_rejects_bad_parameters_on_host(bad):
     rc, h = _init_status(_params(**bad))
     assert rc == hv.HV_EINVAL and not h
     assert len(hv.hv_last_error()) > 0
+
+
+def test_init_rejects_heat_conduction_limit_violation():
+    # h (gamma-1) kappa / n_floor * (4/dx^2 + 4/dz^2) = 0.001 * 2/3 * 10 / 0.05 * 32 = 4.3 > 2
+    rc, h = _init_status(_params(pe_eq=1, kappa=10.0, gamma_e=5.0 / 3.0))
+    assert rc == hv.HV_ECFL and not h
+    assert "heat" in hv.hv_last_error()
 
 
 def test_init_rejects_whistler_limit_violation():

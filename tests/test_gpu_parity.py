@@ -186,6 +186,41 @@ def test_field_smoothing_parity(hvmod, dim, shape):
     ctx.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_electron_energy_equation_parity(hvmod, dim):
+    """p_e advanced with the electron energy equation (adiabatic gamma =
+    5/3, heat conductivity 0.05) together with B in every subcycle."""
+    wl = small_workload(dim, "qs")
+    wl.params.update(pe_eq=1, kappa=0.05, gamma_e=5.0 / 3.0)
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    pe0 = hvmod.hv_electron_pressure(ctx).reshape(-1).astype(np.float64)
+    assert rel_l2(pe0, sim.pe) < 1e-6
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        pe = hvmod.hv_electron_pressure(ctx).reshape(-1).astype(np.float64)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
+        assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+        assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
+        assert rel_l2(pe, sim.pe) < 1e-6
+        assert rel_l2(pe - pe0, sim.pe - pe0) < 1e-3
+    ctx.close()
+
+
+def test_electron_pressure_needs_the_equation(hvmod):
+    wl = small_workload(2, "qs")
+    ctx = hvmod.load_workload(wl)
+    with pytest.raises(hvmod.HVError):
+        hvmod.hv_electron_pressure(ctx)
+    ctx.close()
+
+
 def test_quasi_1d_and_multispecies(hvmod):
     """nz = 1 (one-cell z axis) and two species with different q/m."""
     wl = I.whistler1d(nx=64, ppc=32, steps=1)
