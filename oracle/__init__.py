@@ -48,7 +48,7 @@ class Grid(ctypes.Structure):
                 ("eta", ctypes.c_double), ("eta_h", ctypes.c_double),
                 ("n_floor", ctypes.c_double), ("shape", ctypes.c_int64),
                 ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64),
-                ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double)]
+                ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double), ("es", ctypes.c_int64)]
 
 
 class _Species(ctypes.Structure):
@@ -118,10 +118,10 @@ def _f64(a) -> np.ndarray:
 
 def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
               eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0,
-              field_smooth_passes=0, pe_eq=0, kappa=0.0) -> Grid:
+              field_smooth_passes=0, pe_eq=0, kappa=0.0, es=0) -> Grid:
     s = SHAPES[shape] if isinstance(shape, str) else int(shape)
     return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
-                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa))
+                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa), int(es))
 
 
 def ncell(g: Grid) -> int:

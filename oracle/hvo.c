@@ -39,6 +39,11 @@
  *      the moments held at their half-step values; Ohm's law takes grad p_e
  *      from the field.  At start-up p_e = Te n_f^gamma of the start-up
  *      moments (Eq. 6).
+ *   R17 the optional electrostatic model (Sec. 3, Eq. esohm): Ohm's law
+ *      keeps only E = -grad p_e / n_f (R_ei = 0: no collision model here);
+ *      B is not advanced and stays at its initial value, which the ions
+ *      still feel; with the electron energy equation u_e = J_i / n_f (no
+ *      magnetic current).
  *   R15 the optional field smoothing (Sec. 2.2: a self-consistent field and
  *      moment smoother) applies the same operator S, field_smooth_passes
  *      times, to copies of E^n and B^n that the ions gather in the push;
@@ -76,6 +81,7 @@ typedef struct {
   int64_t field_smooth_passes; /* R15 */
   int64_t pe_eq;                /* R16: 1 = electron energy equation */
   double kappa;                 /* R16: heat conductivity */
+  int64_t es;                   /* R17: 1 = electrostatic Ohm's law */
 } hvo_grid;
 
 typedef struct {
@@ -375,6 +381,10 @@ static void ohm_with(const hvo_grid *g, const double *B, const double *n, const 
   }
   hvo_grad(g, pe, gp);
   for (int64_t c = 0; c < nce; ++c) {
+    if (g->es) {  /* R17: E = -grad p_e / n_f */
+      for (int a = 0; a < 3; ++a) E[a * nce + c] = -gp[a * nce + c] / nf[c];
+      continue;
+    }
     double b[3] = {B[c], B[nce + c], B[2 * nce + c]};
     double jt[3] = {J[c], J[nce + c], J[2 * nce + c]};
     double ui[3] = {Ji[c] / nf[c], Ji[nce + c] / nf[c], Ji[2 * nce + c] / nf[c]};
@@ -418,6 +428,7 @@ void hvo_dpdt(const hvo_grid *g, const double *B, const double *pe, const double
   double *gp = (double *)malloc(sizeof(double) * 3 * nce);
   double *lT = (double *)malloc(sizeof(double) * nce);
   hvo_curl(g, B, J);
+  if (g->es) memset(J, 0, sizeof(double) * 3 * nce); /* R17: no magnetic current */
   for (int64_t c = 0; c < nce; ++c) {
     double nf = n[c] > g->n_floor ? n[c] : g->n_floor;
     for (int a = 0; a < 3; ++a) {
@@ -447,6 +458,7 @@ void hvo_dpdt(const hvo_grid *g, const double *B, const double *pe, const double
  *   B* = B - (h/2) curl E(B),   B <- B - h curl E(B*).
  * n, Ji are held fixed (the half-step moments). */
 void hvo_field_advance(const hvo_grid *g, double *B, const double *n, const double *Ji) {
+  if (g->es) return; /* R17: B is not advanced */
   int64_t nce = ncell_of(g);
   double h = g->dt / (double)g->nsub;
   double *E = (double *)malloc(sizeof(double) * 3 * nce);
@@ -482,11 +494,13 @@ void hvo_field_advance_pe(const hvo_grid *g, double *B, double *pe, const double
     hvo_ohm_pe(g, B, n, Ji, pe, E);
     hvo_curl(g, E, cE);
     hvo_dpdt(g, B, pe, n, Ji, dp);
+    if (g->es) memset(cE, 0, sizeof(double) * 3 * nce); /* R17: B is not advanced */
     for (int64_t c = 0; c < 3 * nce; ++c) Bs[c] = B[c] - 0.5 * h * cE[c];
     for (int64_t c = 0; c < nce; ++c) ps[c] = pe[c] + 0.5 * h * dp[c];
     hvo_ohm_pe(g, Bs, n, Ji, ps, E);
     hvo_curl(g, E, cE);
     hvo_dpdt(g, Bs, ps, n, Ji, dp);
+    if (g->es) memset(cE, 0, sizeof(double) * 3 * nce);
     for (int64_t c = 0; c < 3 * nce; ++c) B[c] = B[c] - h * cE[c];
     for (int64_t c = 0; c < nce; ++c) pe[c] = pe[c] + h * dp[c];
   }

@@ -1,7 +1,8 @@
 """Pins of the oracle's electron energy equation (Sec. 2.1, Eq. dpdt; reading
 R16):  dp_e/dt = -gamma div(p_e u_e) + (gamma - 1) u_e . grad p_e
 + (gamma - 1) kappa lap(T_e),  u_e = -(curl B - J_i)/n_f,  T_e = p_e / n_f,
-advanced with B in explicit-midpoint subcycles.
+advanced with B in explicit-midpoint subcycles; and of the electrostatic
+model (Sec. 3, Eq. esohm; reading R17): E = -grad p_e / n_f, B not advanced.
 
 Closed forms on the cell-centred grid (centred differences, Eq. 12): the
 centred derivative of exp(i k x) is i sin(k dx)/dx exp(i k x) and the
@@ -130,3 +131,49 @@ def test_ohm_uses_the_pressure_field():
     E = O.ohm_pe(g, np.zeros((3, nc)), np.full(nc, n0), np.zeros((3, nc)), pe)
     assert np.abs(E[0] + 0.05 * np.cos(k * x) * math.sin(k * g.dx) / g.dx / n0).max() < 1e-14
     assert np.abs(E[1:]).max() == 0.0
+
+
+# ----------------------------------------------------------------------------
+# electrostatic model (Sec. 3, Eq. esohm; reading R17)
+# ----------------------------------------------------------------------------
+
+def es_grid(pe_eq=1, nsub=4):
+    return O.make_grid(24, 1, 16, 0.5, 1.0, 0.5, 0.02, nsub=nsub, Te=0.1, gamma_e=GAM, eta=1e-3,
+                       eta_h=1e-4, n_floor=0.05, shape="qs", pe_eq=pe_eq, kappa=0.0, es=1)
+
+
+def test_electrostatic_ohm_keeps_only_the_pressure_gradient():
+    """Whatever B and J_i are, E = -grad p_e / n_f."""
+    g = es_grid()
+    nc = g.nx * g.nz
+    rng = np.random.default_rng(5)
+    x, _ = centres(g)
+    k = 2 * math.pi / (g.nx * g.dx)
+    n0 = 1.4
+    pe = 0.4 + 0.05 * np.sin(k * x)
+    E = O.ohm_pe(g, rng.normal(size=(3, nc)), np.full(nc, n0), rng.normal(size=(3, nc)), pe)
+    assert np.abs(E[0] + 0.05 * np.cos(k * x) * math.sin(k * g.dx) / g.dx / n0).max() < 1e-14
+    assert np.abs(E[1:]).max() < 1e-15
+
+
+def test_electrostatic_field_advance_keeps_B_and_moves_p_with_the_ions():
+    """B is not advanced; u_e = J_i / n_f, whatever curl B is."""
+    g = es_grid()
+    nc = g.nx * g.nz
+    rng = np.random.default_rng(6)
+    x, _ = centres(g)
+    k = 2 * math.pi * 2 / (g.nx * g.dx)
+    u0, p0, dl = 0.8, 0.5, 0.01
+    B = rng.normal(size=(3, nc))
+    n = np.ones(nc)
+    Ji = np.zeros((3, nc))
+    Ji[0] = u0
+    pe = p0 + dl * np.sin(k * x)
+    h = g.dt / g.nsub
+    lam = -1j * u0 * math.sin(k * g.dx) / g.dx
+    G = (1 + lam * h + (lam * h) ** 2 / 2) ** g.nsub
+    B1, p1 = O.field_advance_pe(g, B, pe, n, Ji)
+    assert np.array_equal(B1, B)
+    assert np.abs(p1 - (p0 + dl * np.imag(G * np.exp(1j * k * x)))).max() < 1e-14
+    g0 = es_grid(pe_eq=0)
+    assert np.array_equal(O.field_advance(g0, B, n, Ji), B)
