@@ -254,7 +254,7 @@ def oracle_strip_rate(wl, rows: int, steps: int):
     g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
                     p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
                     p["smooth_passes"], p.get("field_smooth_passes", 0), p.get("pe_eq", 0),
-                    p.get("kappa", 0.0))
+                    p.get("kappa", 0.0), p.get("electrostatic", 0))
     sim = O.Sim(g, [sp], B)
     times = []
     for i in range(steps):

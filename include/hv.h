@@ -82,7 +82,9 @@ typedef struct {
   int32_t pe_eq;        /* 1: the electron pressure is a field advanced with
                            the electron energy equation (Sec. 2.1, Eq. dpdt)
                            in the field subcycles; 0: p_e = Te n^gamma_e */
-  int32_t reserved;     /* must be 0 */
+  int32_t electrostatic;/* 1: electrostatic Ohm's law E = -grad p_e / n_e
+                           (Sec. 3, Eq. esohm, without collision terms); B is
+                           then not advanced and keeps its loaded value */
   double kappa;         /* heat conductivity of that equation (>= 0) */
 } hv_params;
 

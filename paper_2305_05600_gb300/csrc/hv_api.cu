@@ -101,7 +101,8 @@ hv_status check_params(const hv_params *p) {
   if (p->field_smooth_passes < 0 || p->field_smooth_passes > 64)
     return fail(HV_EINVAL, "field_smooth_passes in [0, 64]");
   if (p->pe_eq != 0 && p->pe_eq != 1) return fail(HV_EINVAL, "pe_eq must be 0 or 1");
-  if (p->reserved != 0) return fail(HV_EINVAL, "reserved must be 0");
+  if (p->electrostatic != 0 && p->electrostatic != 1)
+    return fail(HV_EINVAL, "electrostatic must be 0 or 1");
   if (!std::isfinite(p->kappa) || p->kappa < 0) return fail(HV_EINVAL, "kappa must be finite and >= 0");
   if (p->pe_eq && p->kappa > 0) {
     // explicit heat conduction at the density floor: the explicit-midpoint
@@ -123,7 +124,8 @@ hv_status check_params(const hv_params *p) {
   if (p->nx > 1) dmin = std::fmin(dmin, p->dx);
   if (p->ny > 1) dmin = std::fmin(dmin, p->dy);
   if (p->nz > 1) dmin = std::fmin(dmin, p->dz);
-  if (dmin < 1e300 && p->dt / p->nsub >= dmin * dmin / M_PI) {
+  // (the electrostatic model has no Hall term and no whistler)
+  if (!p->electrostatic && dmin < 1e300 && p->dt / p->nsub >= dmin * dmin / M_PI) {
     char buf[160];
     snprintf(buf, sizeof buf, "whistler limit violated: dt/nsub = %g >= dx^2/pi = %g",
              p->dt / p->nsub, dmin * dmin / M_PI);
@@ -585,7 +587,9 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       ev.launches[2] = c->launches - l0;
       l0 = c->launches;
     }
-    for (int k = 0; k < c->p.nsub; ++k) {
+    // the electrostatic model advances no B: only p_e, if it is a field
+    const int nsub_run = c->p.electrostatic && !c->p.pe_eq ? 0 : c->p.nsub;
+    for (int k = 0; k < nsub_run; ++k) {
       if (c->p.pe_eq) {
         // B and p_e together (electron energy equation); stage 2 writes in
         // place over its own base cells only
@@ -601,7 +605,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       }
       if (e != cudaSuccess) return cuda_fail(e, "field stage");
     }
-    if (!c->p.pe_eq && fused_substeps(c) && (c->p.nsub & 1)) {
+    if (!c->p.pe_eq && nsub_run > 0 && fused_substeps(c) && (c->p.nsub & 1)) {
       // an odd number of fused substeps leaves B^{n+1} in B*: copy it back
       e = cudaMemcpyAsync(c->B, c->Bs, sizeof(float4) * c->g.ncell, cudaMemcpyDeviceToDevice,
                           c->stream);

@@ -212,6 +212,7 @@ struct FieldConsts {
   float ilx, ily, ilz;          // 1 / Delta^2 per axis (0 on single-cell axes)
   float Te, gamma_e, eta, eta_h, n_floor;
   float kappa;                  // heat conductivity of the electron energy equation
+  int es;                       // electrostatic Ohm's law, B held
   int isothermal;
 };
 
@@ -225,9 +226,10 @@ struct StageArgs {
   float coef;         // B_out = B_base - coef * curl E
   float4 *EB;         // final variant: padded gather array
   // electron energy equation (PEQ variants): p_e of the stage input, of the
-  // base and the output, p_out = p_base + coef * dp_e/dt
+  // base and the output, p_out = p_base + pcoef * dp_e/dt
   const float *pin, *pbase;
   float *pout;
+  float pcoef;
 };
 
 // Output tile and halos.  FINAL = 0: stage (E on halo 1, B on halo 3);
@@ -357,9 +359,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       ly_ += (Jy[jc + sJy] + Jy[jc - sJy] - 2.f * jy) * k.ily;
       lz_ += (Jz[jc + sJy] + Jz[jc - sJy] - 2.f * jz) * k.ily;
     }
-    const float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
-    const float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
-    const float ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz_;
+    float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
+    float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
+    float ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz_;
+    if (k.es) {  // electrostatic Ohm's law (Sec. 3): E = -grad p_e / n_f
+      ex = -gpx * inv;
+      ey = -gpy * inv;
+      ez = -gpz * inv;
+    }
     if (FINAL) {
       // interior cell of the tile: write E, B into the padded gather array
       // at the cell and at each of its ghost images
@@ -392,7 +399,10 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       Ez[r] = ez;
       if (PEQ) {
         // electron flow u_e = -(J - J_i) / n_f, p_e u_e and T_e = p_e / n_f
-        const float ux_e = -(jx - mi.y) * inv, uy_e = -(jy - mi.z) * inv, uz_e = -(jz - mi.w) * inv;
+        // (the electrostatic model has no magnetic current: u_e = J_i / n_f)
+        const float jxm = k.es ? 0.f : jx, jym = k.es ? 0.f : jy, jzm = k.es ? 0.f : jz;
+        const float ux_e = -(jxm - mi.y) * inv, uy_e = -(jym - mi.z) * inv,
+                    uz_e = -(jzm - mi.w) * inv;
         const float p = pe[jc];
         Ux[r] = ux_e;
         Uy[r] = uy_e;
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       }
       const float gm1 = k.gamma_e - 1.f;
       const float dpdt = -k.gamma_e * divpu + gm1 * ugp + gm1 * k.kappa * lapT;
-      a.pout[c] = a.pbase[c] + a.coef * dpdt;
+      a.pout[c] = a.pbase[c] + a.pcoef * dpdt;
     }
   }
 }
@@ -904,6 +914,7 @@ FieldConsts field_consts(const hv_ctx *c) {
   k.n_floor = (float)p.n_floor;
   k.isothermal = p.gamma_e == 1.0;
   k.kappa = (float)p.kappa;
+  k.es = p.electrostatic;
   return k;
 }
 
@@ -1069,6 +1080,7 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   a.EB = nullptr;
   a.pin = a.pbase = nullptr;
   a.pout = nullptr;
+  a.pcoef = 0.f;
   c->launches++;
   if (c->g.dim2) return launch_stage_t<2, 0>(c, a);
   const size_t smem = st3d::kFloats * sizeof(float);
@@ -1183,11 +1195,12 @@ cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bb
   a.Bbase = Bbase;
   a.Bout = Bout;
   a.mom = c->mprev;
-  a.coef = coef;
+  a.coef = c->p.electrostatic ? 0.f : coef;  // the electrostatic model holds B
   a.EB = nullptr;
   a.pin = pin;
   a.pbase = pbase;
   a.pout = pout;
+  a.pcoef = coef;
   c->launches++;
   return c->g.dim2 ? launch_stage_t<2, 0, 1>(c, a) : launch_stage_t<3, 0, 1>(c, a);
 }
@@ -1216,6 +1229,7 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
   a.pin = c->pe;
   a.pbase = nullptr;
   a.pout = nullptr;
+  a.pcoef = 0.f;
   c->launches++;
   cudaError_t e;
   if (c->p.pe_eq)

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
                 ("shape", ctypes.c_int32), ("smooth_passes", ctypes.c_int32),
                 ("sort_every", ctypes.c_int32), ("field_smooth_passes", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("pe_eq", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("kappa", ctypes.c_double)]
+                ("electrostatic", ctypes.c_int32), ("kappa", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -175,7 +175,7 @@ def params_from(d: dict) -> Params:
                   float(d.get("eta_h", 0.0)), float(d.get("n_floor", 0.05)), shape,
                   int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)),
                   int(d.get("field_smooth_passes", 0)),
-                  int(d.get("seed", 0)), int(d.get("pe_eq", 0)), 0,
+                  int(d.get("seed", 0)), int(d.get("pe_eq", 0)), int(d.get("electrostatic", 0)),
                   float(d.get("kappa", 0.0)))
 
 

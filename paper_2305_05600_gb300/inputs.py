@@ -68,11 +68,12 @@ class Workload:
 
 def base_params(nx, ny, nz, dx, dy, dz, dt, nsub, Te, eta=0.0, eta_h=0.0, n_floor=0.05,
                 shape="qs", smooth_passes=0, gamma_e=1.0, sort_every=20, field_smooth_passes=0,
-                pe_eq=0, kappa=0.0):
+                pe_eq=0, kappa=0.0, electrostatic=0):
     return dict(nx=nx, ny=ny, nz=nz, dx=dx, dy=dy if ny > 1 else 1.0, dz=dz, dt=dt,
                 nsub=nsub, Te=Te, gamma_e=gamma_e, eta=eta, eta_h=eta_h, n_floor=n_floor,
                 shape=shape, smooth_passes=smooth_passes, sort_every=sort_every,
-                field_smooth_passes=field_smooth_passes, pe_eq=pe_eq, kappa=kappa)
+                field_smooth_passes=field_smooth_passes, pe_eq=pe_eq, kappa=kappa,
+                electrostatic=electrostatic)
 
 
 def _rng(seed: int) -> np.random.Generator:

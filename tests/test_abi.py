@@ -52,7 +52,8 @@ def _init_status(p):
                                  dict(shape=5), dict(n_floor=0.0), dict(smooth_passes=-1),
                                  dict(Te=-1.0), dict(eta=-1e-3), dict(field_smooth_passes=-1),
                                  dict(field_smooth_passes=65), dict(pe_eq=2),
-                                 dict(pe_eq=1, kappa=-1.0), dict(kappa=math.inf)])
+                                 dict(pe_eq=1, kappa=-1.0), dict(kappa=math.inf),
+                                 dict(electrostatic=2)])
 def test_init_rejects_bad_parameters_on_host(bad):
     rc, h = _init_status(_params(**bad))
     assert rc == hv.HV_EINVAL and not h

@@ -213,6 +213,33 @@ def test_electron_energy_equation_parity(hvmod, dim):
     ctx.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("pe_eq", [0, 1])
+def test_electrostatic_parity(hvmod, dim, pe_eq):
+    """Electrostatic Ohm's law (E = -grad p_e / n_f); B keeps its loaded
+    value, with p_e from the equation of state or the energy equation."""
+    wl = small_workload(dim, "qs")
+    wl.params.update(electrostatic=1, pe_eq=pe_eq, kappa=0.05, gamma_e=5.0 / 3.0)
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    B0 = wl.B0.reshape(3, -1)
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        assert np.array_equal(m["B"].reshape(3, -1), B0)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
+        assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
+        if pe_eq:
+            pe = hvmod.hv_electron_pressure(ctx).reshape(-1).astype(np.float64)
+            assert rel_l2(pe, sim.pe) < 1e-6
+    ctx.close()
+
+
 def test_electron_pressure_needs_the_equation(hvmod):
     wl = small_workload(2, "qs")
     ctx = hvmod.load_workload(wl)
