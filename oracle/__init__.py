@@ -48,7 +48,9 @@ class Grid(ctypes.Structure):
                 ("eta", ctypes.c_double), ("eta_h", ctypes.c_double),
                 ("n_floor", ctypes.c_double), ("shape", ctypes.c_int64),
                 ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64),
-                ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double), ("es", ctypes.c_int64)]
+                ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double),
+                ("ohm_model", ctypes.c_int64), ("relativistic", ctypes.c_int64),
+                ("c_light", ctypes.c_double)]
 
 
 class _Species(ctypes.Structure):
@@ -80,6 +82,7 @@ def lib():
             L.hvo_shape.restype = ctypes.c_int
             L.hvo_gather.argtypes = [P, P, I64, I64, D, D, D, P]
             L.hvo_boris.argtypes = [D, P, P, P]
+            L.hvo_boris_rel.argtypes = [D, D, P, P, P]
             L.hvo_move.argtypes = [P, P, P, P, D]
             L.hvo_deposit.argtypes = [P, P, I64, P, P]
             L.hvo_push_deposit.argtypes = [P, P, I64, P, P, P, P, P]
@@ -118,10 +121,12 @@ def _f64(a) -> np.ndarray:
 
 def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
               eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0,
-              field_smooth_passes=0, pe_eq=0, kappa=0.0, es=0) -> Grid:
+              field_smooth_passes=0, pe_eq=0, kappa=0.0, ohm_model=0, relativistic=0,
+              c_light=0.0) -> Grid:
     s = SHAPES[shape] if isinstance(shape, str) else int(shape)
     return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
-                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa), int(es))
+                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa), int(ohm_model),
+                int(relativistic), float(c_light))
 
 
 def ncell(g: Grid) -> int:
@@ -194,6 +199,14 @@ def boris(qmdt: float, E, B, v) -> np.ndarray:
     v = _f64(v).copy()
     lib().hvo_boris(float(qmdt), _p(E), _p(B), _p(v))
     return v
+
+
+def boris_rel(qmdt: float, c: float, E, B, u) -> np.ndarray:
+    E = _f64(E)
+    B = _f64(B)
+    u = _f64(u).copy()
+    lib().hvo_boris_rel(float(qmdt), float(c), _p(E), _p(B), _p(u))
+    return u
 
 
 def move(g: Grid, cell: int, d, v, frac: float = 1.0):

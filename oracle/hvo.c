@@ -44,6 +44,14 @@
  *      B is not advanced and stays at its initial value, which the ions
  *      still feel; with the electron energy equation u_e = J_i / n_f (no
  *      magnetic current).
+ *   R18 the optional resistive-background model (App. A, kinetic-electron
+ *      beam): E = eta (curl B - J_k), J_k the deposited current of the
+ *      kinetic species; B advances with Faraday's law in the same subcycles.
+ *   R19 the optional relativistic push (Sec. 2.2, App. A): a particle
+ *      carries u = gamma v; Boris with t = (q dt / 2m) B / gamma^-,
+ *      gamma^- = sqrt(1 + |u^-|^2 / c^2); positions and currents use
+ *      v = u / gamma; the kinetic energy is m w (gamma - 1) c^2, written as
+ *      m w |u|^2 / (gamma + 1), and the momentum m w u.
  *   R15 the optional field smoothing (Sec. 2.2: a self-consistent field and
  *      moment smoother) applies the same operator S, field_smooth_passes
  *      times, to copies of E^n and B^n that the ions gather in the push;
@@ -81,7 +89,10 @@ typedef struct {
   int64_t field_smooth_passes; /* R15 */
   int64_t pe_eq;                /* R16: 1 = electron energy equation */
   double kappa;                 /* R16: heat conductivity */
-  int64_t es;                   /* R17: 1 = electrostatic Ohm's law */
+  int64_t ohm_model;            /* 0 hybrid (Eq. 2), 1 electrostatic (R17),
+                                   2 resistive background (R18) */
+  int64_t relativistic;         /* R19: relativistic Boris push */
+  double c_light;               /* R19: speed of light */
 } hvo_grid;
 
 typedef struct {
@@ -204,6 +215,31 @@ void hvo_boris(double qmdt, const double *E, const double *B, double *v) {
   for (int a = 0; a < 3; ++a) v[a] = vq[a] + h * E[a];
 }
 
+/* Relativistic Boris push (reading R19): u = gamma v in place,
+ *   u- = u + h E,  gamma- = sqrt(1 + |u-|^2 / c^2),  t = h B / gamma-,
+ *   rotation as in hvo_boris,  u <- u+ + h E,  h = q dt / 2m. */
+void hvo_boris_rel(double qmdt, double c, const double *E, const double *B, double *u) {
+  double h = 0.5 * qmdt;
+  double um[3], t[3], s[3], up[3], uq[3];
+  for (int a = 0; a < 3; ++a) um[a] = u[a] + h * E[a];
+  double gm = sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) / (c * c));
+  for (int a = 0; a < 3; ++a) t[a] = h * B[a] / gm;
+  double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + tt);
+  up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+  up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+  up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+  uq[0] = um[0] + (up[1] * s[2] - up[2] * s[1]);
+  uq[1] = um[1] + (up[2] * s[0] - up[0] * s[2]);
+  uq[2] = um[2] + (up[0] * s[1] - up[1] * s[0]);
+  for (int a = 0; a < 3; ++a) u[a] = uq[a] + h * E[a];
+}
+
+/* Lorentz factor of u = gamma v (R19). */
+static double lorentz(double c, const double *u) {
+  return sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (c * c));
+}
+
 /* Move a particle by v * (frac * dt) (Sec. 2.2, Eq. 10) in cell-index +
  * relative-coordinate form (reading R1): d <- d + 2 v frac dt / Delta,
  * shift m = floor((d+1)/2), d <- d - 2m, cell <- cell + m (periodic).
@@ -253,6 +289,10 @@ void hvo_deposit(const hvo_grid *g, const hvo_species *sp, int64_t nsp, double *
     for (int64_t p = 0; p < sp[s].n; ++p) {
       double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
       double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
+      if (g->relativistic) {  /* R19: the stored u = gamma v */
+        double gi = 1.0 / lorentz(g->c_light, v);
+        for (int a = 0; a < 3; ++a) v[a] *= gi;
+      }
       deposit_one(g, sp[s].cell[p], d, v, sp[s].q * sp[s].w[p], n, J);
     }
   }
@@ -275,7 +315,15 @@ void hvo_push_deposit(const hvo_grid *g, hvo_species *sp, int64_t nsp,
       double Ep[3], Bp[3];
       hvo_gather(g, E, 3, cell, d[0], d[1], d[2], Ep);
       hvo_gather(g, B, 3, cell, d[0], d[1], d[2], Bp);
-      hvo_boris(qmdt, Ep, Bp, v);
+      double u[3] = {v[0], v[1], v[2]}, gam = 1.0;
+      if (g->relativistic) {  /* R19 */
+        hvo_boris_rel(qmdt, g->c_light, Ep, Bp, u);
+        gam = lorentz(g->c_light, u);
+        for (int a = 0; a < 3; ++a) v[a] = u[a] / gam;
+      } else {
+        hvo_boris(qmdt, Ep, Bp, v);
+        for (int a = 0; a < 3; ++a) u[a] = v[a];
+      }
       /* half-step position for the deposit */
       int64_t ch = cell;
       double dh[3] = {d[0], d[1], d[2]};
@@ -287,14 +335,15 @@ void hvo_push_deposit(const hvo_grid *g, hvo_species *sp, int64_t nsp,
       sp[s].ox[p] = d[0];
       sp[s].oy[p] = d[1];
       sp[s].oz[p] = d[2];
-      sp[s].vx[p] = v[0];
-      sp[s].vy[p] = v[1];
-      sp[s].vz[p] = v[2];
+      sp[s].vx[p] = u[0];
+      sp[s].vy[p] = u[1];
+      sp[s].vz[p] = u[2];
       double mw = sp[s].m * sp[s].w[p];
-      kin[0] += 0.5 * mw * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      kin[1] += mw * v[0];
-      kin[2] += mw * v[1];
-      kin[3] += mw * v[2];
+      double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+      kin[0] += g->relativistic ? mw * uu / (gam + 1.0) : 0.5 * mw * uu;
+      kin[1] += mw * u[0];
+      kin[2] += mw * u[1];
+      kin[3] += mw * u[2];
     }
   }
 }
@@ -381,8 +430,12 @@ static void ohm_with(const hvo_grid *g, const double *B, const double *n, const 
   }
   hvo_grad(g, pe, gp);
   for (int64_t c = 0; c < nce; ++c) {
-    if (g->es) {  /* R17: E = -grad p_e / n_f */
+    if (g->ohm_model == 1) {  /* R17: E = -grad p_e / n_f */
       for (int a = 0; a < 3; ++a) E[a * nce + c] = -gp[a * nce + c] / nf[c];
+      continue;
+    }
+    if (g->ohm_model == 2) {  /* R18: E = eta (curl B - J_k) */
+      for (int a = 0; a < 3; ++a) E[a * nce + c] = g->eta * (J[a * nce + c] - Ji[a * nce + c]);
       continue;
     }
     double b[3] = {B[c], B[nce + c], B[2 * nce + c]};
@@ -428,7 +481,7 @@ void hvo_dpdt(const hvo_grid *g, const double *B, const double *pe, const double
   double *gp = (double *)malloc(sizeof(double) * 3 * nce);
   double *lT = (double *)malloc(sizeof(double) * nce);
   hvo_curl(g, B, J);
-  if (g->es) memset(J, 0, sizeof(double) * 3 * nce); /* R17: no magnetic current */
+  if (g->ohm_model == 1) memset(J, 0, sizeof(double) * 3 * nce); /* R17: no magnetic current */
   for (int64_t c = 0; c < nce; ++c) {
     double nf = n[c] > g->n_floor ? n[c] : g->n_floor;
     for (int a = 0; a < 3; ++a) {
@@ -458,7 +511,7 @@ void hvo_dpdt(const hvo_grid *g, const double *B, const double *pe, const double
  *   B* = B - (h/2) curl E(B),   B <- B - h curl E(B*).
  * n, Ji are held fixed (the half-step moments). */
 void hvo_field_advance(const hvo_grid *g, double *B, const double *n, const double *Ji) {
-  if (g->es) return; /* R17: B is not advanced */
+  if (g->ohm_model == 1) return; /* R17: B is not advanced */
   int64_t nce = ncell_of(g);
   double h = g->dt / (double)g->nsub;
   double *E = (double *)malloc(sizeof(double) * 3 * nce);
@@ -494,13 +547,13 @@ void hvo_field_advance_pe(const hvo_grid *g, double *B, double *pe, const double
     hvo_ohm_pe(g, B, n, Ji, pe, E);
     hvo_curl(g, E, cE);
     hvo_dpdt(g, B, pe, n, Ji, dp);
-    if (g->es) memset(cE, 0, sizeof(double) * 3 * nce); /* R17: B is not advanced */
+    if (g->ohm_model == 1) memset(cE, 0, sizeof(double) * 3 * nce); /* R17: B is not advanced */
     for (int64_t c = 0; c < 3 * nce; ++c) Bs[c] = B[c] - 0.5 * h * cE[c];
     for (int64_t c = 0; c < nce; ++c) ps[c] = pe[c] + 0.5 * h * dp[c];
     hvo_ohm_pe(g, Bs, n, Ji, ps, E);
     hvo_curl(g, E, cE);
     hvo_dpdt(g, Bs, ps, n, Ji, dp);
-    if (g->es) memset(cE, 0, sizeof(double) * 3 * nce);
+    if (g->ohm_model == 1) memset(cE, 0, sizeof(double) * 3 * nce);
     for (int64_t c = 0; c < 3 * nce; ++c) B[c] = B[c] - h * cE[c];
     for (int64_t c = 0; c < nce; ++c) pe[c] = pe[c] + h * dp[c];
   }

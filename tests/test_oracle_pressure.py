@@ -139,7 +139,7 @@ def test_ohm_uses_the_pressure_field():
 
 def es_grid(pe_eq=1, nsub=4):
     return O.make_grid(24, 1, 16, 0.5, 1.0, 0.5, 0.02, nsub=nsub, Te=0.1, gamma_e=GAM, eta=1e-3,
-                       eta_h=1e-4, n_floor=0.05, shape="qs", pe_eq=pe_eq, kappa=0.0, es=1)
+                       eta_h=1e-4, n_floor=0.05, shape="qs", pe_eq=pe_eq, kappa=0.0, ohm_model=1)
 
 
 def test_electrostatic_ohm_keeps_only_the_pressure_gradient():
