@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="harris2d",
                     choices=["harris2d", "harris2d_small", "alfven2d", "beam3d_small", "beam3d",
-                             "beam3d_2ppc", "harris3d", "harris3d_quarter"])
+                             "beam3d_2ppc", "harris3d", "harris3d_quarter", "ebeam2d"])
     ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
     ap.add_argument("--sort-every", type=int, default=None,
                     help="override the workload's sort interval")
@@ -79,6 +79,8 @@ def make_workload(name, shape, seed_offset=0):
         return I.harris3d(shape=shape, seed=3000 + seed_offset)
     if name == "harris3d_quarter":  # 256x128x128 cells, 32 ppc, 134M ions
         return I.harris3d(nx=256, ny=128, nz=128, shape=shape, seed=3000 + seed_offset)
+    if name == "ebeam2d":  # relativistic electron beam, resistive background, 640x320, 13.1M
+        return I.ebeam2d(shape=shape, seed=8000 + seed_offset)
     raise ValueError(name)
 
 
@@ -254,7 +256,8 @@ def oracle_strip_rate(wl, rows: int, steps: int):
     g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
                     p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
                     p["smooth_passes"], p.get("field_smooth_passes", 0), p.get("pe_eq", 0),
-                    p.get("kappa", 0.0), p.get("electrostatic", 0))
+                    p.get("kappa", 0.0), p.get("ohm_model", 0), p.get("relativistic", 0),
+                    p.get("c_light", 0.0))
     sim = O.Sim(g, [sp], B)
     times = []
     for i in range(steps):

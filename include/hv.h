@@ -61,7 +61,7 @@ typedef enum {
 
 typedef enum { HV_SHAPE_NGP = 0, HV_SHAPE_QS = 1, HV_SHAPE_CIC = 2 } hv_shape;
 
-/* Simulation parameters (Secs. 2.1-2.2).  Layout is fixed (128 bytes). */
+/* Simulation parameters (Secs. 2.1-2.2).  Layout is fixed (144 bytes). */
 typedef struct {
   int32_t nx, ny, nz;   /* cells per axis, each >= 1, nx*ny*nz < 2^31 */
   int32_t nsub;         /* field subcycles per particle step (Sec. 2.1), >= 1 */
@@ -82,10 +82,20 @@ typedef struct {
   int32_t pe_eq;        /* 1: the electron pressure is a field advanced with
                            the electron energy equation (Sec. 2.1, Eq. dpdt)
                            in the field subcycles; 0: p_e = Te n^gamma_e */
-  int32_t electrostatic;/* 1: electrostatic Ohm's law E = -grad p_e / n_e
-                           (Sec. 3, Eq. esohm, without collision terms); B is
-                           then not advanced and keeps its loaded value */
+  int32_t ohm_model;    /* 0: hybrid Ohm's law (Eq. 2);
+                           1: electrostatic E = -grad p_e / n_e (Sec. 3, Eq.
+                              esohm, without collision terms), B not advanced
+                              and kept at its loaded value;
+                           2: resistive background E = eta (curl B - J_k)
+                              (App. A), J_k the deposited current of the
+                              kinetic species */
   double kappa;         /* heat conductivity of that equation (>= 0) */
+  int32_t relativistic; /* 1: the particles carry u = gamma v (loaded and
+                           returned in place of v) and move with the
+                           relativistic Boris push (App. A) */
+  int32_t reserved;     /* must be 0 */
+  double c_light;       /* speed of light in the velocity unit, > 0 when
+                           relativistic (ignored otherwise) */
 } hv_params;
 
 /* FP64 diagnostics of the last completed step (or of the start-up state). */

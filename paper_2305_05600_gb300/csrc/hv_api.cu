@@ -101,8 +101,12 @@ hv_status check_params(const hv_params *p) {
   if (p->field_smooth_passes < 0 || p->field_smooth_passes > 64)
     return fail(HV_EINVAL, "field_smooth_passes in [0, 64]");
   if (p->pe_eq != 0 && p->pe_eq != 1) return fail(HV_EINVAL, "pe_eq must be 0 or 1");
-  if (p->electrostatic != 0 && p->electrostatic != 1)
-    return fail(HV_EINVAL, "electrostatic must be 0 or 1");
+  if (p->ohm_model < 0 || p->ohm_model > 2) return fail(HV_EINVAL, "ohm_model must be 0, 1 or 2");
+  if (p->relativistic != 0 && p->relativistic != 1)
+    return fail(HV_EINVAL, "relativistic must be 0 or 1");
+  if (p->relativistic && !finite_pos(p->c_light))
+    return fail(HV_EINVAL, "c_light must be finite and > 0 for the relativistic push");
+  if (p->reserved != 0) return fail(HV_EINVAL, "reserved must be 0");
   if (!std::isfinite(p->kappa) || p->kappa < 0) return fail(HV_EINVAL, "kappa must be finite and >= 0");
   if (p->pe_eq && p->kappa > 0) {
     // explicit heat conduction at the density floor: the explicit-midpoint
@@ -124,8 +128,22 @@ hv_status check_params(const hv_params *p) {
   if (p->nx > 1) dmin = std::fmin(dmin, p->dx);
   if (p->ny > 1) dmin = std::fmin(dmin, p->dy);
   if (p->nz > 1) dmin = std::fmin(dmin, p->dz);
-  // (the electrostatic model has no Hall term and no whistler)
-  if (!p->electrostatic && dmin < 1e300 && p->dt / p->nsub >= dmin * dmin / M_PI) {
+  if (p->ohm_model == 2 && p->eta > 0) {
+    // resistive diffusion of B: the explicit-midpoint step is stable for
+    // h eta sum 4 / Delta^2 <= 2 (centred curl of curl: sin^2 <= 1)
+    double s2 = 0;
+    if (p->nx > 1) s2 += 4.0 / (p->dx * p->dx);
+    if (p->ny > 1) s2 += 4.0 / (p->dy * p->dy);
+    if (p->nz > 1) s2 += 4.0 / (p->dz * p->dz);
+    const double r = p->dt / p->nsub * p->eta * s2;
+    if (r > 2.0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "resistive diffusion limit violated: h eta sum 4/dx^2 = %g > 2", r);
+      return fail(HV_ECFL, buf);
+    }
+  }
+  // (only the hybrid Ohm's law has the Hall term and its whistler)
+  if (p->ohm_model == 0 && dmin < 1e300 && p->dt / p->nsub >= dmin * dmin / M_PI) {
     char buf[160];
     snprintf(buf, sizeof buf, "whistler limit violated: dt/nsub = %g >= dx^2/pi = %g",
              p->dt / p->nsub, dmin * dmin / M_PI);
@@ -588,7 +606,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       l0 = c->launches;
     }
     // the electrostatic model advances no B: only p_e, if it is a field
-    const int nsub_run = c->p.electrostatic && !c->p.pe_eq ? 0 : c->p.nsub;
+    const int nsub_run = c->p.ohm_model == 1 && !c->p.pe_eq ? 0 : c->p.nsub;
     for (int k = 0; k < nsub_run; ++k) {
       if (c->p.pe_eq) {
         // B and p_e together (electron energy equation); stage 2 writes in
@@ -596,6 +614,10 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
         e = launch_field_stage_pe(c, c->B, c->B, c->Bs, c->pe, c->pe, c->pes, 0.5f * h);
         if (e == cudaSuccess)
           e = launch_field_stage_pe(c, c->Bs, c->B, c->B, c->pes, c->pe, c->pe, h);
+      } else if (c->p.ohm_model != 0) {
+        // the resistive background: tiled stages
+        e = launch_field_stage_tiled(c, c->B, c->B, c->Bs, 0.5f * h);
+        if (e == cudaSuccess) e = launch_field_stage_tiled(c, c->Bs, c->B, c->B, h);
       } else if (fused_substeps(c)) {
         // B and B* alternate so that a substep never writes what it reads
         e = launch_substep(c, (k & 1) ? c->Bs : c->B, (k & 1) ? c->B : c->Bs, h);
@@ -605,7 +627,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       }
       if (e != cudaSuccess) return cuda_fail(e, "field stage");
     }
-    if (!c->p.pe_eq && nsub_run > 0 && fused_substeps(c) && (c->p.nsub & 1)) {
+    if (!c->p.pe_eq && c->p.ohm_model == 0 && fused_substeps(c) && (c->p.nsub & 1)) {
       // an odd number of fused substeps leaves B^{n+1} in B*: copy it back
       e = cudaMemcpyAsync(c->B, c->Bs, sizeof(float4) * c->g.ncell, cudaMemcpyDeviceToDevice,
                           c->stream);

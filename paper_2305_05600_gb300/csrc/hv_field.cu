@@ -212,7 +212,7 @@ struct FieldConsts {
   float ilx, ily, ilz;          // 1 / Delta^2 per axis (0 on single-cell axes)
   float Te, gamma_e, eta, eta_h, n_floor;
   float kappa;                  // heat conductivity of the electron energy equation
-  int es;                       // electrostatic Ohm's law, B held
+  int model;                    // Ohm's law: 0 hybrid, 1 electrostatic, 2 resistive
   int isothermal;
 };
 
@@ -362,10 +362,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
     float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
     float ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz_;
-    if (k.es) {  // electrostatic Ohm's law (Sec. 3): E = -grad p_e / n_f
+    if (k.model == 1) {  // electrostatic Ohm's law (Sec. 3): E = -grad p_e / n_f
       ex = -gpx * inv;
       ey = -gpy * inv;
       ez = -gpz * inv;
+    } else if (k.model == 2) {  // resistive background (App. A): E = eta (J - J_k)
+      ex = k.eta * (jx - mi.y);
+      ey = k.eta * (jy - mi.z);
+      ez = k.eta * (jz - mi.w);
     }
     if (FINAL) {
       // interior cell of the tile: write E, B into the padded gather array
@@ -400,7 +404,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       if (PEQ) {
         // electron flow u_e = -(J - J_i) / n_f, p_e u_e and T_e = p_e / n_f
         // (the electrostatic model has no magnetic current: u_e = J_i / n_f)
-        const float jxm = k.es ? 0.f : jx, jym = k.es ? 0.f : jy, jzm = k.es ? 0.f : jz;
+        const bool es = k.model == 1;
+        const float jxm = es ? 0.f : jx, jym = es ? 0.f : jy, jzm = es ? 0.f : jz;
         const float ux_e = -(jxm - mi.y) * inv, uy_e = -(jym - mi.z) * inv,
                     uz_e = -(jzm - mi.w) * inv;
         const float p = pe[jc];
@@ -914,7 +919,7 @@ FieldConsts field_consts(const hv_ctx *c) {
   k.n_floor = (float)p.n_floor;
   k.isothermal = p.gamma_e == 1.0;
   k.kappa = (float)p.kappa;
-  k.es = p.electrostatic;
+  k.model = p.ohm_model;
   return k;
 }
 
@@ -1195,7 +1200,7 @@ cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bb
   a.Bbase = Bbase;
   a.Bout = Bout;
   a.mom = c->mprev;
-  a.coef = c->p.electrostatic ? 0.f : coef;  // the electrostatic model holds B
+  a.coef = c->p.ohm_model == 1 ? 0.f : coef;  // the electrostatic model holds B
   a.EB = nullptr;
   a.pin = pin;
   a.pbase = pbase;
@@ -1203,6 +1208,26 @@ cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bb
   a.pcoef = coef;
   c->launches++;
   return c->g.dim2 ? launch_stage_t<2, 0, 1>(c, a) : launch_stage_t<3, 0, 1>(c, a);
+}
+
+// One explicit-midpoint stage of B alone with the tiled stage kernel (2D
+// and 3D), for the Ohm's laws the fused kernels do not implement.
+cudaError_t launch_field_stage_tiled(hv_ctx *c, const float4 *Bin, const float4 *Bbase,
+                                     float4 *Bout, float coef) {
+  StageArgs a;
+  a.g = c->g;
+  a.k = field_consts(c);
+  a.Bin = Bin;
+  a.Bbase = Bbase;
+  a.Bout = Bout;
+  a.mom = c->mprev;
+  a.coef = coef;
+  a.EB = nullptr;
+  a.pin = a.pbase = nullptr;
+  a.pout = nullptr;
+  a.pcoef = 0.f;
+  c->launches++;
+  return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
 }
 
 cudaError_t launch_pe_init(hv_ctx *c) {

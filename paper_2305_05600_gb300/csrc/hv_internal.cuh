@@ -161,6 +161,7 @@ struct PushConsts {
   float qmdt2;          // (q/m) dt / 2
   float cx, cy, cz;     // dt / Delta per axis (0 for single-cell axes)
   float qvc;            // q / V_c
+  float ic2;            // 1 / c^2 (relativistic push only)
   float mass;           // m
 };
 
@@ -251,6 +252,8 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom);
 cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bbase, float4 *Bout,
                                   const float *pin, const float *pbase, float *pout, float coef);
 cudaError_t launch_pe_init(hv_ctx *c);
+cudaError_t launch_field_stage_tiled(hv_ctx *c, const float4 *Bin, const float4 *Bbase,
+                                     float4 *Bout, float coef);
 const float4 *gather_array(const hv_ctx *c);
 // learned moment filter (x-z layout)
 cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out);

@@ -411,9 +411,11 @@ __device__ __forceinline__ void voxel_coords(const Geom &g, int vox, int &ip, in
 }
 
 // One ion of the step: gather E^n, B^n at x^n, Boris push, move to x^{n+1}
-// (MODE 0; the state is updated in place and the kinetic-energy/momentum
-// terms are added to rk), then the deposit values at the half-step
-// position.  Returns the voxel of the deposit key, or INT_MIN for a corrupt
+// (MODE 0 and 2; the state is updated in place and the kinetic-energy/
+// momentum terms are added to rk), then the deposit values at the half-step
+// position.  MODE 2 and 3 are relativistic: the state carries u = gamma v,
+// the Boris rotation uses (q dt / 2m) B / gamma^-, positions and currents
+// use v = u / gamma, and the kinetic energy is m w |u|^2 / (gamma + 1).  Returns the voxel of the deposit key, or INT_MIN for a corrupt
 // cell index (latched in the error word; the ion is left as it is).
 template <int DIM, int SHAPE, int MODE>
 __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i0, int j0,
@@ -437,12 +439,13 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
                      (DIM == 2 || (ry >= -W::H && ry < W::TY + W::H));
   const int eslot = (rx + W::RE) + (DIM == 2 ? 0 : (ry + W::RE) * W::EX) +
                     (rz + W::RE) * W::EX * W::EY;
+  constexpr bool PUSH = (MODE & 1) == 0, REL = MODE >= 2;
   const float dy0 = DIM == 3 ? oy : 0.f;
   float vxp = vx, vyp = vy, vzp = vz;
   float hx = ox, hy = dy0, hz = oz;
   int shx = 0, shy = 0, shz = 0;
 
-  if (MODE == 0) {
+  if (PUSH) {
     // gather E^n, B^n at x^n with the deposit's weights (App. B)
     float wt[NT];
     const int ks_ = shape_weights<DIM, SHAPE>(ox, dy0, oz, g, wt);
@@ -493,7 +496,13 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
     // Boris: half E kick, rotation, half E kick (Eq. 9)
     const float h = a.k.qmdt2;
     const float vmx = vxp + h * ex, vmy = vyp + h * ey, vmz = vzp + h * ez;
-    const float tx = h * bx, ty = h * by, tz = h * bz;
+    float tx = h * bx, ty = h * by, tz = h * bz;
+    if (REL) {  // rotation of u^- by (q dt / 2m) B / gamma^-
+      const float ig = __frcp_rn(sqrtf(1.f + (vmx * vmx + vmy * vmy + vmz * vmz) * a.k.ic2));
+      tx *= ig;
+      ty *= ig;
+      tz *= ig;
+    }
     // 2 * rn(1/x) equals rn(2/x): scaling by 2 is exact
     const float f = 2.f * __frcp_rn(1.f + (tx * tx + ty * ty + tz * tz));
     const float sx = f * tx, sy = f * ty, sz = f * tz;
@@ -503,6 +512,16 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
     vxp = vmx + (vpy * sz - vpz * sy) + h * ex;
     vyp = vmy + (vpz * sx - vpx * sz) + h * ey;
     vzp = vmz + (vpx * sy - vpy * sx) + h * ez;
+    // the new state (u for the relativistic push) and the velocity that
+    // moves and deposits
+    float unx = vxp, uny = vyp, unz = vzp, gam = 1.f;
+    if (REL) {
+      gam = sqrtf(1.f + (unx * unx + uny * uny + unz * unz) * a.k.ic2);
+      const float ig = __frcp_rn(gam);
+      vxp = unx * ig;
+      vyp = uny * ig;
+      vzp = unz * ig;
+    }
 
     // half-step and full-step positions (Eq. 10; App. B); the
     // displacement coefficients are 0 along single-cell axes
@@ -523,9 +542,9 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
       hx = nxo = ox;
       hy = nyo = dy0;
       hz = nzo = oz;
-      vxp = vx;
-      vyp = vy;
-      vzp = vz;
+      vxp = unx = vx;
+      vyp = uny = vy;
+      vzp = unz = vz;
     }
     shx = rebase(hx);
     shz = rebase(hz);
@@ -545,14 +564,21 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
     ox = nxo;
     if (DIM == 3) oy = nyo;
     oz = nzo;
-    vx = vxp;
-    vy = vyp;
-    vz = vzp;
+    vx = unx;
+    vy = uny;
+    vz = unz;
     const float mw = a.k.mass * w;
-    rk[0] += 0.5f * mw * (vxp * vxp + vyp * vyp + vzp * vzp);
-    rk[1] += mw * vxp;
-    rk[2] += mw * vyp;
-    rk[3] += mw * vzp;
+    const float uu = unx * unx + uny * uny + unz * unz;
+    rk[0] += REL ? mw * uu * __frcp_rn(gam + 1.f) : 0.5f * mw * uu;
+    rk[1] += mw * unx;
+    rk[2] += mw * uny;
+    rk[3] += mw * unz;
+  } else if (REL) {
+    // start-up deposit of a relativistic particle: v = u / gamma
+    const float ig = __frcp_rn(sqrtf(1.f + (vx * vx + vy * vy + vz * vz) * a.k.ic2));
+    vxp = vx * ig;
+    vyp = vy * ig;
+    vzp = vz * ig;
   }
 
   // deposit q w S / V_c and q w v S / V_c at the half-step position
@@ -612,7 +638,8 @@ struct Run {
 };
 
 // MODE 0: full step.  MODE 1: start-up deposit at the current position with
-// the stored velocity (no push, no move, no write-back).
+// the stored velocity (no push, no move, no write-back).  MODE 2 and 3: the
+// same with the relativistic push.
 //
 // kPushSplit blocks per supercell tile, each taking a contiguous part of the
 // tile's ion range (finer work units than whole tiles keep the last wave of
@@ -629,6 +656,7 @@ template <int DIM, int SHAPE, int MODE>
 // (3D: the larger staging and window buffers allow two blocks per SM)
 __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
     push_kernel(PushArgs a) {
+  constexpr bool PUSH = (MODE & 1) == 0;  // full step (not the start-up deposit)
   using L = Layout<DIM, SHAPE>;
   using W = Win<DIM>;
   using SL = Slot<DIM>;
@@ -674,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   }
 
   // stage E, B of the window
-  if (MODE == 0) {
+  if (PUSH) {
     for (int c = threadIdx.x; c < W::NEB; c += kThreads) {
       const int wx = c % W::EX, wy = (c / W::EX) % W::EY, wz = c / (W::EX * W::EY);
       const int ip = i0 + wx - W::RE + kGhost, kp = k0 + wz - W::RE + kGhost;
@@ -737,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
         if (pk == INT_MIN) continue;
         run.add(a, pk, dep);
       }
-      if (MODE == 0) {
+      if (PUSH) {
         stv<kGroup>(&TC[SL::CELL][e0], cc);
         stv<kGroup>(&T[SL::OX][e0], ox);
         if (DIM == 3) stv<kGroup>(&T[SL::OY][e0], oy);
@@ -748,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
       }
     }
     run.finish(a);
-    if (MODE == 0) {
+    if (PUSH) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) kahan_add(ks[m], kc[m], rk[m]);
     }
@@ -757,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
     // field but w
     fence_async_smem();
     __syncwarp();
-    if (MODE == 0 && lane == 0) {
+    if (PUSH && lane == 0) {
       const uint32_t bytes = (uint32_t)nqt * 16u;
 #pragma unroll
       for (int f = 0; f < NA; ++f)
@@ -769,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   if (lane == 0) bulk_wait_all();  // stores done before the block exits
   __syncthreads();
 
-  if (MODE == 0) {
+  if (PUSH) {
     // FP64 block partials of W_K and P (deterministic order)
     __shared__ double red[nwarps][4];
     double d[4];
@@ -841,18 +869,28 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.k.cy = c->g.ny > 1 ? (float)(c->p.dt / c->p.dy) : 0.f;
   a.k.cz = c->g.nz > 1 ? (float)(c->p.dt / c->p.dz) : 0.f;
   a.k.qvc = (float)(sp.q / c->vc);
+  a.k.ic2 = c->p.relativistic ? (float)(1.0 / (c->p.c_light * c->p.c_light)) : 0.f;
   a.k.mass = (float)sp.m;
   a.part = c->pushpart + (size_t)species * c->push_blocks * 4;
   a.err = c->err;
   c->launches++;
   const int shape = c->p.shape;
   const int blocks = c->push_blocks;  // kPushSplit blocks per supercell tile
+  const int m = mode + (c->p.relativistic ? 2 : 0);
   if (c->g.dim2) {
-    return mode == 0 ? launch_shape<2, 0>(shape, a, blocks, c->stream)
-                     : launch_shape<2, 1>(shape, a, blocks, c->stream);
+    switch (m) {
+      case 0: return launch_shape<2, 0>(shape, a, blocks, c->stream);
+      case 1: return launch_shape<2, 1>(shape, a, blocks, c->stream);
+      case 2: return launch_shape<2, 2>(shape, a, blocks, c->stream);
+      default: return launch_shape<2, 3>(shape, a, blocks, c->stream);
+    }
   }
-  return mode == 0 ? launch_shape<3, 0>(shape, a, blocks, c->stream)
-                   : launch_shape<3, 1>(shape, a, blocks, c->stream);
+  switch (m) {
+    case 0: return launch_shape<3, 0>(shape, a, blocks, c->stream);
+    case 1: return launch_shape<3, 1>(shape, a, blocks, c->stream);
+    case 2: return launch_shape<3, 2>(shape, a, blocks, c->stream);
+    default: return launch_shape<3, 3>(shape, a, blocks, c->stream);
+  }
 }
 
 }  // namespace hv

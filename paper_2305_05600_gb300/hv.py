@@ -37,7 +37,9 @@ class Params(ctypes.Structure):
                 ("shape", ctypes.c_int32), ("smooth_passes", ctypes.c_int32),
                 ("sort_every", ctypes.c_int32), ("field_smooth_passes", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("pe_eq", ctypes.c_int32),
-                ("electrostatic", ctypes.c_int32), ("kappa", ctypes.c_double)]
+                ("ohm_model", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("relativistic", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("c_light", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -69,7 +71,7 @@ class Info(ctypes.Structure):
                 ("n", ctypes.c_int64 * 8), ("step", ctypes.c_int64)]
 
 
-assert ctypes.sizeof(Params) == 128, ctypes.sizeof(Params)
+assert ctypes.sizeof(Params) == 144, ctypes.sizeof(Params)
 
 _lib = None
 _lock = threading.Lock()
@@ -175,8 +177,9 @@ def params_from(d: dict) -> Params:
                   float(d.get("eta_h", 0.0)), float(d.get("n_floor", 0.05)), shape,
                   int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)),
                   int(d.get("field_smooth_passes", 0)),
-                  int(d.get("seed", 0)), int(d.get("pe_eq", 0)), int(d.get("electrostatic", 0)),
-                  float(d.get("kappa", 0.0)))
+                  int(d.get("seed", 0)), int(d.get("pe_eq", 0)), int(d.get("ohm_model", 0)),
+                  float(d.get("kappa", 0.0)), int(d.get("relativistic", 0)), 0,
+                  float(d.get("c_light", 0.0)))
 
 
 def _ptr(a):

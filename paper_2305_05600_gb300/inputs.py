@@ -68,12 +68,12 @@ class Workload:
 
 def base_params(nx, ny, nz, dx, dy, dz, dt, nsub, Te, eta=0.0, eta_h=0.0, n_floor=0.05,
                 shape="qs", smooth_passes=0, gamma_e=1.0, sort_every=20, field_smooth_passes=0,
-                pe_eq=0, kappa=0.0, electrostatic=0):
+                pe_eq=0, kappa=0.0, ohm_model=0, relativistic=0, c_light=0.0):
     return dict(nx=nx, ny=ny, nz=nz, dx=dx, dy=dy if ny > 1 else 1.0, dz=dz, dt=dt,
                 nsub=nsub, Te=Te, gamma_e=gamma_e, eta=eta, eta_h=eta_h, n_floor=n_floor,
                 shape=shape, smooth_passes=smooth_passes, sort_every=sort_every,
                 field_smooth_passes=field_smooth_passes, pe_eq=pe_eq, kappa=kappa,
-                electrostatic=electrostatic)
+                ohm_model=ohm_model, relativistic=relativistic, c_light=c_light)
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -389,6 +389,39 @@ def explosion2d(nx=512, nz=512, length=1000.0, ppc=200, n_debris=1 << 20, mach=1
                           f"{smooth_passes} smoothing passes")
 
 
+def ebeam2d(nx=640, nz=320, lx=80.0, lz=20.0, ppc=64, gamma_d=2.96, u_th=0.3, lam=1.0,
+            eta=0.01, dt=0.04, nsub=4, seed=8000, steps=2000, shape="qs",
+            sort_every=20) -> Workload:
+    """Relativistic electron beam in a resistive background (App. A), x-z
+    plane, periodic: electrons (q = -1, m = 1, c = 1 in electron units)
+    drifting along x with Lorentz factor gamma_d and a thermal spread u_th
+    in u = gamma v, density n0 sech^2((z - Lz/2)/lam) on a floor of 1e-3;
+    B_y(z) from the beam current so that curl B = J_beam initially; Ohm's
+    law E = eta (curl B - J_beam)."""
+    dx, dz = lx / nx, lz / nz
+    p = base_params(nx, 1, nz, dx, 1.0, dz, dt, nsub, Te=0.0, eta=eta, n_floor=1e-3,
+                    shape=shape, sort_every=sort_every, ohm_model=2, relativistic=1,
+                    c_light=1.0)
+    rng = _rng(seed)
+    _, _, zc = cell_centres(p)
+    prof = 1.0 / np.cosh((zc - 0.5 * lz) / lam) ** 2 + 1e-3
+    cell, off = load_cells(p, np.full(nx * nz, ppc), rng, (nx, 1, nz))
+    n = cell.shape[0]
+    k = cell // nx
+    u = u_th * _box_muller(rng, (3, n))
+    ud = math.sqrt(gamma_d * gamma_d - 1.0)
+    u[0] += ud
+    w = prof[k] * dx * dz / ppc
+    # B_y with -dB_y/dz = J_x = q n v_d (v_d = ud / gamma_d), zero mean
+    jx = -1.0 * prof * ud / gamma_d
+    By = -np.cumsum(jx) * dz
+    By -= By.mean()
+    B = np.zeros((3, nz, 1, nx))
+    B[1] = By[:, None, None]
+    return Workload("ebeam2d", p, B.astype(np.float32), [_finish(cell, off, u, w, q=-1.0, m=1.0)],
+                    steps, notes=f"{nx}x{nz} cells, {ppc} ppc, gamma_d={gamma_d}, eta={eta}")
+
+
 WORKLOADS = {
     "alfven2d": alfven2d,
     "harris2d": harris2d,
@@ -396,4 +429,5 @@ WORKLOADS = {
     "harris3d": harris3d,
     "whistler1d": whistler1d,
     "explosion2d": explosion2d,
+    "ebeam2d": ebeam2d,
 }

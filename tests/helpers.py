@@ -11,7 +11,8 @@ def oracle_grid(p, **over):
     return O.make_grid(q["nx"], q["ny"], q["nz"], q["dx"], q["dy"], q["dz"], q["dt"],
                        q["nsub"], q["Te"], q["gamma_e"], q["eta"], q["eta_h"], q["n_floor"],
                        q["shape"], q["smooth_passes"], q.get("field_smooth_passes", 0),
-                       q.get("pe_eq", 0), q.get("kappa", 0.0), q.get("electrostatic", 0))
+                       q.get("pe_eq", 0), q.get("kappa", 0.0), q.get("ohm_model", 0),
+                       q.get("relativistic", 0), q.get("c_light", 0.0))
 
 
 def oracle_species(wl):

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_function():
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(hv.Params) == 128
+    assert ctypes.sizeof(hv.Params) == 144
     assert ctypes.sizeof(hv.Diag) == 8 * 9 + 8
     assert ctypes.sizeof(hv.Prof) == 8 * 14
 
@@ -53,7 +53,8 @@ def _init_status(p):
                                  dict(Te=-1.0), dict(eta=-1e-3), dict(field_smooth_passes=-1),
                                  dict(field_smooth_passes=65), dict(pe_eq=2),
                                  dict(pe_eq=1, kappa=-1.0), dict(kappa=math.inf),
-                                 dict(electrostatic=2)])
+                                 dict(ohm_model=3), dict(relativistic=1),
+                                 dict(relativistic=1, c_light=-1.0)])
 def test_init_rejects_bad_parameters_on_host(bad):
     rc, h = _init_status(_params(**bad))
     assert rc == hv.HV_EINVAL and not h

@@ -219,7 +219,7 @@ def test_electrostatic_parity(hvmod, dim, pe_eq):
     """Electrostatic Ohm's law (E = -grad p_e / n_f); B keeps its loaded
     value, with p_e from the equation of state or the energy equation."""
     wl = small_workload(dim, "qs")
-    wl.params.update(electrostatic=1, pe_eq=pe_eq, kappa=0.05, gamma_e=5.0 / 3.0)
+    wl.params.update(ohm_model=1, pe_eq=pe_eq, kappa=0.05, gamma_e=5.0 / 3.0)
     p = wl.params
     ctx = hvmod.load_workload(wl)
     sim = oracle_sim(wl)
@@ -237,6 +237,41 @@ def test_electrostatic_parity(hvmod, dim, pe_eq):
         if pe_eq:
             pe = hvmod.hv_electron_pressure(ctx).reshape(-1).astype(np.float64)
             assert rel_l2(pe, sim.pe) < 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_relativistic_beam_resistive_parity(hvmod, dim):
+    """Kinetic relativistic electrons (u = gamma v, relativistic Boris) in a
+    resistive background, E = eta (curl B - J_k) (App. A)."""
+    if dim == 2:
+        wl = I.ebeam2d(nx=40, nz=24, lx=5.0, lz=3.0, ppc=16, eta=0.02, dt=0.02, nsub=2, seed=31,
+                       sort_every=1)
+    else:
+        wl = I.beam3d(nx=12, ny=10, nz=9, n_core=6, n_beam=3, dx=0.5, seed=32, sort_every=1)
+        s = wl.species[0]
+        wl.species[0] = I.SpeciesInput(-1.0, 1.0, s.cell, s.off, (s.v * 0.3).astype(np.float32),
+                                       s.w)
+        wl.params.update(ohm_model=2, relativistic=1, c_light=1.0, eta=0.02)
+    wl = I.with_distinct_weights(wl)
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    m0 = hvmod.hv_moments(ctx)
+    assert rel_l2(m0["J"].reshape(3, -1), sim.J_prev) < 1e-5
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
+        assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+        assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
+        d = hvmod.hv_diag(ctx)
+        od = sim.diags[-1]
+        assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
     ctx.close()
 
 
