@@ -146,7 +146,11 @@ hv_status hv_set_allocator(hv_alloc_fn alloc, hv_free_fn free_fn, void *user);
  * the uniform field (1, 0, 0).  cuda_stream: a cudaStream_t (NULL = legacy
  * default stream).  Validates p (HV_EINVAL) and the whistler time-step limit
  * Omega_ci (dt/nsub) < min(dx,dy,dz)^2 / pi over axes with more than one cell
- * (Sec. 2.1; HV_ECFL).  On success *out owns the device state. */
+ * (Sec. 2.1; HV_ECFL) for the hybrid Ohm's law; with the electron energy
+ * equation also h (gamma_e - 1) kappa / n_floor * sum 4/Delta^2 <= 2, and
+ * for the resistive background h eta sum 4/Delta^2 <= 2 (explicit-midpoint
+ * stability of the diffusion terms; HV_ECFL).  On success *out owns the
+ * device state. */
 hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stream,
                        hv_ctx **out);
 
@@ -154,7 +158,8 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
  * already loaded; up to 8) with charge q and mass m (q_s = Z_s e, m_s; Sec.
  * 2.1) and n macro-particles: cell[n] int32 in [0, ncell), off3 [3][n]
  * relative coordinates in [-1, 1) (ignored along single-cell axes),
- * v3 [3][n] velocities v^{-1/2}, w[n] weights (Sec. 2.2).  The arrays are
+ * v3 [3][n] velocities v^{-1/2} (u = gamma v for a relativistic context),
+ * w[n] weights (Sec. 2.2).  The arrays are
  * copied to the device (on_device != 0: they are device pointers) and every
  * value is checked there before the call returns (HV_EINVAL on a bad index,
  * offset or non-finite value; nothing of the species is kept then).  The

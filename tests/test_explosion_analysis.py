@@ -83,3 +83,18 @@ def test_sectors_see_only_their_directions():
     ma = X.sector_metrics(n, dx, X.SECTORS["along_B0"], half_width=0.15)
     mc = X.sector_metrics(n, dx, X.SECTORS["across_B0"])
     assert ma["layers"] == 2.0 and mc["layers"] == 1.0
+
+
+def test_hose_channel_measures_kink_and_width():
+    from paper_2305_05600_gb300 import hose as H
+    nz, nx, dz = 64, 32, 0.25
+    z = (np.arange(nz) + 0.5) * dz
+    x = np.arange(nx)
+    # a Gaussian channel of width 1 whose centre moves as 0.5 sin(2 pi x / nx)
+    zc = 8.0 + 0.5 * np.sin(2 * np.pi * x / nx)
+    n = -np.exp(-0.5 * (z[:, None] - zc[None, :]) ** 2)  # electrons: negative density
+    kink, width = H.channel(n, dz)
+    assert abs(kink - 0.5 / np.sqrt(2)) < 0.01
+    assert abs(width - 1.0) < 0.02
+    kink0, _ = H.channel(-np.exp(-0.5 * (z[:, None] - 8.0) ** 2) * np.ones((1, nx)), dz)
+    assert kink0 < 1e-12
