@@ -11,6 +11,7 @@
 //    array;
 //  * diagnostics: FP64 block partials of sum |B|^2/2 V_c, sum n V_c and
 //    max |div B|, reduced in a fixed order with the particle partials.
+#include <algorithm>
 #include <utility>
 
 #include "hv_internal.cuh"
@@ -183,6 +184,60 @@ __global__ void __launch_bounds__(256) smooth_kernel(Geom g, const float4 *in, f
       }
     }
     out[c] = s;
+  }
+}
+
+// Up to kSmoothMax binomial passes in one launch (x-z layout): a block
+// loads a 32x32 output tile with a halo of one cell per pass into shared
+// memory and applies the passes there, each on a region one cell smaller,
+// as an x sweep then a z sweep of (1/4, 1/2, 1/4) (the tensor-product
+// stencil of smooth_kernel, rounded per sweep).  Global memory is read and
+// written once per launch instead of once per pass.
+namespace smz {
+constexpr int T = 32, kMax = 8, R = T + 2 * kMax, kThreads = 256;
+constexpr size_t kBytes = 2 * (size_t)R * R * sizeof(float4);
+}  // namespace smz
+
+__global__ void __launch_bounds__(smz::kThreads) smooth2d_multi_kernel(Geom g, const float4 *in,
+                                                                       float4 *out, int passes) {
+  using namespace smz;
+  extern __shared__ __align__(16) float4 sb[];
+  float4 *a = sb, *b = sb + R * R;
+  const int ntx = (g.nx + T - 1) / T;
+  const int x0 = (blockIdx.x % ntx) * T, z0 = (blockIdx.x / ntx) * T;
+  const int H = passes, W = T + 2 * H;  // loaded region W x W (row pitch R)
+  for (int r = threadIdx.x; r < W * W; r += blockDim.x) {
+    const int lx = r % W - H, lz = r / W - H;
+    const int gx = wrapn(x0 + lx, g.nx), gz = wrapn(z0 + lz, g.nz);
+    a[(lz + H) * R + (lx + H)] = in[gx + g.nx * gz];
+  }
+  __syncthreads();
+  for (int q = 0; q < passes; ++q) {
+    // region of the result of this pass: halo H - q - 1
+    const int h = H - q - 1, w = T + 2 * h, o = q + 1;  // first row/column in the arrays
+    // x sweep over rows o-1 .. o+w (the z sweep needs one row above and below)
+    for (int r = threadIdx.x; r < w * (w + 2); r += blockDim.x) {
+      const int ix = o + r % w, iz = o - 1 + r / w;
+      const float4 l = a[iz * R + ix - 1], c = a[iz * R + ix], rr = a[iz * R + ix + 1];
+      b[iz * R + ix] = make_float4(0.25f * l.x + 0.5f * c.x + 0.25f * rr.x,
+                                   0.25f * l.y + 0.5f * c.y + 0.25f * rr.y,
+                                   0.25f * l.z + 0.5f * c.z + 0.25f * rr.z,
+                                   0.25f * l.w + 0.5f * c.w + 0.25f * rr.w);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < w * w; r += blockDim.x) {
+      const int ix = o + r % w, iz = o + r / w;
+      const float4 d = b[(iz - 1) * R + ix], c = b[iz * R + ix], u = b[(iz + 1) * R + ix];
+      a[iz * R + ix] = make_float4(0.25f * d.x + 0.5f * c.x + 0.25f * u.x,
+                                   0.25f * d.y + 0.5f * c.y + 0.25f * u.y,
+                                   0.25f * d.z + 0.5f * c.z + 0.25f * u.z,
+                                   0.25f * d.w + 0.5f * c.w + 0.25f * u.w);
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < T * T; r += blockDim.x) {
+    const int gx = x0 + r % T, gz = z0 + r / T;
+    if (gx < g.nx && gz < g.nz) out[gx + g.nx * gz] = a[(r / T + H) * R + (r % T + H)];
   }
 }
 
@@ -1025,6 +1080,38 @@ static int elem_blocks(int n) {
   return b < 1 ? 1 : (b > 4096 ? 4096 : b);
 }
 
+// `passes` binomial passes of the float4 grid in x, with y as scratch;
+// *res receives whichever of the two holds the result.  The x-z layout
+// runs up to smz::kMax passes per launch.
+static cudaError_t smooth_grid(hv_ctx *c, float4 *x, float4 *y, int passes, float4 **res) {
+  const Geom &g = c->g;
+  const bool fused = g.dim2;
+  static bool attr_set = false;
+  if (fused && !attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(smooth2d_multi_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smz::kBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int nb = elem_blocks(g.ncell);
+  const int tiles = ((g.nx + smz::T - 1) / smz::T) * ((g.nz + smz::T - 1) / smz::T);
+  for (int done = 0; done < passes;) {
+    const int k = fused ? std::min(passes - done, smz::kMax) : 1;
+    c->launches++;
+    if (fused)
+      smooth2d_multi_kernel<<<tiles, smz::kThreads, smz::kBytes, c->stream>>>(g, x, y, k);
+    else
+      smooth_kernel<<<nb, 256, 0, c->stream>>>(g, x, y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::swap(x, y);
+    done += k;
+  }
+  *res = x;
+  return cudaSuccess;
+}
+
 cudaError_t launch_moments(hv_ctx *c, int init) {
   MomArgs a;
   a.g = c->g;
@@ -1057,15 +1144,8 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
     if (e != cudaSuccess) return e;
     src = c->mhalf;
   } else {
-    for (int p = 0; p < passes; ++p) {
-      c->launches++;
-      smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, src, dst);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      float4 *t = src;
-      src = dst;
-      dst = t;
-    }
+    e = smooth_grid(c, src, dst, passes, &src);
+    if (e != cudaSuccess) return e;
   }
   c->launches++;
   extrap_kernel<<<nb, 256, 0, c->stream>>>(c->g.ncell, src, c->mprev, c->mprev, c->mext, init);
@@ -1177,14 +1257,11 @@ static cudaError_t launch_field_smoothing(hv_ctx *c) {
   const int nb = elem_blocks(c->g.ncell);
   float4 *a0 = c->fsm[0], *a1 = c->fsm[1], *b0 = c->fsm[2], *b1 = c->fsm[3];
   eb_unpad_kernel<<<nb, 256, 0, c->stream>>>(c->g, c->EB, a0, b0);
-  for (int p = 0; p < passes; ++p) {
-    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, a0, a1);
-    smooth_kernel<<<nb, 256, 0, c->stream>>>(c->g, b0, b1);
-    std::swap(a0, a1);
-    std::swap(b0, b1);
-  }
+  cudaError_t e = smooth_grid(c, a0, a1, passes, &a0);
+  if (e == cudaSuccess) e = smooth_grid(c, b0, b1, passes, &b0);
+  if (e != cudaSuccess) return e;
   eb_pad_kernel<<<nb, 256, 0, c->stream>>>(c->g, a0, b0, c->EBs);
-  c->launches += 2 + 2 * passes;
+  c->launches += 2;
   return cudaGetLastError();
 }
 

@@ -283,6 +283,27 @@ def test_electron_pressure_needs_the_equation(hvmod):
     ctx.close()
 
 
+def test_many_smoothing_passes_parity(hvmod):
+    """Ten passes on the moments and on the gathered fields: the x-z layout
+    applies them in two launches of up to eight passes each."""
+    wl = small_workload(2, "qs")
+    wl.params["smooth_passes"] = 10
+    wl.params["field_smooth_passes"] = 10
+    p = wl.params
+    ctx = hvmod.load_workload(wl)
+    sim = oracle_sim(wl)
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+        assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
+    ctx.close()
+
+
 def test_quasi_1d_and_multispecies(hvmod):
     """nz = 1 (one-cell z axis) and two species with different q/m."""
     wl = I.whistler1d(nx=64, ppc=32, steps=1)
