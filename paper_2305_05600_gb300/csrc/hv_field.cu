@@ -73,6 +73,7 @@ __device__ __forceinline__ void finish_moment(const MomArgs &a, int c, float4 m)
 // next step by a memset after the fold: zeroing each voxel right after
 // reading it made the 3D fold six times slower on GB300.
 __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
+  pdl_begin();
   const Geom &g = a.g;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, k;
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
 // stencil reaches one of its images.  The other record buffer (read by the
 // previous fold) is zeroed for the next deposit.
 __global__ void __launch_bounds__(256) fold_records_kernel(MomArgs a) {
+  pdl_begin();
   const Geom &g = a.g;
   const float c6 = 1.f / 6.f, c12 = 1.f / 12.f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
@@ -313,6 +315,7 @@ struct Tile {
 
 template <int DIM, int FINAL, int PEQ = 0>
 __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
+  pdl_begin();
   using T = Tile<DIM, FINAL, PEQ>;
   using RB = typename T::template R<T::HB>;
   using RJ = typename T::template R<T::HJ>;
@@ -589,6 +592,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a) {
+  pdl_begin();
   using namespace st3d;
   // cells per thread in each plane region; a thread keeps the x-y part of
   // its cells' global offsets, so a plane adds only its z offset
@@ -852,6 +856,7 @@ __device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, fl
 constexpr int kSubThreads = HV_SUB_THREADS;
 
 __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
+  pdl_begin();
   using namespace sub2d;
   extern __shared__ float sm[];
   const Geom &g = a.g;
@@ -992,8 +997,7 @@ cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
   const int ntx = (c->g.nx + T::OX - 1) / T::OX;
   const int nty = DIM == 2 ? 1 : (c->g.ny + T::OY - 1) / T::OY;
   const int ntz = (c->g.nz + T::OZ - 1) / T::OZ;
-  stage_kernel<DIM, FINAL, PEQ><<<ntx * nty * ntz, 256, smem, c->stream>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(stage_kernel<DIM, FINAL, PEQ>, ntx * nty * ntz, 256, smem, c->stream, a);
 }
 
 // ----------------------------------------------------------------------------
@@ -1128,7 +1132,8 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
   const int nb = elem_blocks(c->g.ncell);
   c->launches++;
   if (uses_records(c)) {
-    fold_records_kernel<<<nb, 256, 0, c->stream>>>(a);
+    cudaError_t el = launch_pdl(fold_records_kernel, nb, 256, 0, c->stream, a);
+    if (el != cudaSuccess) return el;
     c->accpar ^= 1;
   } else {
     fold_kernel<<<(c->g.ncell + 255) / 256, 256, 0, c->stream>>>(a);
@@ -1179,8 +1184,7 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   const Geom &g = c->g;
   const int blocks = ((g.nx + st3d::X - 1) / st3d::X) * ((g.ny + st3d::Y - 1) / st3d::Y) *
                      ((g.nz + st3d::Z - 1) / st3d::Z);
-  stage3d_kernel<<<blocks, st3d::kThreads, smem, c->stream>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(stage3d_kernel, blocks, st3d::kThreads, smem, c->stream, a);
 }
 
 bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0; }
@@ -1204,8 +1208,7 @@ cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) 
   const int ntx = (c->g.nx + sub2d::SX - 1) / sub2d::SX;
   const int ntz = (c->g.nz + sub2d::SZ - 1) / sub2d::SZ;
   c->launches++;
-  substep2d_kernel<<<ntx * ntz, kSubThreads, smem, c->stream>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(substep2d_kernel, ntx * ntz, kSubThreads, smem, c->stream, a);
 }
 
 // Self-consistent field smoothing (Sec. 2.2): the push gathers S^p E and

@@ -12,6 +12,33 @@
 
 namespace hv {
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// launch_pdl may be scheduled while the previous kernel of its stream is
+// still draining.  Every kernel of the step calls pdl_begin() first: it
+// lets the next kernel be scheduled once all of its own blocks have
+// started, and waits until the previous kernel has completed and its
+// memory is visible, before touching anything.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 constexpr int kMaxSpecies = 8;
 
 // QS deposit in the x-z layout accumulates, per cell and channel

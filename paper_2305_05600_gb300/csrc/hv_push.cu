@@ -656,6 +656,7 @@ template <int DIM, int SHAPE, int MODE>
 // (3D: the larger staging and window buffers allow two blocks per SM)
 __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
     push_kernel(PushArgs a) {
+  pdl_begin();
   constexpr bool PUSH = (MODE & 1) == 0;  // full step (not the start-up deposit)
   using L = Layout<DIM, SHAPE>;
   using W = Win<DIM>;
@@ -835,6 +836,8 @@ cudaError_t launch_t(const PushArgs &a, int blocks, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  // an ordinary launch: the push may follow a wait on the side stream's
+  // sort, which a programmatic launch must not overtake
   push_kernel<DIM, SHAPE, MODE><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
