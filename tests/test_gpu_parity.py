@@ -127,7 +127,7 @@ def test_one_step_parity(hvmod, dim, shape):
     vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
     compare_particles(p, g, sim.species[0], vscale)
     m1 = hvmod.hv_moments(ctx)
-    # deposited half-step moments (spec bound 1e-5 relative L2)
+    # deposited half-step moments (benchmark tolerance: 1e-5 relative L2)
     assert rel_l2(m1["n"].reshape(-1), sim.n_prev) < 1e-5
     for a in range(3):
         assert rel_l2(m1["J"][a].reshape(-1), sim.J_prev[a]) < 1e-5
