@@ -564,12 +564,14 @@ constexpr int J0 = P, NJ = P * (Y + 4);          // J, n: rows 1 .. Y+4
 constexpr int E0 = 2 * P, NE = P * (Y + 2);      // E, moments: rows 2 .. Y+3
 constexpr int kThreads = HV_ST3D_THREADS;
 // ring depths: B planes zj-2..zj+2 (E reads zj-2, J zj-1..zj+1, the copy
-// fills zj+2); J, n and E each hold three planes being read and one being
-// written; the moment float4 at E cells one read and one in flight
-constexpr int kRB = 5, kRJ = 4, kRN = 4, kRM = 2, kRE = 4;
+// fills zj+2); J, p_e and E each hold three planes being read and one being
+// written; n one plane read (by the J phase, for p_e) and one in flight; the
+// moment float4 at E cells one read and one in flight
+constexpr int kRB = 5, kRJ = 4, kRP = 4, kRN = 2, kRM = 2, kRE = 4;
 constexpr int kB = 0;                    // [kRB][3][NP]
 constexpr int kJ = kB + kRB * 3 * NP;    // [kRJ][3][NP]
-constexpr int kN = kJ + kRJ * 3 * NP;    // [kRN][NP]   ion density n
+constexpr int kP = kJ + kRJ * 3 * NP;    // [kRP][NP]   electron pressure p_e
+constexpr int kN = kP + kRP * NP;        // [kRN][NP]   ion density n
 constexpr int kM = kN + kRN * NP;        // [kRM][NP]   {n, Jix, Jiy, Jiz} as float4
 constexpr int kE = kM + kRM * 4 * NP;    // [kRE][3][NP]
 constexpr int kFloats = kE + kRE * 3 * NP;
@@ -677,6 +679,7 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
   copy_B(z0 - 3);
   copy_B(z0 - 2);
   copy_B(z0 - 1);
+  copy_n(z0 - 2);
   cp_async_commit();
   for (int q = 0; q < Z + 6; ++q) {
     const int zj = z0 - 2 + q, ze = zj - 2, zo = ze - 2;
@@ -692,15 +695,17 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
     // one step ahead: B for the next J plane, n and the moments for the
     // next E plane
     if (q <= Z + 2) copy_B(zj + 2);
-    if (q <= Z + 3) copy_n(zj);
+    if (q <= Z + 2) copy_n(zj + 1);
     if (q >= 2 && q <= Z + 3) copy_m(ze + 1);
     cp_async_commit();
 
-    if (q <= Z + 3) {  // J = curl B on plane zj
+    if (q <= Z + 3) {  // J = curl B and p_e on plane zj
       const float *bm = sm + kB + slot(zj - 1, kRB) * 3 * NP;
       const float *b0 = sm + kB + slot(zj, kRB) * 3 * NP;
       const float *bp = sm + kB + slot(zj + 1, kRB) * 3 * NP;
+      const float *nn = sm + kN + slot(zj, kRN) * NP;
       float *j = sm + kJ + slot(zj, kRJ) * 3 * NP;
+      float *pp = sm + kP + slot(zj, kRP) * NP;
 #pragma unroll
       for (int u = 0; u < LJ; ++u) {
         const int r = t + u * kThreads;
@@ -715,15 +720,16 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
         j[c] = dBz_dy - dBy_dz;
         j[NP + c] = dBx_dz - dBz_dx;
         j[2 * NP + c] = dBy_dx - dBx_dy;
+        pp[c] = pe(nn[c]);
       }
     }
     if (q >= 3 && q <= Z + 4) {  // E from Ohm's law on plane ze
       const float *jm = sm + kJ + slot(ze - 1, kRJ) * 3 * NP;
       const float *j0 = sm + kJ + slot(ze, kRJ) * 3 * NP;
       const float *jp = sm + kJ + slot(ze + 1, kRJ) * 3 * NP;
-      const float *nm = sm + kN + slot(ze - 1, kRN) * NP;
-      const float *n0 = sm + kN + slot(ze, kRN) * NP;
-      const float *np = sm + kN + slot(ze + 1, kRN) * NP;
+      const float *pm = sm + kP + slot(ze - 1, kRP) * NP;
+      const float *p0 = sm + kP + slot(ze, kRP) * NP;
+      const float *pq = sm + kP + slot(ze + 1, kRP) * NP;
       const float4 *m0 = reinterpret_cast<const float4 *>(sm + kM) + slot(ze, kRM) * NP;
       const float *b0 = sm + kB + slot(ze, kRB) * 3 * NP;
       float *e = sm + kE + slot(ze, kRE) * 3 * NP;
@@ -737,9 +743,9 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
         const float bxv = b0[c], byv = b0[NP + c], bzv = b0[2 * NP + c];
         const float jx = j0[c], jy = j0[NP + c], jz = j0[2 * NP + c];
         const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
-        const float gpx = (pe(n0[c + 1]) - pe(n0[c - 1])) * k.idx2;
-        const float gpy = (pe(n0[c + P]) - pe(n0[c - P])) * k.idy2;
-        const float gpz = (pe(np[c]) - pe(nm[c])) * k.idz2;
+        const float gpx = (p0[c + 1] - p0[c - 1]) * k.idx2;
+        const float gpy = (p0[c + P] - p0[c - P]) * k.idy2;
+        const float gpz = (pq[c] - pm[c]) * k.idz2;
         float l[3];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
