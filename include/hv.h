@@ -89,7 +89,8 @@ typedef struct {
                            2: resistive background E = eta (curl B - J_k)
                               (App. A), J_k the deposited current of the
                               kinetic species */
-  double kappa;         /* heat conductivity of that equation (>= 0) */
+  double kappa;         /* heat conductivity of the electron energy
+                           equation (>= 0) */
   int32_t relativistic; /* 1: the particles carry u = gamma v (loaded and
                            returned in place of v) and move with the
                            relativistic Boris push (App. A) */
@@ -102,8 +103,9 @@ typedef struct {
 typedef struct {
   int64_t step;      /* completed steps */
   double t;          /* step * dt */
-  double W_K;        /* sum over ions of 1/2 m w |v^{n+1/2}|^2 */
-  double P[3];       /* sum over ions of m w v^{n+1/2} */
+  double W_K;        /* sum over ions of 1/2 m w |v^{n+1/2}|^2 (relativistic:
+                        m w (gamma - 1) c^2) */
+  double P[3];       /* sum over ions of m w v^{n+1/2} (relativistic: m w u) */
   double charge;     /* sum over cells of n^{n+1/2} V_c (= sum q w) */
   double W_B;        /* sum over cells of 1/2 |B^{n+1}|^2 V_c */
   double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12) */
