@@ -414,7 +414,7 @@ cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
-  const int blocks = (int)std::min<int64_t>((sp.n + 1023) / 1024, 16 * 1024);
+  const int blocks = (int)std::max<int64_t>((sp.n + 1023) / 1024, 1);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, st);
   if (e != cudaSuccess) return e;
   bucket_count_kernel<<<blocks, 256, 0, st>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
@@ -437,7 +437,8 @@ hv_status sort_species(hv_ctx *c, int sidx, cudaStream_t stream) {
   if (st != HV_OK) return st;
   cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off, stream);
   if (e != cudaSuccess) return cuda_fail(e, "sort counts");
-  const int blocks = (int)std::min<int64_t>((sp.n + 255) / 256, 64 * 1024);
+  // one ion per thread: every ion's loads are in flight at once
+  const int blocks = (int)std::max<int64_t>((sp.n + 255) / 256, 1);
   bucket_scatter_kernel<<<blocks, 256, 0, stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
                                                            sp.n, cnt, rank);
   c->launches++;
