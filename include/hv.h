@@ -4,7 +4,8 @@
  * method of Hybrid-VPIC (arXiv 2305.05600).
  *
  * One step n -> n+1 (Sec. 2.2 of the paper):
- *   [periodic stable counting sort of the ions by cell]
+ *   [every sort_every steps: stable counting sort of the ions by supercell
+ *    key (tile, then cell in the tile)]
  *   gather E^n, B^n at x^n with the particle shape (NGP Eq. 13, QS Eqs. 17-19,
  *   or CIC on cell centres) -> non-relativistic Boris push (Eq. 9) ->
  *   deposit n, J_i at the half-step position (App. B) -> move (Eq. 10)
@@ -55,7 +56,7 @@ typedef enum {
   HV_ECFL = 4,     /* a particle moved more than one cell in a step, or the
                       whistler limit Omega dt/nsub < dx^2/pi (Sec. 2.1) fails */
   HV_ENAN = 5,     /* a non-finite particle or diagnostic */
-  HV_ETIMEOUT = 6, /* reserved: a bounded device wait gave up */
+  HV_ETIMEOUT = 6, /* a bounded device wait gave up (error bit 8) */
   HV_ESTATE = 7    /* call out of order (e.g. loading ions after stepping) */
 } hv_status;
 
@@ -83,7 +84,7 @@ typedef struct {
                            the electron energy equation (Sec. 2.1, Eq. dpdt)
                            in the field subcycles; 0: p_e = Te n^gamma_e */
   int32_t ohm_model;    /* 0: hybrid Ohm's law (Eq. 2);
-                           1: electrostatic E = -grad p_e / n_e (Sec. 3, Eq.
+                           1: electrostatic E = -grad p_e / n_e (Sec. 4, Eq.
                               esohm, without collision terms), B not advanced
                               and kept at its loaded value;
                            2: resistive background E = eta (curl B - J_k)
@@ -109,12 +110,17 @@ typedef struct {
   double charge;     /* sum over cells of n^{n+1/2} V_c (= sum q w) */
   double W_B;        /* sum over cells of 1/2 |B^{n+1}|^2 V_c */
   double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12) */
-  int32_t err_word;  /* device error bits: 1 CFL, 2 non-finite particle */
+  int32_t err_word;  /* device error bits: 1 CFL, 2 non-finite particle,
+                        4 corrupt cell index, 8 bounded wait gave up */
   int32_t pad;
 } hv_diag_t;
 
-/* Accumulated device time per phase while profiling is on (CUDA events on
- * the context stream), and the number of kernels launched. */
+/* Accumulated device time per phase while profiling is on, and the number
+ * of kernels launched.  Phases are timed with CUDA events on the context
+ * stream; a sort issued ahead of its step on the library's side stream is
+ * timed with events on that stream, so ms_sort is the sorts' own duration
+ * even where they overlap the field phase (ms_field then includes the
+ * overlap). */
 typedef struct {
   double ms_sort, ms_push, ms_moments, ms_field, ms_ohm, ms_diag;
   int64_t n_sort, n_push, n_moments, n_field, n_ohm, n_diag; /* launches */
@@ -165,8 +171,8 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
  * copied to the device (on_device != 0: they are device pointers) and every
  * value is checked there before the call returns (HV_EINVAL on a bad index,
  * offset or non-finite value; nothing of the species is kept then).  The
- * library reorders ions as it steps (sorted by cell, any order within a
- * cell) and copies weights bit for bit.  Only before the first step
+ * library reorders ions as it steps (a stable sort by supercell key, see
+ * hv_get_tile_offsets) and copies weights bit for bit.  Only before the first step
  * (HV_ESTATE afterwards). */
 hv_status hv_load_ions(hv_ctx *ctx, int32_t species, double q, double m, int64_t n,
                        const int32_t *cell, const float *off3, const float *v3,
@@ -255,6 +261,31 @@ hv_status hv_filter_get_params(hv_ctx *ctx, float *params_out);
  * both x fastest) whenever it sorts them, with tile extents as reported. */
 hv_status hv_query(const hv_ctx *ctx, hv_info_t *out);
 
+/* The ion range of every supercell tile of species `species` in the
+ * library's current particle order: tile_off [ntiles + 1] (host memory)
+ * receives the first ion of each tile and, last, the ion count.  After a
+ * sort these are the offsets of a stable counting sort of the ions'
+ * supercell keys (the key of a cell is its tile index times the cells per
+ * tile plus its cell inside the tile, x fastest; hv_query gives the tile
+ * extents); before the first sort they split the ions evenly.  The sort is
+ * an ordering device of the GPU layout (the paper prescribes none; it
+ * changes results only through FP32 summation order).  Synchronises and
+ * reports latched device errors. */
+hv_status hv_get_tile_offsets(hv_ctx *ctx, int32_t species, int32_t *tile_off);
+
+/* Fault injection for testing the failure path: OR `bits` (a non-empty
+ * combination of the hv_diag_t err_word bits 1, 2, 4, 8) into the context's
+ * device error word, as a kernel that detected the fault would.  The next
+ * synchronising call reports it (hv_error_status gives the mapping).
+ * HV_EINVAL for other bits.  Nothing on the GPU faults or waits. */
+hv_status hv_inject_error(hv_ctx *ctx, int32_t bits);
+
+/* The status that a synchronising call returns for device error word
+ * `err_word` (hv_last_error() then names the cause), without a context or a
+ * GPU: bit 2 non-finite -> HV_ENAN, else bit 1 -> HV_ECFL, else bit 4 ->
+ * HV_ECUDA, else bit 8 -> HV_ETIMEOUT, else HV_OK. */
+hv_status hv_error_status(int32_t err_word);
+
 /* Turn per-phase CUDA-event timing on (1) or off (0); turning it on resets
  * the counters.  hv_profile_read synchronises and returns the totals. */
 hv_status hv_profile(hv_ctx *ctx, int enable);
@@ -263,9 +294,9 @@ hv_status hv_profile_read(hv_ctx *ctx, hv_prof_t *out);
 /* Release every device buffer of the context (NULL is allowed). */
 void hv_destroy(hv_ctx *ctx);
 
-/* Stable sort by key, the sort the step applies to ions (keyed by the
- * supercell order of their cells); it is a device of the GPU layout and
- * changes results only through FP32 summation order.
+/* Stable sort by key: the radix passes of the step's general sort path
+ * (which sorts ions by supercell key the same way), on caller keys.  Not in
+ * the paper; it is a device of the GPU layout.
  * keys [n] int32 in [0, nkeys) on the device; perm [n] receives the gather
  * permutation (keys[perm[i]] non-decreasing, equal keys in input order);
  * counts [nkeys] (may be NULL) receives the number of each key.  All three

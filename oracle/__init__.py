@@ -29,13 +29,16 @@ SHAPES = {"ngp": 0, "qs": 1, "cic": 2}
 
 def build(force: bool = False) -> str:
     """Compile hvo.c into a shared library with gcc (no FMA contraction, so
-    x86 and Arm hosts round identically)."""
+    x86 and Arm hosts round identically), with OpenMP where gcc has it (the
+    all-core baseline; one thread unless set_threads is called)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+                "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -107,8 +110,25 @@ def lib():
             L.hvo_filter_apply.argtypes = [P, P, P, D, D, ctypes.c_int, P, P]
             L.hvo_filter_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P, P]
             L.hvo_filter_loss_grad.restype = D
+            L.hvo_set_threads.argtypes = [ctypes.c_int]
+            L.hvo_get_threads.restype = ctypes.c_int
+            L.hvo_max_threads.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the particle and cell loops (1, the default, for parity)."""
+    lib().hvo_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().hvo_get_threads())
+
+
+def max_threads() -> int:
+    """Threads OpenMP can use on this host (1 without OpenMP)."""
+    return int(lib().hvo_max_threads())
 
 
 def _p(a: np.ndarray):
@@ -344,6 +364,26 @@ def sort_stable(keys, nkeys):
     if rc != 0:
         raise ValueError("key out of range")
     return perm, counts, offsets
+
+
+def supercell_keys(cell, nx, ny, nz, tile):
+    """Keys of the library's documented ion order (``include/hv.h``,
+    hv_query / hv_get_tile_offsets), restated here so that the oracle side
+    never calls the product: for linear cell c = i + nx (j + ny k) and tile
+    extents (tx, ty, tz), key = tile index * (tx ty tz) + the cell's linear
+    index inside its tile, both x fastest.  The paper prescribes no ion
+    order; sorting only permutes the oracle's FP64 summation order."""
+    c = np.asarray(cell, dtype=np.int64)
+    tx, ty, tz = (int(t) for t in tile)
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    ntx, nty = -(-nx // tx), -(-ny // ty)
+    t = (i // tx) + ntx * ((j // ty) + nty * (k // tz))
+    return t * (tx * ty * tz) + (i % tx) + tx * ((j % ty) + ty * (k % tz))
+
+
+def supercell_nkeys(nx, ny, nz, tile) -> int:
+    tx, ty, tz = (int(t) for t in tile)
+    return (-(-nx // tx)) * (-(-ny // ty)) * (-(-nz // tz)) * tx * ty * tz
 
 
 FILTER_NPARAM = 3492

@@ -20,7 +20,8 @@
  *             coordinates in [-1,1]^3, NGP shape (Eq. 13), smoothing.
  *   App. B    QS particle shape: deposit weights (Eq. 17), interpolation
  *             coefficients (Eq. 18) and field at the particle (Eq. 19).
- *   Sec. 2.3  periodic boundaries (the only ones built here).
+ *   Sec. 2.3  boundaries: fully periodic (the simplest case, named at the
+ *             start of the section).
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   R1 relative coordinates are taken in [-1,1): a particle exactly on the
@@ -39,7 +40,7 @@
  *      the moments held at their half-step values; Ohm's law takes grad p_e
  *      from the field.  At start-up p_e = Te n_f^gamma of the start-up
  *      moments (Eq. 6).
- *   R17 the optional electrostatic model (Sec. 3, Eq. esohm): Ohm's law
+ *   R17 the optional electrostatic model (Sec. 4, Eq. esohm): Ohm's law
  *      keeps only E = -grad p_e / n_f (R_ei = 0: no collision model here);
  *      B is not advanced and stays at its initial value, which the ions
  *      still feel; with the electron energy equation u_e = J_i / n_f (no
@@ -78,6 +79,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by the particle loop and the cell loops (1 by default: the
+ * parity reference runs on one thread).  With T > 1 the particles are split
+ * into T contiguous ranges, each thread deposits into private grids, and the
+ * private grids and energy sums are added in thread order, so results are
+ * deterministic for a given T and differ from T = 1 only in FP64 summation
+ * order.  Cell loops write one output per cell and are unchanged by T. */
+static int g_threads = 1;
+
+void hvo_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+int hvo_get_threads(void) { return g_threads; }
+
+/* Threads available to OpenMP (1 when built without it). */
+int hvo_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 typedef struct {
   int64_t nx, ny, nz;
@@ -298,53 +323,91 @@ void hvo_deposit(const hvo_grid *g, const hvo_species *sp, int64_t nsp, double *
   }
 }
 
-/* The particle part of one step: for every ion, gather E^n, B^n at x^n,
+/* One ion of the particle part of a step: gather E^n, B^n at x^n,
  * Boris-push v^{n-1/2} -> v^{n+1/2}, deposit n, J at the half-step position
- * x^{n+1/2} (App. B; reading R2), then move to x^{n+1}.  n_acc, J_acc are
- * accumulated into; kin[0..3] receive sum 1/2 m w |v|^2 and sum m w v. */
+ * x^{n+1/2} (App. B; reading R2), then move to x^{n+1}.  n_acc, J_acc, kin
+ * are accumulated into (kin: sum 1/2 m w |v|^2 and sum m w v). */
+static void push_one(const hvo_grid *g, hvo_species *sp, int64_t p, double qmdt,
+                     const double *E, const double *B, double *n_acc, double *J_acc,
+                     double *kin) {
+  int64_t cell = sp->cell[p];
+  double d[3] = {sp->ox[p], sp->oy[p], sp->oz[p]};
+  double v[3] = {sp->vx[p], sp->vy[p], sp->vz[p]};
+  double Ep[3], Bp[3];
+  hvo_gather(g, E, 3, cell, d[0], d[1], d[2], Ep);
+  hvo_gather(g, B, 3, cell, d[0], d[1], d[2], Bp);
+  double u[3] = {v[0], v[1], v[2]}, gam = 1.0;
+  if (g->relativistic) {  /* R19 */
+    hvo_boris_rel(qmdt, g->c_light, Ep, Bp, u);
+    gam = lorentz(g->c_light, u);
+    for (int a = 0; a < 3; ++a) v[a] = u[a] / gam;
+  } else {
+    hvo_boris(qmdt, Ep, Bp, v);
+    for (int a = 0; a < 3; ++a) u[a] = v[a];
+  }
+  /* half-step position for the deposit */
+  int64_t ch = cell;
+  double dh[3] = {d[0], d[1], d[2]};
+  hvo_move(g, &ch, dh, v, 0.5);
+  deposit_one(g, ch, dh, v, sp->q * sp->w[p], n_acc, J_acc);
+  /* full move */
+  hvo_move(g, &cell, d, v, 1.0);
+  sp->cell[p] = cell;
+  sp->ox[p] = d[0];
+  sp->oy[p] = d[1];
+  sp->oz[p] = d[2];
+  sp->vx[p] = u[0];
+  sp->vy[p] = u[1];
+  sp->vz[p] = u[2];
+  double mw = sp->m * sp->w[p];
+  double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  kin[0] += g->relativistic ? mw * uu / (gam + 1.0) : 0.5 * mw * uu;
+  kin[1] += mw * u[0];
+  kin[2] += mw * u[1];
+  kin[3] += mw * u[2];
+}
+
+/* The particle part of one step over every ion (push_one); n_acc, J_acc
+ * are accumulated into and kin[0..3] receive the energy and momentum sums.
+ * With more than one thread each thread takes a contiguous range of ions
+ * and its own grids, added in thread order afterwards. */
 void hvo_push_deposit(const hvo_grid *g, hvo_species *sp, int64_t nsp,
                       const double *E, const double *B, double *n_acc, double *J_acc,
                       double *kin) {
+  int64_t nce = ncell_of(g);
   for (int a = 0; a < 4; ++a) kin[a] = 0.0;
   for (int64_t s = 0; s < nsp; ++s) {
     double qmdt = sp[s].q / sp[s].m * g->dt;
-    for (int64_t p = 0; p < sp[s].n; ++p) {
-      int64_t cell = sp[s].cell[p];
-      double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
-      double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
-      double Ep[3], Bp[3];
-      hvo_gather(g, E, 3, cell, d[0], d[1], d[2], Ep);
-      hvo_gather(g, B, 3, cell, d[0], d[1], d[2], Bp);
-      double u[3] = {v[0], v[1], v[2]}, gam = 1.0;
-      if (g->relativistic) {  /* R19 */
-        hvo_boris_rel(qmdt, g->c_light, Ep, Bp, u);
-        gam = lorentz(g->c_light, u);
-        for (int a = 0; a < 3; ++a) v[a] = u[a] / gam;
-      } else {
-        hvo_boris(qmdt, Ep, Bp, v);
-        for (int a = 0; a < 3; ++a) u[a] = v[a];
-      }
-      /* half-step position for the deposit */
-      int64_t ch = cell;
-      double dh[3] = {d[0], d[1], d[2]};
-      hvo_move(g, &ch, dh, v, 0.5);
-      deposit_one(g, ch, dh, v, sp[s].q * sp[s].w[p], n_acc, J_acc);
-      /* full move */
-      hvo_move(g, &cell, d, v, 1.0);
-      sp[s].cell[p] = cell;
-      sp[s].ox[p] = d[0];
-      sp[s].oy[p] = d[1];
-      sp[s].oz[p] = d[2];
-      sp[s].vx[p] = u[0];
-      sp[s].vy[p] = u[1];
-      sp[s].vz[p] = u[2];
-      double mw = sp[s].m * sp[s].w[p];
-      double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-      kin[0] += g->relativistic ? mw * uu / (gam + 1.0) : 0.5 * mw * uu;
-      kin[1] += mw * u[0];
-      kin[2] += mw * u[1];
-      kin[3] += mw * u[2];
+    int nt = g_threads;
+    if (nt <= 1 || sp[s].n < 2) {
+      for (int64_t p = 0; p < sp[s].n; ++p) push_one(g, &sp[s], p, qmdt, E, B, n_acc, J_acc, kin);
+      continue;
     }
+    double *priv = (double *)calloc((size_t)nt * (size_t)(4 * nce + 4), sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+      int tid = 0, team = 1;
+#ifdef _OPENMP
+      tid = omp_get_thread_num();
+      team = omp_get_num_threads();
+#endif
+      /* range t of nt whatever the team size OpenMP grants */
+      for (int t = tid; t < nt; t += team) {
+        double *pn = priv + (size_t)t * (4 * nce + 4);
+        int64_t p0 = sp[s].n * t / nt, p1 = sp[s].n * (t + 1) / nt;
+        for (int64_t p = p0; p < p1; ++p)
+          push_one(g, &sp[s], p, qmdt, E, B, pn, pn + nce, pn + 4 * nce);
+      }
+    }
+    for (int t = 0; t < nt; ++t) {
+      const double *pn = priv + (size_t)t * (4 * nce + 4);
+      for (int64_t c = 0; c < nce; ++c) n_acc[c] += pn[c];
+      for (int64_t c = 0; c < 3 * nce; ++c) J_acc[c] += pn[nce + c];
+      for (int a = 0; a < 4; ++a) kin[a] += pn[4 * nce + a];
+    }
+    free(priv);
   }
 }
 
@@ -363,6 +426,9 @@ static double dcen(const hvo_grid *g, const double *f, int a, int64_t i, int64_t
 void hvo_curl(const hvo_grid *g, const double *A, double *out) {
   int64_t nce = ncell_of(g);
   const double *Ax = A, *Ay = A + nce, *Az = A + 2 * nce;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
   for (int64_t c = 0; c < nce; ++c) {
     int64_t i, j, k;
     cdecode(g, c, &i, &j, &k);
@@ -375,6 +441,9 @@ void hvo_curl(const hvo_grid *g, const double *A, double *out) {
 /* out = grad f (centred) [3][ncell] */
 void hvo_grad(const hvo_grid *g, const double *f, double *out) {
   int64_t nce = ncell_of(g);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
   for (int64_t c = 0; c < nce; ++c) {
     int64_t i, j, k;
     cdecode(g, c, &i, &j, &k);
@@ -385,6 +454,9 @@ void hvo_grad(const hvo_grid *g, const double *f, double *out) {
 /* out = div A (centred) [ncell] */
 void hvo_div(const hvo_grid *g, const double *A, double *out) {
   int64_t nce = ncell_of(g);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
   for (int64_t c = 0; c < nce; ++c) {
     int64_t i, j, k;
     cdecode(g, c, &i, &j, &k);
@@ -397,6 +469,9 @@ void hvo_lap(const hvo_grid *g, const double *A, int64_t nc, double *out) {
   int64_t nce = ncell_of(g);
   for (int64_t a = 0; a < nc; ++a) {
     const double *f = A + a * nce;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (int64_t c = 0; c < nce; ++c) {
       int64_t i, j, k;
       cdecode(g, c, &i, &j, &k);
@@ -429,6 +504,9 @@ static void ohm_with(const hvo_grid *g, const double *B, const double *n, const 
     pe[c] = pe_field ? pe_field[c] : g->Te * pow(nf[c], g->gamma_e);
   }
   hvo_grad(g, pe, gp);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
   for (int64_t c = 0; c < nce; ++c) {
     if (g->ohm_model == 1) {  /* R17: E = -grad p_e / n_f */
       for (int a = 0; a < 3; ++a) E[a * nce + c] = -gp[a * nce + c] / nf[c];
@@ -573,6 +651,9 @@ void hvo_smooth(const hvo_grid *g, double *q, int64_t nc, int64_t passes) {
     for (int64_t a = 0; a < nc; ++a) {
       double *f = q + a * nce;
       for (int ax = 0; ax < 3; ++ax) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
         for (int64_t c = 0; c < nce; ++c) {
           int64_t i, j, k;
           cdecode(g, c, &i, &j, &k);

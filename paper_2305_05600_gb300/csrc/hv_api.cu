@@ -256,18 +256,25 @@ int eblocks(int64_t n) {
   return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
 }
 
-hv_status latched(hv_ctx *c, int *word) {
-  int e = 0;
-  cudaError_t r = cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
-  if (r != cudaSuccess) return cuda_fail(r, "synchronise");
-  if (word) *word = e;
+// The status reported for a device error word (see hv_error_status).
+hv_status status_of_word(int e) {
   if (e & kErrNonFinite) return fail(HV_ENAN, "a particle became non-finite");
   if (e & kErrCfl) return fail(HV_ECFL, "a particle moved more than one cell in one step");
   if (e & kErrIndex) return fail(HV_ECUDA, "a corrupt particle cell index was found");
   if (e & kErrTimeout) return fail(HV_ETIMEOUT, "a bounded device wait gave up");
   return HV_OK;
 }
+
+hv_status latched(hv_ctx *c, int *word) {
+  int e = 0;
+  cudaError_t r = cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "synchronise");
+  if (word) *word = e;
+  return status_of_word(e);
+}
+
+__global__ void inject_error_kernel(int *err, int bits) { atomicOr(err, bits); }
 
 hv_status startup(hv_ctx *c) {
   for (int s = 0; s < c->nspecies; ++s) {
@@ -286,9 +293,13 @@ hv_status startup(hv_ctx *c) {
   return HV_OK;
 }
 
+// Events of one profiled step: e[0..5] bracket the phases on the context
+// stream; e[6], e[7] bracket a sort issued on the side stream (side = 1),
+// whose own duration is added to the sort time.
 struct StepEvents {
-  cudaEvent_t e[6];
+  cudaEvent_t e[8];
   int64_t launches[5];
+  int side;
 };
 
 }  // namespace
@@ -325,7 +336,7 @@ cudaEvent_t prof_event(ProfStore *ps) {
 
 void prof_recycle(ProfStore *ps) {
   for (auto &r : ps->rec)
-    for (int i = 0; i < 6; ++i) ps->pool.push_back(r.e[i]);
+    for (int i = 0; i < 8; ++i) ps->pool.push_back(r.e[i]);
   ps->rec.clear();
 }
 
@@ -366,6 +377,7 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->p = *p;
   c->g = make_geom(p);
   c->stream = (cudaStream_t)cuda_stream;
+  c->since_sort = -1;  // ions arrive in load order
   cudaGetDevice(&c->device);
   c->vc = p->dx * p->dy * p->dz;
   c->push_blocks = c->g.ntiles * kPushSplit;  // push blocks (kPushSplit per supercell tile)
@@ -477,11 +489,12 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
     s.vz = (float *)(p + arr * slot++);
     s.w = (float *)(p + arr * slot++);
   }
-  sp.tile_off = (int *)dev_alloc(sizeof(int) * (g.ntiles + 1), c->stream);
+  sp.tile_off = (int *)dev_alloc(sizeof(int) * 2 * (g.ntiles + 1), c->stream);
   if (!sp.tile_off) {
     for (int b = 0; b < 2; ++b) dev_free(sp.base[b], sp.bytes[b], c->stream);
     return fail(HV_ENOMEM, "tile range allocation failed");
   }
+  sp.tile_off_next = sp.tile_off + (g.ntiles + 1);
   sp.cur = 0;
   // copy straight from the caller's arrays, then check and convert on the
   // device (interior cell -> voxel, single-cell-axis offsets -> 0)
@@ -512,7 +525,7 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess || bad) {
     for (int b = 0; b < 2; ++b) dev_free(sp.base[b], sp.bytes[b], c->stream);
-    dev_free(sp.tile_off, sizeof(int) * (g.ntiles + 1), c->stream);
+    dev_free(std::min(sp.tile_off, sp.tile_off_next), sizeof(int) * 2 * (g.ntiles + 1), c->stream);
     memset(&sp, 0, sizeof(sp));
     if (e != cudaSuccess) return cuda_fail(e, "hv_load_ions upload");
     if (bad & 1) return fail(HV_EINVAL, "cell index out of range");
@@ -549,7 +562,8 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
     StepEvents ev;
     int64_t l0 = c->launches;
     if (ps) {
-      for (int i = 0; i < 6; ++i) ev.e[i] = prof_event(ps);
+      for (int i = 0; i < 8; ++i) ev.e[i] = prof_event(ps);
+      ev.side = 0;
       cudaEventRecord(ev.e[0], c->stream);
     }
     const bool sort_now = c->p.sort_every > 0 && c->step % c->p.sort_every == 0;
@@ -562,6 +576,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
         hv_status st = sort_species(c, sp, c->stream);
         if (st != HV_OK) return st;
       }
+      c->since_sort = 0;
     }
     if (ps) {
       cudaEventRecord(ev.e[1], c->stream);
@@ -572,6 +587,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       cudaError_t e = launch_push(c, sp, 0);
       if (e != cudaSuccess) return cuda_fail(e, "push");
     }
+    if (c->since_sort >= 0) c->since_sort++;
     if (ps) {
       cudaEventRecord(ev.e[2], c->stream);
       ev.launches[1] = c->launches - l0;
@@ -587,10 +603,16 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       if (st != HV_OK) return st;
       cudaEventRecord(c->ev_push, c->stream);
       cudaStreamWaitEvent(c->side, c->ev_push, 0);
+      if (ps) {
+        cudaEventRecord(ev.e[6], c->side);
+        ev.side = 1;
+      }
       for (int sp = 0; sp < c->nspecies; ++sp) {
         st = sort_species(c, sp, c->side);
         if (st != HV_OK) return st;
       }
+      if (ps) cudaEventRecord(ev.e[7], c->side);
+      c->since_sort = 0;
       cudaEventRecord(c->ev_sort, c->side);
       c->presorted = 1;
       if (ps) {
@@ -955,6 +977,29 @@ hv_status hv_query(const hv_ctx *c, hv_info_t *out) {
   return HV_OK;
 }
 
+hv_status hv_get_tile_offsets(hv_ctx *c, int32_t species, int32_t *tile_off) {
+  if (!c || !tile_off) return fail(HV_EINVAL, "ctx or tile_off is NULL");
+  if (species < 0 || species >= c->nspecies) return fail(HV_EINVAL, "no such species");
+  cudaError_t e = cudaMemcpyAsync(tile_off, c->sp[species].tile_off,
+                                  sizeof(int32_t) * (size_t)(c->g.ntiles + 1),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_get_tile_offsets");
+  return latched(c, nullptr);
+}
+
+hv_status hv_inject_error(hv_ctx *c, int32_t bits) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (bits <= 0 || (bits & ~(kErrCfl | kErrNonFinite | kErrIndex | kErrTimeout)))
+    return fail(HV_EINVAL, "bits must be a non-empty combination of 1, 2, 4 and 8");
+  inject_error_kernel<<<1, 1, 0, c->stream>>>(c->err, bits);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "hv_inject_error");
+  return HV_OK;
+}
+
+hv_status hv_error_status(int32_t err_word) { return status_of_word(err_word); }
+
 hv_status hv_profile(hv_ctx *c, int enable) {
   if (!c) return fail(HV_EINVAL, "ctx is NULL");
   ProfStore *ps = prof_store(c, true);
@@ -975,6 +1020,11 @@ hv_status hv_profile_read(hv_ctx *c, hv_prof_t *out) {
   for (auto &r : ps->rec) {
     float ms[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], r.e[i], r.e[i + 1]);
+    if (r.side) {
+      float side_ms = 0.f;
+      cudaEventElapsedTime(&side_ms, r.e[6], r.e[7]);
+      ms[0] += side_ms;
+    }
     c->prof.ms_sort += ms[0];
     c->prof.ms_push += ms[1];
     c->prof.ms_moments += ms[2];
@@ -1005,7 +1055,8 @@ void hv_destroy(hv_ctx *c) {
   prof_destroy(c);
   for (int s = 0; s < c->nspecies; ++s) {
     for (int b = 0; b < 2; ++b) dev_free(c->sp[s].base[b], c->sp[s].bytes[b], c->stream);
-    dev_free(c->sp[s].tile_off, sizeof(int) * (c->g.ntiles + 1), c->stream);
+    dev_free(std::min(c->sp[s].tile_off, c->sp[s].tile_off_next),
+             sizeof(int) * 2 * (c->g.ntiles + 1), c->stream);
   }
   sort_release(c);
   for (int i = 0; i < c->nallocs; ++i) dev_free(c->allocs[i], c->alloc_bytes[i], c->stream);

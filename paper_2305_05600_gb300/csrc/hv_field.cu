@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
     float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
     float ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz_;
-    if (k.model == 1) {  // electrostatic Ohm's law (Sec. 3): E = -grad p_e / n_f
+    if (k.model == 1) {  // electrostatic Ohm's law (Sec. 4): E = -grad p_e / n_f
       ex = -gpx * inv;
       ey = -gpy * inv;
       ez = -gpz * inv;
@@ -993,13 +993,9 @@ template <int DIM, int FINAL, int PEQ = 0>
 cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
   using T = Tile<DIM, FINAL, PEQ>;
   const size_t smem = T::smem_floats * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<DIM, FINAL, PEQ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(stage_kernel<DIM, FINAL, PEQ>, smem, attr_set);
+  if (e != cudaSuccess) return e;
   const int ntx = (c->g.nx + T::OX - 1) / T::OX;
   const int nty = DIM == 2 ? 1 : (c->g.ny + T::OY - 1) / T::OY;
   const int ntz = (c->g.nz + T::OZ - 1) / T::OZ;
@@ -1096,13 +1092,10 @@ static int elem_blocks(int n) {
 static cudaError_t smooth_grid(hv_ctx *c, float4 *x, float4 *y, int passes, float4 **res) {
   const Geom &g = c->g;
   const bool fused = g.dim2;
-  static bool attr_set = false;
-  if (fused && !attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(smooth2d_multi_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smz::kBytes);
+  static std::atomic<uint64_t> attr_set{0};
+  if (fused) {
+    cudaError_t e = set_smem_once(smooth2d_multi_kernel, smz::kBytes, attr_set);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const int nb = elem_blocks(g.ncell);
   const int tiles = ((g.nx + smz::T - 1) / smz::T) * ((g.nz + smz::T - 1) / smz::T);
@@ -1180,13 +1173,9 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   c->launches++;
   if (c->g.dim2) return launch_stage_t<2, 0>(c, a);
   const size_t smem = st3d::kFloats * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(stage3d_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(stage3d_kernel, smem, attr_set);
+  if (e != cudaSuccess) return e;
   const Geom &g = c->g;
   const int blocks = ((g.nx + st3d::X - 1) / st3d::X) * ((g.ny + st3d::Y - 1) / st3d::Y) *
                      ((g.nz + st3d::Z - 1) / st3d::Z);
@@ -1204,13 +1193,9 @@ cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) 
   a.mom = c->mprev;
   a.h = h;
   const size_t smem = sub2d::kFloats * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(substep2d_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(substep2d_kernel, smem, attr_set);
+  if (e != cudaSuccess) return e;
   const int ntx = (c->g.nx + sub2d::SX - 1) / sub2d::SX;
   const int ntz = (c->g.nz + sub2d::SZ - 1) / sub2d::SZ;
   c->launches++;

@@ -398,13 +398,9 @@ __global__ void adam_kernel(float *P, float *grad, float *mom1, float *mom2, int
 size_t filter_smem_bytes() { return sizeof(Smem); }
 
 cudaError_t launch_filter(hv_ctx *c, const FilterParams &fp, const float4 *in, float4 *out) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(filter_kernel, sizeof(Smem), attr_set);
+  if (e != cudaSuccess) return e;
   const int ntx = (c->g.nx + kFT - 1) / kFT, ntz = (c->g.nz + kFT - 1) / kFT;
   c->launches++;
   filter_kernel<<<ntx * ntz, kThreads, sizeof(Smem), c->stream>>>(c->g, fp, (float)c->p.n_floor,
@@ -459,14 +455,9 @@ void pack_filter_transposed(const float *P, std::vector<__nv_bfloat16> &wt) {
 cudaError_t launch_filter_grad(hv_ctx *c, const FilterParams &fp, const __nv_bfloat16 *wt,
                                const float4 *m, const float4 *tg, int nbatch, float *grad,
                                double *loss) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(filter_grad_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(TrainSmem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(filter_grad_kernel, sizeof(TrainSmem), attr_set);
+  if (e != cudaSuccess) return e;
   const int ntx = (c->g.nx + kFT - 1) / kFT, ntz = (c->g.nz + kFT - 1) / kFT;
   const float inv = 1.f / (4.f * (float)c->g.ncell * (float)nbatch);
   c->launches++;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,22 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned bl
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per device:
+// the attribute belongs to the device that is current when it is set, so
+// `done` keeps one bit per device ordinal (ordinals above 63 set it on every
+// call).
+template <typename Kern>
+inline cudaError_t set_smem_once(Kern kern, size_t bytes, std::atomic<uint64_t> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load() & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit);
+  return e;
 }
 
 constexpr int kMaxSpecies = 8;
@@ -176,8 +193,11 @@ struct Species {
   int64_t n, cap;
   int *tile_off;        // [ntiles + 1] first ion of each tile in the live
                         // buffer (valid ranges even before the first sort)
-  int32_t *bucket;      // step sort: key counts, then offsets / cursors, and
-  size_t bucket_bytes;  // scan sums
+  int *tile_off_next;   // [ntiles + 1] the ranges the next sort writes
+  int32_t *bucket;      // step sort: key counts (then offsets), scan sums
+  size_t bucket_bytes;  // and every ion's rank in its key
+  int32_t *wcnt;        // windowed sort: per tile and window slot, the count
+  size_t wcnt_bytes;    // and then the prefix over earlier tiles
   Soa buf[2];
   int cur;              // index of the live buffer set
   void *base[2];        // allocation bases
@@ -215,6 +235,8 @@ struct hv_ctx {
                         // the previous step's field advance
   cudaEvent_t ev_push, ev_sort;
   int presorted;        // the current step's sort was issued on `side`
+  int since_sort;       // pushes since the last sort (-1: the ions are in
+                        // load order, not sorted yet)
   int device;
   double vc;
   // grids (device)
@@ -300,10 +322,13 @@ cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h);
 cudaError_t launch_diag(hv_ctx *c);
 int grid_reduce_blocks(int device);
 
-// sort: sorts species `s` of the context by cell (stable), swapping buffers
-// Counting sort of species s on stream st (the scratch is allocated on the
-// first call).
+// Stable counting sort of species s by supercell key on stream st, into the
+// other buffer set (the scratch is allocated on the first call).  The
+// windowed path is taken when every ion can have moved at most
+// sort_window(c) cells per axis since the last sort; otherwise the general
+// radix path.
 hv_status sort_species(hv_ctx *c, int s, cudaStream_t st);
+int sort_window(const hv_ctx *c);
 // equal split of species s into tile ranges (used before the first sort)
 cudaError_t tile_ranges_even(hv_ctx *c, int s);
 void sort_release(hv_ctx *c);

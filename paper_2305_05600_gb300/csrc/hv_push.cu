@@ -829,13 +829,9 @@ size_t push_smem() {
 template <int DIM, int SHAPE, int MODE>
 cudaError_t launch_t(const PushArgs &a, int blocks, cudaStream_t s) {
   const size_t smem = push_smem<DIM, SHAPE, MODE>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(push_kernel<DIM, SHAPE, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  cudaError_t e = set_smem_once(push_kernel<DIM, SHAPE, MODE>, smem, attr_set);
+  if (e != cudaSuccess) return e;
   // an ordinary launch: the push may follow a wait on the side stream's
   // sort, which a programmatic launch must not overtake
   push_kernel<DIM, SHAPE, MODE><<<blocks, kThreads, smem, s>>>(a);

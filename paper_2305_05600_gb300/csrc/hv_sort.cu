@@ -2,11 +2,15 @@
 // two cells so that gathers hit shared memory and deposits aggregate; the
 // method's result changes only through FP32 summation order).
 //
-// The step sorts each species by supercell key with one counting-sort pass
-// (sort_species).  The stable key sort of the ABI (hv_sort_keys) is a
-// least-significant-digit radix sort on (key, index) pairs with 8-bit
-// digits, ceil(log2(nkeys)/8) passes.  Each pass is reduce-then-scan, so no
-// kernel waits on another block:
+// The step sorts each species by supercell key with a stable counting sort
+// (sort_species): ions of one key keep their order, so the permutation is
+// that of a plain stable counting sort of the keys.  It has a general path
+// and a windowed path for ions that moved at most a few cells since the last
+// sort (described before sort_species below).  The general path, and the
+// stable key sort of the ABI (hv_sort_keys), is a least-significant-digit
+// radix sort on (key, index) pairs with 8-bit digits, ceil(log2(nkeys)/8)
+// passes.  Each pass is reduce-then-scan, so no kernel waits on another
+// block:
 //   upsweep   per 4096-key tile digit counts -> table[digit][tile]
 //   scan      exclusive scan of the table in digit-major order
 //   downsweep stable per-tile ranks (warp match + per-warp counters) and
@@ -300,75 +304,538 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
   return cudaSuccess;
 }
 
-// The step's sort: a counting sort of the ions by supercell key.  Counts
-// and ranks (warp-aggregated atomics), an exclusive scan of the counts,
-// then every ion is copied once to its key's offset plus its rank.  Ions
-// of one key keep no particular order among themselves (the atomics'
-// order); the deposit sums them in any order.
-// Each warp takes kUnroll consecutive chunks of 32 ions per iteration and
-// issues all their loads (and, in the count, all their atomics) before it
-// needs a result, so memory latencies overlap.
-constexpr int kUnroll = 4;
+// ----------------------------------------------------------------------------
+// The step's sort: a stable counting sort of the ions by supercell key (tile,
+// then cell in the tile); ions with equal keys keep the order they had.  Two
+// paths give the same permutation:
+//
+// General path (the first sort after loading, long sort intervals): the keys
+// go through the stable radix passes above, the ions are gathered by the
+// resulting permutation and the tile ranges are found by binary search in
+// the sorted keys.
+//
+// Windowed path: between two sorts an ion moves at most one cell per axis
+// per step (a larger move is a CFL error and the ion is held), so when at
+// most H steps have passed, every ion of tile t's last range
+// [tile_off[t], tile_off[t+1]) lies in t's window: the tile grown by H cells
+// on each side, periodically.  A cell's position in that window is its slot.
+//   rank:    one block per tile walks the tile's range in order, each warp
+//            a contiguous part with warp-private slot counters; a first walk
+//            counts, an exclusive scan over the warps turns the counts into
+//            starting ranks, a second walk gives every ion its rank among
+//            the earlier ions of the range in the same slot;
+//   prefix:  per key, the tiles whose windows hold its cell, in tile order:
+//            each (tile, slot) count becomes the number of ions of that key
+//            in earlier tiles' ranges, and their sum is the key's count;
+//   scan:    counts -> offsets (in place), tile ranges from the offsets;
+//   scatter: one block per tile moves every ion to
+//            offset[key] + prefix[tile][slot] + rank.
+// ----------------------------------------------------------------------------
+template <int DIM>
+struct SortWin {
+  static constexpr int TX = DIM == 2 ? kTile2X : kTile3;
+  static constexpr int TY = DIM == 2 ? 1 : kTile3;
+  static constexpr int TZ = DIM == 2 ? kTile2Z : kTile3;
+  static constexpr int H = DIM == 2 ? 8 : 4;  // window halo in cells
+  static constexpr int WX = TX + 2 * H, WY = DIM == 2 ? 1 : TY + 2 * H, WZ = TZ + 2 * H;
+  static constexpr int NS = WX * WY * WZ;     // slots per window
+  static constexpr int WARPS = DIM == 2 ? 8 : 4;
+  static constexpr size_t rank_smem = sizeof(int32_t) * WARPS * NS;
+  static constexpr size_t scatter_smem = sizeof(int32_t) * NS;
+  static_assert(NS <= 65536, "slots are cached as 16-bit values");
+};
 
-// Key counts with warp-aggregated atomics; the value an atomic returns
-// gives every ion its rank among the ions of its key, which the scatter
-// uses to place it without atomics of its own.
-__global__ void bucket_count_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *cnt,
-                                    int32_t *rank) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wstride = (int64_t)gridDim.x * blockDim.x * kUnroll;
-  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kUnroll;
-       base < n; base += wstride) {
-    int v[kUnroll];
+constexpr int kSortUnroll = 4;
+
+// v mod n in [0, n) (v is almost always already in range)
+__device__ __forceinline__ int wrap0(int v, int n) {
+  if (v >= 0 && v < n) return v;
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Interior cell of a voxel index; false for a voxel that is not interior.
+__device__ __forceinline__ bool vox_cell(const Geom &g, int vox, int &i, int &j, int &k) {
+  if (vox < g.vlo || vox >= g.vhi) return false;
+  const uint32_t v = (uint32_t)vox;
+  const uint32_t q = fdiv(v, g.div_px);
+  i = (int)(v - q * (uint32_t)g.px) - kGhost;
+  if (g.dim2) {
+    j = 0;
+    k = (int)q - kGhost;
+  } else {
+    const int kp = (int)fdiv(q, g.div_py);
+    j = (int)q - kp * g.py - kGhost;
+    k = kp - kGhost;
+  }
+  return (unsigned)i < (unsigned)g.nx && (unsigned)j < (unsigned)g.ny &&
+         (unsigned)k < (unsigned)g.nz;
+}
+
+// Origin cell of tile t.
+template <int DIM>
+__device__ __forceinline__ void tile_origin(const Geom &g, int t, int &x0, int &y0, int &z0) {
+  using SW = SortWin<DIM>;
+  x0 = (t % g.ntx) * SW::TX;
+  y0 = ((t / g.ntx) % g.nty) * SW::TY;
+  z0 = (t / (g.ntx * g.nty)) * SW::TZ;
+}
+
+// Slot of cell (i, j, k) in the window of the tile with origin (x0, y0, z0),
+// or -1 outside it.  The periodic offset is taken in [0, n) per axis, so
+// every cell has one slot even where the window is wider than the grid.
+template <int DIM>
+__device__ __forceinline__ int win_slot(const Geom &g, int x0, int y0, int z0, int i, int j,
+                                        int k) {
+  using SW = SortWin<DIM>;
+  const int sx = wrap0(i - x0 + SW::H, g.nx);
+  const int sz = wrap0(k - z0 + SW::H, g.nz);
+  const int sy = DIM == 2 ? 0 : wrap0(j - y0 + SW::H, g.ny);
+  if (sx >= SW::WX || sy >= SW::WY || sz >= SW::WZ) return -1;
+  return sx + SW::WX * (sy + SW::WY * sz);
+}
+
+// Slot of an ion in tile t's window; an ion that is not in the window (only
+// a corrupt cell index can do that) takes slot 0 and raises the index error.
+template <int DIM>
+__device__ __forceinline__ int ion_slot(const Geom &g, int x0, int y0, int z0, int vox,
+                                        bool &bad) {
+  int i, j, k;
+  int s = -1;
+  if (vox_cell(g, vox, i, j, k)) s = win_slot<DIM>(g, x0, y0, z0, i, j, k);
+  if (s < 0) {
+    bad = true;
+    s = 0;
+  }
+  return s;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(SortWin<DIM>::WARPS * 32)
+    wsort_rank_kernel(Geom g, const int32_t *vox, const int *tile_off, int32_t *wcnt,
+                      int32_t *rank, uint16_t *slot_cache, int *err) {
+  using SW = SortWin<DIM>;
+  extern __shared__ int32_t cw[];  // [WARPS][NS] warp-private slot counters
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x;
+  int x0, y0, z0;
+  tile_origin<DIM>(g, t, x0, y0, z0);
+  for (int s = threadIdx.x; s < SW::WARPS * SW::NS; s += blockDim.x) cw[s] = 0;
+  __syncthreads();
+  const int a = tile_off[t], b = tile_off[t + 1];
+  const int64_t len = b - a;
+  const int wa = a + (int)(len * warp / SW::WARPS), wb = a + (int)(len * (warp + 1) / SW::WARPS);
+  int32_t *mine = cw + warp * SW::NS;
+  const unsigned lt = (1u << lane) - 1u;
+  bool bad = false;
+  for (int walk = 0; walk < 2; ++walk) {
+    for (int base = wa; base < wb; base += 32 * kSortUnroll) {
+      int sl[kSortUnroll];
+      if (walk == 0) {
+        // the first walk computes the slots and keeps them for the second
+        int v[kSortUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t i = base + 32 * u + lane;
-      v[u] = i < n ? vox[i] : 0;
+        for (int u = 0; u < kSortUnroll; ++u) {
+          const int idx = base + 32 * u + lane;
+          v[u] = idx < wb ? vox[idx] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+          const int idx = base + 32 * u + lane;
+          sl[u] = idx < wb ? ion_slot<DIM>(g, x0, y0, z0, v[u], bad) : 0;
+          if (idx < wb) slot_cache[idx] = (uint16_t)sl[u];
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+          const int idx = base + 32 * u + lane;
+          sl[u] = idx < wb ? (int)slot_cache[idx] : 0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kSortUnroll; ++u) {
+        const int idx = base + 32 * u + lane;
+        const unsigned act = __ballot_sync(kFull, idx < wb);
+        if (idx < wb) {
+          const unsigned peers = __match_any_sync(act, sl[u]);
+          const int before = mine[sl[u]];
+          __syncwarp(act);
+          if (lane == __ffs(peers) - 1) mine[sl[u]] = before + __popc(peers);
+          if (walk == 1) rank[idx] = before + __popc(peers & lt);
+        }
+        __syncwarp();
+      }
     }
-    int r[kUnroll];
+    __syncthreads();
+    if (walk == 0) {
+      // per slot: the warps' counts -> their starting ranks; the tile's total
+      for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) {
+        int run = 0;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t i = base + 32 * u + lane;
-      const unsigned act = __ballot_sync(kFull, i < n);
-      if (i >= n) continue;
-      const int key = ion_key(g, v[u]);
-      const unsigned peers = __match_any_sync(act, key);
-      const int leader = __ffs(peers) - 1;
-      int first = 0;
-      if (lane == leader) first = atomicAdd(&cnt[key], __popc(peers));
-      first = __shfl_sync(act, first, leader);
-      r[u] = first + __popc(peers & ((1u << lane) - 1u));
+        for (int w = 0; w < SW::WARPS; ++w) {
+          const int c = cw[w * SW::NS + s];
+          cw[w * SW::NS + s] = run;
+          run += c;
+        }
+        wcnt[(size_t)t * SW::NS + s] = run;
+      }
+      __syncthreads();
+    }
+  }
+  if (bad) atomicOr(err, kErrIndex);
+}
+
+// Distinct tile coordinates T-1, T, T+1 (periodic) on an axis of n tiles.
+__device__ __forceinline__ int tile_neighbours(int T, int n, int *out) {
+  int c = 0;
+  const int cand[3] = {T == 0 ? n - 1 : T - 1, T, T == n - 1 ? 0 : T + 1};
+  for (int q = 0; q < 3; ++q) {
+    bool dup = false;
+    for (int r = 0; r < c; ++r) dup = dup || out[r] == cand[q];
+    if (!dup) out[c++] = cand[q];
+  }
+  return c;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) wsort_prefix_kernel(Geom g, int32_t *wcnt, int32_t *cnt) {
+  using SW = SortWin<DIM>;
+  const int nkeys = g.ntiles << g.tlog;
+  for (int key = blockIdx.x * blockDim.x + threadIdx.x; key < nkeys;
+       key += gridDim.x * blockDim.x) {
+    const int T = key >> g.tlog, l = key & ((1 << g.tlog) - 1);
+    const int Tx = T % g.ntx, Ty = (T / g.ntx) % g.nty, Tz = T / (g.ntx * g.nty);
+    const int i = Tx * SW::TX + l % SW::TX;
+    const int j = Ty * SW::TY + (l / SW::TX) % SW::TY;
+    const int k = Tz * SW::TZ + l / (SW::TX * SW::TY);
+    if (i >= g.nx || j >= g.ny || k >= g.nz) {  // a cell of a ragged tile that does not exist
+      cnt[key] = 0;
+      continue;
+    }
+    int cx[3], cy[3], cz[3];
+    const int nxc = tile_neighbours(Tx, g.ntx, cx);
+    const int nyc = DIM == 2 ? 1 : tile_neighbours(Ty, g.nty, cy);
+    if (DIM == 2) cy[0] = 0;
+    const int nzc = tile_neighbours(Tz, g.ntz, cz);
+    int cand[27];
+    int nc = 0;
+    for (int c3 = 0; c3 < nzc; ++c3)
+      for (int c2 = 0; c2 < nyc; ++c2)
+        for (int c1 = 0; c1 < nxc; ++c1) {
+          // insertion into ascending order: ranges lie in tile order
+          const int v = cx[c1] + g.ntx * (cy[c2] + g.nty * cz[c3]);
+          int p = nc++;
+          while (p > 0 && cand[p - 1] > v) {
+            cand[p] = cand[p - 1];
+            --p;
+          }
+          cand[p] = v;
+        }
+    int run = 0;
+    for (int q = 0; q < nc; ++q) {
+      int x0, y0, z0;
+      tile_origin<DIM>(g, cand[q], x0, y0, z0);
+      const int s = win_slot<DIM>(g, x0, y0, z0, i, j, k);
+      if (s < 0) continue;
+      int32_t *p = wcnt + (size_t)cand[q] * SW::NS + s;
+      const int c = *p;
+      *p = run;
+      run += c;
+    }
+    cnt[key] = run;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) wsort_scatter_kernel(Geom g, Soa in, Soa out,
+                                                            const int *tile_off,
+                                                            const int32_t *wpre,
+                                                            const int32_t *off,
+                                                            const int32_t *rank) {
+  using SW = SortWin<DIM>;
+  extern __shared__ int32_t dbase[];  // [NS] first destination of each slot
+  const int t = blockIdx.x;
+  int x0, y0, z0;
+  tile_origin<DIM>(g, t, x0, y0, z0);
+  for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) {
+    const int sx = s % SW::WX, sy = (s / SW::WX) % SW::WY, sz = s / (SW::WX * SW::WY);
+    const int i = wrap0(x0 - SW::H + sx, g.nx);
+    const int j = DIM == 2 ? 0 : wrap0(y0 - SW::H + sy, g.ny);
+    const int k = wrap0(z0 - SW::H + sz, g.nz);
+    dbase[s] = off[supercell_key(g, i, j, k)] + wpre[(size_t)t * SW::NS + s];
+  }
+  __syncthreads();
+  const int a = tile_off[t], b = tile_off[t + 1];
+  const bool has_y = in.oy != nullptr;
+  bool bad = false;
+  for (int i0 = a + threadIdx.x; i0 < b; i0 += blockDim.x * kSortUnroll) {
+    int c[kSortUnroll], r[kSortUnroll];
+    float x[kSortUnroll], y[kSortUnroll], z[kSortUnroll], vx[kSortUnroll], vy[kSortUnroll],
+        vz[kSortUnroll], w[kSortUnroll];
+#pragma unroll
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i >= b) continue;
+      c[u] = in.cell[i];
+      r[u] = rank[i];
+      x[u] = in.ox[i];
+      y[u] = has_y ? in.oy[i] : 0.f;
+      z[u] = in.oz[i];
+      vx[u] = in.vx[i];
+      vy[u] = in.vy[i];
+      vz[u] = in.vz[i];
+      w[u] = in.w[i];
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t i = base + 32 * u + lane;
-      if (i < n) rank[i] = r[u];
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i >= b) continue;
+      const int d = dbase[ion_slot<DIM>(g, x0, y0, z0, c[u], bad)] + r[u];
+      out.cell[d] = c[u];
+      out.ox[d] = x[u];
+      if (has_y) out.oy[d] = y[u];
+      out.oz[d] = z[u];
+      out.vx[d] = vx[u];
+      out.vy[d] = vy[u];
+      out.vz[d] = vz[u];
+      out.w[d] = w[u];
     }
   }
 }
 
-// Copy every ion to off[key] + rank.  (Issuing several ions' loads per
-// thread measured no faster: at a sort every few steps the drifted ions
-// make short store segments, and those, not load latency, set the pace.)
-__global__ void bucket_scatter_kernel(Geom g, Soa in, Soa out, int64_t n, const int32_t *off,
-                                      const int32_t *rank) {
+// The same scatter with the stores grouped: a block takes its tile's ions in
+// chunks of kScatChunk, places each chunk in shared memory grouped by window
+// slot (the chunk's ions of one slot have consecutive destinations), and
+// writes the staged ions out in that order, so a warp's store covers one or
+// two contiguous runs instead of the five or so that 32 consecutive ions of
+// a drifted tile scatter to.
+// Scatter variant of the windowed path: 0 per-tile blocks, 1 per-tile
+// blocks with staged stores, 2 one ion per thread over the whole array.
+#ifndef HV_WSCATTER_MODE
+#define HV_WSCATTER_MODE 2
+#endif
+constexpr int kScatChunk = 1024;
+
+template <int DIM>
+struct ScatSmem {
+  static constexpr int NS = SortWin<DIM>::NS;
+  // dbase[NS], bins[NS], dest[chunk], fields[8][chunk]
+  static constexpr size_t bytes = sizeof(int32_t) * (2 * NS + 9 * kScatChunk);
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(256) wsort_scatter_staged_kernel(Geom g, Soa in, Soa out,
+                                                                   const int *tile_off,
+                                                                   const int32_t *wpre,
+                                                                   const int32_t *off,
+                                                                   const int32_t *rank) {
+  using SW = SortWin<DIM>;
+  constexpr int PT = kScatChunk / 256;  // ions per thread per chunk
+  constexpr int BPT = (SW::NS + 255) / 256;  // bins per thread in the scan
+  __shared__ int s_warp[kWarps + 1];
+  extern __shared__ int32_t ssm[];
+  int32_t *dbase = ssm;                 // first destination of each slot
+  int32_t *bins = dbase + SW::NS;       // chunk counts per slot, then offsets
+  int32_t *sdst = bins + SW::NS;        // destinations in staged order
+  int32_t *sval = sdst + kScatChunk;    // [8][chunk] fields in staged order
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int t = blockIdx.x;
+  int x0, y0, z0;
+  tile_origin<DIM>(g, t, x0, y0, z0);
+  for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) {
+    const int sx = s % SW::WX, sy = (s / SW::WX) % SW::WY, sz = s / (SW::WX * SW::WY);
+    const int i = wrap0(x0 - SW::H + sx, g.nx);
+    const int j = DIM == 2 ? 0 : wrap0(y0 - SW::H + sy, g.ny);
+    const int k = wrap0(z0 - SW::H + sz, g.nz);
+    dbase[s] = off[supercell_key(g, i, j, k)] + wpre[(size_t)t * SW::NS + s];
+  }
+  const int a = tile_off[t], b = tile_off[t + 1];
   const bool has_y = in.oy != nullptr;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int c = in.cell[i];
-    const float x = in.ox[i];
-    const float y = has_y ? in.oy[i] : 0.f;
-    const float z = in.oz[i];
-    const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
-    const int d = __ldg(off + ion_key(g, c)) + rank[i];
-    out.cell[d] = c;
-    out.ox[d] = x;
-    if (has_y) out.oy[d] = y;
-    out.oz[d] = z;
-    out.vx[d] = vx;
-    out.vy[d] = vy;
-    out.vz[d] = vz;
-    out.w[d] = w;
+  bool bad = false;
+  for (int c0 = a; c0 < b; c0 += kScatChunk) {
+    for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) bins[s] = 0;
+    __syncthreads();
+    int sl[PT], d[PT], pos[PT];
+    uint32_t f[PT][8];
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int i = c0 + threadIdx.x + 256 * u;
+      sl[u] = 0;
+      if (i >= b) continue;
+      const int c = in.cell[i];
+      d[u] = rank[i];
+      f[u][0] = (uint32_t)c;
+      f[u][1] = __float_as_uint(in.ox[i]);
+      f[u][2] = has_y ? __float_as_uint(in.oy[i]) : 0u;
+      f[u][3] = __float_as_uint(in.oz[i]);
+      f[u][4] = __float_as_uint(in.vx[i]);
+      f[u][5] = __float_as_uint(in.vy[i]);
+      f[u][6] = __float_as_uint(in.vz[i]);
+      f[u][7] = __float_as_uint(in.w[i]);
+      sl[u] = ion_slot<DIM>(g, x0, y0, z0, c, bad);
+      d[u] += dbase[sl[u]];
+    }
+    // position of each ion within its slot's group of the chunk
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int i = c0 + threadIdx.x + 256 * u;
+      const unsigned act = __ballot_sync(kFull, i < b);
+      if (i < b) {
+        const unsigned peers = __match_any_sync(act, sl[u]);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&bins[sl[u]], __popc(peers));
+        base = __shfl_sync(act, base, leader);
+        pos[u] = base + __popc(peers & lt);
+      }
+    }
+    __syncthreads();
+    // exclusive scan of the slot counts: BPT consecutive bins per thread
+    {
+      int v[BPT], tot = 0;
+#pragma unroll
+      for (int q = 0; q < BPT; ++q) {
+        const int s = threadIdx.x * BPT + q;
+        v[q] = s < SW::NS ? bins[s] : 0;
+        tot += v[q];
+      }
+      int total;
+      int ex = block_exclusive_scan(tot, s_warp, total);
+#pragma unroll
+      for (int q = 0; q < BPT; ++q) {
+        const int s = threadIdx.x * BPT + q;
+        if (s < SW::NS) bins[s] = ex;
+        ex += v[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int i = c0 + threadIdx.x + 256 * u;
+      if (i >= b) continue;
+      const int j = bins[sl[u]] + pos[u];
+      sdst[j] = d[u];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sval[q * kScatChunk + j] = (int32_t)f[u][q];
+    }
+    __syncthreads();
+    const int m = min(kScatChunk, b - c0);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const int dd = sdst[j];
+      out.cell[dd] = sval[j];
+      out.ox[dd] = __int_as_float(sval[kScatChunk + j]);
+      if (has_y) out.oy[dd] = __int_as_float(sval[2 * kScatChunk + j]);
+      out.oz[dd] = __int_as_float(sval[3 * kScatChunk + j]);
+      out.vx[dd] = __int_as_float(sval[4 * kScatChunk + j]);
+      out.vy[dd] = __int_as_float(sval[5 * kScatChunk + j]);
+      out.vz[dd] = __int_as_float(sval[6 * kScatChunk + j]);
+      out.w[dd] = __int_as_float(sval[7 * kScatChunk + j]);
+    }
+    __syncthreads();
+  }
+}
+
+// First destination of every (tile, slot): the key's offset plus the count
+// of its ions in earlier tiles' ranges (in place over the prefixes).
+template <int DIM>
+__global__ void __launch_bounds__(256) wsort_base_kernel(Geom g, int32_t *wpre,
+                                                         const int32_t *off) {
+  using SW = SortWin<DIM>;
+  const int64_t total = (int64_t)g.ntiles * SW::NS;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / SW::NS), s = (int)(e - (int64_t)t * SW::NS);
+    int x0, y0, z0;
+    tile_origin<DIM>(g, t, x0, y0, z0);
+    const int sx = s % SW::WX, sy = (s / SW::WX) % SW::WY, sz = s / (SW::WX * SW::WY);
+    const int i = wrap0(x0 - SW::H + sx, g.nx);
+    const int j = DIM == 2 ? 0 : wrap0(y0 - SW::H + sy, g.ny);
+    const int k = wrap0(z0 - SW::H + sz, g.nz);
+    wpre[e] += off[supercell_key(g, i, j, k)];
+  }
+}
+
+// The scatter with one ion per thread over the whole array (full occupancy):
+// each warp finds the tile range holding its first ion by binary search in
+// tile_off, its lanes step forward across range ends, and an ion goes to
+// wbase[tile][slot] + rank.
+template <int DIM>
+__global__ void __launch_bounds__(256) wsort_scatter_flat_kernel(Geom g, Soa in, Soa out, int64_t n,
+                                                                 const int *tile_off,
+                                                                 const int32_t *wbase,
+                                                                 const int32_t *rank) {
+  using SW = SortWin<DIM>;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i0 = i - (threadIdx.x & 31);  // the warp's first ion
+  if (i0 >= n) return;
+  int t = 0;
+  if ((threadIdx.x & 31) == 0) {
+    int lo = 0, hi = g.ntiles;  // last tile whose range starts at or before i0
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)__ldg(tile_off + mid) <= i0) lo = mid;
+      else hi = mid;
+    }
+    t = lo;
+  }
+  t = __shfl_sync(kFull, t, 0);
+  if (i >= n) return;
+  while (t + 1 < g.ntiles && (int64_t)__ldg(tile_off + t + 1) <= i) ++t;
+  int x0, y0, z0;
+  tile_origin<DIM>(g, t, x0, y0, z0);
+  const int c = in.cell[i];
+  const int r = rank[i];
+  const bool has_y = in.oy != nullptr;
+  const float x = in.ox[i], y = has_y ? in.oy[i] : 0.f, z = in.oz[i];
+  const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
+  bool bad = false;
+  const int d = __ldg(wbase + (size_t)t * SW::NS + ion_slot<DIM>(g, x0, y0, z0, c, bad)) + r;
+  out.cell[d] = c;
+  out.ox[d] = x;
+  if (has_y) out.oy[d] = y;
+  out.oz[d] = z;
+  out.vx[d] = vx;
+  out.vy[d] = vy;
+  out.vz[d] = vz;
+  out.w[d] = w;
+}
+
+// General path: keys, gather by permutation, tile ranges from sorted keys.
+__global__ void ion_keys_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = ion_key(g, vox[i]);
+}
+
+__global__ void gather_kernel(Soa in, Soa out, const int32_t *perm, int64_t n) {
+  const bool has_y = in.oy != nullptr;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = perm[i];
+    out.cell[i] = in.cell[s];
+    out.ox[i] = in.ox[s];
+    if (has_y) out.oy[i] = in.oy[s];
+    out.oz[i] = in.oz[s];
+    out.vx[i] = in.vx[s];
+    out.vy[i] = in.vy[s];
+    out.vz[i] = in.vz[s];
+    out.w[i] = in.w[s];
+  }
+}
+
+// tile_off[t] = first index whose sorted key is >= t << tlog (binary search)
+__global__ void tile_bounds_kernel(const int32_t *skeys, int64_t n, int tlog, int ntiles,
+                                   int *tile_off) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
+    const int64_t target = (int64_t)t << tlog;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)skeys[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    tile_off[t] = (int)lo;
   }
 }
 
@@ -387,64 +854,122 @@ __global__ void tile_even_kernel(int64_t n, int ntiles, int *off) {
 
 namespace {
 
-// Per-species key counts, scan sums and ion ranks, allocated at the first
-// sort.
-hv_status bucket_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum,
-                         int32_t **rank) {
+// Per-species scratch of the windowed path: key counts (scanned in place
+// into offsets), the scan's chunk sums, every ion's rank, and the per-tile
+// window counts; allocated at the species' first windowed sort.
+template <int DIM>
+hv_status window_reserve(hv_ctx *c, Species &sp, int32_t **cnt, int32_t **bsum, int32_t **rank,
+                         uint16_t **slots) {
   const Geom &g = c->g;
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
   const size_t kb = align256(sizeof(int32_t) * nkeys), bb = align256(sizeof(int32_t) * nb);
+  const size_t rb = align256(sizeof(int32_t) * std::max<int64_t>(sp.n, 1));
   if (!sp.bucket) {
-    sp.bucket_bytes = kb + bb + align256(sizeof(int32_t) * std::max<int64_t>(sp.n, 1));
+    sp.bucket_bytes = kb + bb + rb + align256(sizeof(uint16_t) * std::max<int64_t>(sp.n, 1));
     sp.bucket = (int32_t *)dev_alloc(sp.bucket_bytes, c->stream);
     if (!sp.bucket) return fail(HV_ENOMEM, "sort scratch allocation failed");
+  }
+  if (!sp.wcnt) {
+    sp.wcnt_bytes = sizeof(int32_t) * (size_t)g.ntiles * SortWin<DIM>::NS;
+    sp.wcnt = (int32_t *)dev_alloc(sp.wcnt_bytes, c->stream);
+    if (!sp.wcnt) return fail(HV_ENOMEM, "sort window allocation failed");
   }
   *cnt = sp.bucket;
   *bsum = (int32_t *)((char *)sp.bucket + kb);
   *rank = (int32_t *)((char *)sp.bucket + kb + bb);
+  *slots = (uint16_t *)((char *)sp.bucket + kb + bb + rb);
   return HV_OK;
 }
 
-// Counts of the live buffer's keys and every ion's rank in its key, the
-// counts scanned in place into offsets, and the tile starts taken from them
-// into tile_off.
-cudaError_t key_offsets(hv_ctx *c, Species &sp, int32_t *cnt, int32_t *bsum, int32_t *rank,
-                        int *tile_off, cudaStream_t st) {
+template <int DIM>
+hv_status sort_windowed(hv_ctx *c, Species &sp, cudaStream_t st) {
+  using SW = SortWin<DIM>;
   const Geom &g = c->g;
+  int32_t *cnt, *bsum, *rank;
+  uint16_t *slots;
+  hv_status hs = window_reserve<DIM>(c, sp, &cnt, &bsum, &rank, &slots);
+  if (hs != HV_OK) return hs;
+  static std::atomic<uint64_t> attr_rank{0}, attr_scatter{0};
+  cudaError_t e = set_smem_once(wsort_rank_kernel<DIM>, SW::rank_smem, attr_rank);
+  if (e == cudaSuccess && HV_WSCATTER_MODE == 1)
+    e = set_smem_once(wsort_scatter_staged_kernel<DIM>, ScatSmem<DIM>::bytes, attr_scatter);
+  if (e == cudaSuccess && HV_WSCATTER_MODE == 0)
+    e = set_smem_once(wsort_scatter_kernel<DIM>, SW::scatter_smem, attr_scatter);
+  if (e != cudaSuccess) return cuda_fail(e, "sort kernel attributes");
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
-  const int blocks = (int)std::max<int64_t>((sp.n + 1023) / 1024, 1);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nkeys, st);
-  if (e != cudaSuccess) return e;
-  bucket_count_kernel<<<blocks, 256, 0, st>>>(g, sp.buf[sp.cur].cell, sp.n, cnt, rank);
+  const Soa &src = sp.buf[sp.cur];
+  wsort_rank_kernel<DIM><<<g.ntiles, SW::WARPS * 32, SW::rank_smem, st>>>(
+      g, src.cell, sp.tile_off, sp.wcnt, rank, slots, c->err);
+  wsort_prefix_kernel<DIM><<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(g, sp.wcnt, cnt);
   chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
   scan_bsum_kernel<<<1, kThreads, 0, st>>>(bsum, nb);
   chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
   tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(cnt, g.tlog, g.ntiles, sp.n,
-                                                                     tile_off);
-  c->launches += 5;
-  return cudaGetLastError();
+                                                             sp.tile_off_next);
+  if (HV_WSCATTER_MODE == 2) {
+    const int64_t tot = (int64_t)g.ntiles * SW::NS;
+    wsort_base_kernel<DIM><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8 * 2048), 256, 0, st>>>(
+        g, sp.wcnt, cnt);
+    wsort_scatter_flat_kernel<DIM><<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(
+        g, src, sp.buf[sp.cur ^ 1], sp.n, sp.tile_off, sp.wcnt, rank);
+    c->launches++;
+  } else if (HV_WSCATTER_MODE == 1) {
+    wsort_scatter_staged_kernel<DIM><<<g.ntiles, 256, ScatSmem<DIM>::bytes, st>>>(
+        g, src, sp.buf[sp.cur ^ 1], sp.tile_off, sp.wcnt, cnt, rank);
+  } else {
+    wsort_scatter_kernel<DIM><<<g.ntiles, 256, SW::scatter_smem, st>>>(
+        g, src, sp.buf[sp.cur ^ 1], sp.tile_off, sp.wcnt, cnt, rank);
+  }
+  c->launches += 7;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "windowed sort");
+  return HV_OK;
+}
+
+hv_status sort_general(hv_ctx *c, Species &sp, cudaStream_t st) {
+  const Geom &g = c->g;
+  if (!scratch_reserve(c->sort, sp.n, st)) return fail(HV_ENOMEM, "sort scratch allocation failed");
+  SortScratch *s = c->sort;
+  const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
+  const Soa &src = sp.buf[sp.cur];
+  const int eb = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 2048);
+  // the keys live in v[1]: the first radix pass reads them and writes
+  // k[0], v[0]; later passes overwrite them only after that
+  ion_keys_kernel<<<eb, 256, 0, st>>>(g, src.cell, sp.n, s->v[1]);
+  int32_t *perm = nullptr, *skeys = nullptr;
+  int64_t launches = 1;
+  cudaError_t e = radix_perm(s->v[1], sp.n, nkeys, s, st, &perm, &launches, &skeys);
+  if (e == cudaSuccess) {
+    gather_kernel<<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(src, sp.buf[sp.cur ^ 1], perm,
+                                                                  sp.n);
+    tile_bounds_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(skeys, sp.n, g.tlog, g.ntiles,
+                                                              sp.tile_off_next);
+    launches += 2;
+    e = cudaGetLastError();
+  }
+  c->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(e, "general sort");
+  return HV_OK;
 }
 
 }  // namespace
 
+int sort_window(const hv_ctx *c) { return c->g.dim2 ? SortWin<2>::H : SortWin<3>::H; }
+
 hv_status sort_species(hv_ctx *c, int sidx, cudaStream_t stream) {
   Species &sp = c->sp[sidx];
-  if (sp.n <= 1) return HV_OK;
-  int32_t *cnt, *bsum, *rank;
-  hv_status st = bucket_reserve(c, sp, &cnt, &bsum, &rank);
+  if (sp.n == 0) return HV_OK;
+  const bool windowed = c->since_sort >= 0 && c->since_sort <= sort_window(c);
+  hv_status st;
+  if (windowed)
+    st = c->g.dim2 ? sort_windowed<2>(c, sp, stream) : sort_windowed<3>(c, sp, stream);
+  else
+    st = sort_general(c, sp, stream);
   if (st != HV_OK) return st;
-  cudaError_t e = key_offsets(c, sp, cnt, bsum, rank, sp.tile_off, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "sort counts");
-  // one ion per thread: every ion's loads are in flight at once
-  const int blocks = (int)std::max<int64_t>((sp.n + 255) / 256, 1);
-  bucket_scatter_kernel<<<blocks, 256, 0, stream>>>(c->g, sp.buf[sp.cur], sp.buf[sp.cur ^ 1],
-                                                           sp.n, cnt, rank);
-  c->launches++;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "sort");
   sp.cur ^= 1;
+  std::swap(sp.tile_off, sp.tile_off_next);
   return HV_OK;
 }
 
@@ -465,7 +990,9 @@ void sort_release(hv_ctx *c) {
   for (int s = 0; s < kMaxSpecies; ++s) {
     Species &sp = c->sp[s];
     if (sp.bucket) dev_free(sp.bucket, sp.bucket_bytes, c->stream);
+    if (sp.wcnt) dev_free(sp.wcnt, sp.wcnt_bytes, c->stream);
     sp.bucket = nullptr;
+    sp.wcnt = nullptr;
   }
 }
 

@@ -85,8 +85,8 @@ EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_mo
            "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
            "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
-           "hv_filter_get_params", "hv_electron_pressure",
-           "hv_last_error"]
+           "hv_filter_get_params", "hv_electron_pressure", "hv_get_tile_offsets",
+           "hv_inject_error", "hv_error_status", "hv_last_error"]
 
 
 def library_path() -> str:
@@ -113,6 +113,9 @@ def lib():
         L.hv_electron_pressure.argtypes = [P, P, ctypes.c_int]
         L.hv_get_ions.argtypes = [P, I32, ctypes.POINTER(I64), P, P, P, P, ctypes.c_int]
         L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
+        L.hv_get_tile_offsets.argtypes = [P, I32, P]
+        L.hv_inject_error.argtypes = [P, I32]
+        L.hv_error_status.argtypes = [I32]
         L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
         L.hv_filter_moments.argtypes = [P, P, P, ctypes.c_int]
         L.hv_filter_train_init.argtypes = [P, P, P]
@@ -378,16 +381,23 @@ def hv_query(ctx: Ctx) -> dict:
             "nspecies": info.nspecies, "n": list(info.n)[:info.nspecies], "step": info.step}
 
 
-def supercell_keys(cell, params, tile):
-    """Supercell sort keys of linear cell indices (the order hv_step sorts
-    ions into): tile index, then the cell inside the tile, x fastest."""
-    c = np.asarray(cell, dtype=np.int64)
-    nx, ny = int(params["nx"]), int(params["ny"])
-    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
-    tx, ty, tz = tile
-    ntx, nty = -(-nx // tx), -(-ny // ty)
-    t = (i // tx) + ntx * ((j // ty) + nty * (k // tz))
-    return t * (tx * ty * tz) + (i % tx) + tx * ((j % ty) + ty * (k % tz))
+def hv_get_tile_offsets(ctx: Ctx, species: int = 0) -> np.ndarray:
+    """Ion range of every supercell tile of a species (ntiles + 1 offsets)."""
+    nt = hv_query(ctx)["ntiles"]
+    out = np.zeros(nt + 1, np.int32)
+    _check(lib().hv_get_tile_offsets(ctx.handle, int(species), out.ctypes.data))
+    return out
+
+
+def hv_inject_error(ctx: Ctx, bits: int):
+    """OR error bits into the context's device error word (failure-path
+    testing); the next synchronising call reports them."""
+    _check(lib().hv_inject_error(ctx.handle, int(bits)))
+
+
+def hv_error_status(err_word: int) -> int:
+    """Status code a synchronising call returns for a device error word."""
+    return int(lib().hv_error_status(int(err_word)))
 
 
 def hv_profile(ctx: Ctx, enable: bool = True):
@@ -421,14 +431,30 @@ def hv_sort_keys(keys, nkeys: int, stream=None):
 def hv_sort_keys_noalloc(keys, nkeys: int, perm, counts=None, stream=None):
     """The allocation-free key sort: the caller supplies the output tensors
     (int32 CUDA perm [n] and optional counts [nkeys]); the library uses only
-    its static device scratch (n <= 1,048,576)."""
+    its static device scratch (n <= 1,048,576).  The C side cannot check
+    buffer sizes, so every tensor is checked here: contiguous int32 on one
+    CUDA device, perm with at least n and counts with at least nkeys
+    elements.  The call runs with that device current."""
     import torch
-    if keys.dtype != torch.int32 or not keys.is_cuda or perm.dtype != torch.int32:
-        raise TypeError("keys and perm must be int32 CUDA tensors")
+    named = [("keys", keys), ("perm", perm)] + ([("counts", counts)] if counts is not None else [])
+    for name, t in named:
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or not t.is_cuda:
+            raise TypeError(f"{name} must be an int32 CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if len({t.device for _, t in named}) != 1:
+        raise ValueError("keys, perm and counts must be on one device")
     n = keys.numel()
-    _check(lib().hv_sort_keys_noalloc(keys.data_ptr(), n, int(nkeys), perm.data_ptr(),
-                                      counts.data_ptr() if counts is not None else None,
-                                      _stream_handle(stream)))
+    if int(nkeys) < 1:
+        raise ValueError("nkeys must be >= 1")
+    if perm.numel() < n:
+        raise ValueError(f"perm has {perm.numel()} elements, fewer than the {n} keys")
+    if counts is not None and counts.numel() < int(nkeys):
+        raise ValueError(f"counts has {counts.numel()} elements, fewer than nkeys = {nkeys}")
+    with torch.cuda.device(keys.device):
+        _check(lib().hv_sort_keys_noalloc(keys.data_ptr(), n, int(nkeys), perm.data_ptr(),
+                                          counts.data_ptr() if counts is not None else None,
+                                          _stream_handle(stream)))
     return perm, counts
 
 

@@ -431,3 +431,73 @@ WORKLOADS = {
     "explosion2d": explosion2d,
     "ebeam2d": ebeam2d,
 }
+
+
+def harris_device(nx=512, ny=256, nz=256, ppc=32, dx=0.5, seed=3000, steps=1000, shape="qs",
+                  guide=0.1, sort_every=20, lam=1.0, nb=0.2, pert=0.1, dt=0.02, nsub=10,
+                  device="cuda", chunk=1 << 26) -> Workload:
+    """The Harris sheet of ``harris`` generated on the GPU with torch, for
+    sizes whose host generation would need more memory and time than the
+    run (the 3D sheet at 512x256x256 with 32 ppc is 1.07e9 ions, 34 GB of
+    FP32 particle data).  Same recipe: ions in cell order, every cell holds
+    ``ppc`` ions split between the two sheets and the background by the
+    local densities (sheet ions first), uniform relative coordinates,
+    drifting Maxwellian velocities and per-population weights; the random
+    numbers come from torch's seeded CUDA generator, so the arrays are not
+    bit-identical to ``harris`` with the same seed.  The B0 field is built on
+    the host exactly as in ``harris``.  Species arrays are CUDA tensors."""
+    import torch
+    p = base_params(nx, ny, nz, dx, dx, dx, dt, nsub, Te=1.0 / 12.0, eta=1e-3, eta_h=1e-4,
+                    n_floor=0.05, shape=shape, sort_every=sort_every)
+    Ti = 5.0 / 12.0
+    Lx, Lz = nx * dx, nz * dx
+    x, y, z = cell_centres(p)
+    Bx_z, ns1_z, ns2_z, _ = harris_profile(z, Lz, lam, nb)
+    wdt = 2.0 * lam
+    A0 = pert * wdt * math.exp(0.5)
+    X, Z = np.meshgrid(x, z)
+    Ay2 = A0 * np.exp(-((X - 0.5 * Lx) ** 2 + (Z - 0.75 * Lz) ** 2) / (2.0 * wdt ** 2))
+    Ay = np.broadcast_to(Ay2[:, None, :], (nz, ny, nx)).copy()
+    B = _curl_of_vector_potential(p, Ay=Ay)
+    B[0] += Bx_z[:, None, None]
+    B[1] += guide
+    n_tot = ns1_z + ns2_z + nb
+    c1 = np.floor(ppc * ns1_z / n_tot + 0.5).astype(np.int64)
+    c2 = np.floor(ppc * ns2_z / n_tot + 0.5).astype(np.int64)
+    cb = ppc - c1 - c2
+    vc = dx * p["dy"] * dx
+    w1 = ns1_z * vc / np.maximum(c1, 1)
+    w2 = ns2_z * vc / np.maximum(c2, 1)
+    wb = nb * vc / np.maximum(cb, 1)
+    dev = torch.device(device)
+    tc1 = torch.as_tensor(c1, device=dev)
+    tc2 = torch.as_tensor(c2, device=dev)
+    tw = torch.as_tensor(np.stack([w1, w2, wb]), dtype=torch.float32, device=dev)  # [3][nz]
+    ncell = nx * ny * nz
+    n = ncell * ppc
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty((3, n), dtype=torch.float32, device=dev)
+    v = torch.empty((3, n), dtype=torch.float32, device=dev)
+    w = torch.empty(n, dtype=torch.float32, device=dev)
+    U = 2.0 * Ti / lam
+    below1 = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        idx = torch.arange(a, b, device=dev, dtype=torch.int64)
+        c = idx // ppc
+        j = idx - c * ppc
+        k = c // (nx * ny)
+        pop = torch.where(j < tc1[k], 0, torch.where(j < tc1[k] + tc2[k], 1, 2))
+        cell[a:b] = c.to(torch.int32)
+        o = torch.rand((3, b - a), generator=gen, device=dev, dtype=torch.float32) * 2.0 - 1.0
+        off[:, a:b] = o.clamp_(max=below1)
+        vv = torch.randn((3, b - a), generator=gen, device=dev, dtype=torch.float32) * math.sqrt(Ti)
+        vv[1] += torch.where(pop == 0, U, torch.where(pop == 1, -U, 0.0)).to(torch.float32)
+        v[:, a:b] = vv
+        w[a:b] = tw[pop, k]
+    sp = SpeciesInput(1.0, 1.0, cell, off, v, w)
+    return Workload("harris3d", p, B.astype(np.float32), [sp], steps,
+                    notes=f"{nx}x{ny}x{nz} cells, {ppc} ppc, dx={dx}, guide={guide}, seed={seed}, "
+                          f"generated on the GPU")

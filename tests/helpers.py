@@ -39,3 +39,37 @@ def periodic_delta(p, a, b):
     L = np.array([p["nx"] * p["dx"], p["ny"] * p["dy"], p["nz"] * p["dz"]])[:, None]
     d = a - b
     return d - L * np.round(d / L)
+
+
+def check_diagnostics(p, d, sim, B_gpu):
+    """The FP64 diagnostics of a GPU step against the oracle's step.
+
+    * charge within 1e-6 and W_K within 1e-5 relative, W_B within 1e-6;
+    * each momentum component P_a = sum m w v_a: the GPU sums FP32 products
+      (Kahan-compensated per lane, FP64 across lanes), so its error is a few
+      FP32 roundings of the summed magnitudes; the bound is 1e-6 of
+      sum m w |v_a| (P itself may be near zero by symmetry);
+    * max |div B|: the GPU value must equal the oracle's centred divergence
+      (Eq. 12) of the GPU's own B to FP64 rounding, and differ from the
+      oracle's value by at most the divergence the FP32 difference of the two
+      B fields can carry, sum_a max|dB_a| / Delta_a (div is linear and its
+      stencil is (B[+1] - B[-1]) / (2 Delta))."""
+    od = sim.diags[-1]
+    assert abs(d["charge"] - od["charge"]) < 1e-6 * abs(od["charge"])
+    assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+    assert abs(d["W_B"] - od["W_B"]) < 1e-6 * od["W_B"]
+    absP = np.zeros(3)
+    for s in sim.species:
+        absP += np.sum(s.m * s.w * np.abs(s.v), axis=1)
+    for a in range(3):
+        assert abs(d["P"][a] - od["P"][a]) <= 1e-6 * absP[a], (a, d["P"][a], od["P"][a], absP[a])
+    B_gpu = np.asarray(B_gpu, np.float64).reshape(3, -1)
+    g = oracle_grid(p)
+    _, _, md_own = O.diag_grid(g, B_gpu, np.zeros(B_gpu.shape[1]))
+    assert abs(d["max_divB"] - md_own) <= 1e-9 * md_own + 1e-300, (d["max_divB"], md_own)
+    dl = (p["dx"], p["dy"], p["dz"])
+    nn = (p["nx"], p["ny"], p["nz"])
+    dB = np.abs(B_gpu - sim.B)
+    bound = sum(dB[a].max() / dl[a] for a in range(3) if nn[a] > 1)
+    assert abs(d["max_divB"] - od["max_divB"]) <= bound + 1e-12, (d["max_divB"], od["max_divB"],
+                                                                  bound)

@@ -86,3 +86,33 @@ def test_allocator_hooks_must_come_in_pairs():
     a = hv.ALLOC_FN(lambda n, s, u: None)
     assert L.hv_set_allocator(a, hv.FREE_FN(0), None) == hv.HV_EINVAL
     assert L.hv_set_allocator(hv.ALLOC_FN(0), hv.FREE_FN(0), None) == hv.HV_OK
+
+
+def test_error_word_maps_to_status_without_a_gpu():
+    """The device error word -> status mapping every synchronising call
+    uses (SURVEY's failure-detection codes), checked on the host: each bit
+    alone and the precedence when several are set."""
+    st = hv.hv_error_status
+    assert st(0) == hv.HV_OK
+    assert st(1) == hv.HV_ECFL
+    assert st(2) == hv.HV_ENAN
+    assert st(4) == hv.HV_ECUDA
+    assert st(8) == hv.HV_ETIMEOUT
+    assert "bounded device wait" in hv.hv_last_error()
+    assert st(8 | 1) == hv.HV_ECFL
+    assert st(8 | 2 | 1) == hv.HV_ENAN
+    assert st(8 | 4) == hv.HV_ECUDA
+
+
+def test_context_calls_reject_null_on_host():
+    L = hv.lib()
+    assert L.hv_inject_error(None, 8) == hv.HV_EINVAL
+    assert L.hv_get_tile_offsets(None, 0, None) == hv.HV_EINVAL
+
+
+def test_noalloc_binding_rejects_host_tensors():
+    torch = pytest.importorskip("torch")
+    keys = torch.zeros(8, dtype=torch.int32)
+    perm = torch.zeros(8, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        hv.hv_sort_keys_noalloc(keys, 4, perm)

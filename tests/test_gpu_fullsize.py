@@ -28,7 +28,7 @@ import numpy as np
 import pytest
 
 from paper_2305_05600_gb300 import inputs as I
-from tests.helpers import oracle_sim, periodic_delta, phys_pos
+from tests.helpers import check_diagnostics, oracle_sim, periodic_delta, phys_pos
 
 pytestmark = pytest.mark.gpu
 
@@ -163,9 +163,7 @@ def one_step_check(hvmod, wl, nsample=NSAMPLE, seed=2024):
     assert rel_l2(m["E"].reshape(3, -1)[:, clean_e], sim.E[:, clean_e]) < 1e-4
     qw = float(np.sum(w.astype(np.float64))) * s.q
     assert abs(d["charge"] - qw) < 1e-6 * qw
-    assert abs(d["charge"] - od["charge"]) < 1e-6 * od["charge"]
-    assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
-    assert abs(d["W_B"] - od["W_B"]) < 1e-6 * od["W_B"]
+    check_diagnostics(p, d, sim, m["B"])
     print(f"face-ambiguous ions {int(amb.sum())}, cells they can reach {taint.mean():.2e}")
 
     # the sampled ions, located on both sides by their marker weights

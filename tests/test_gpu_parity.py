@@ -16,7 +16,7 @@ import pytest
 
 import oracle as O
 from paper_2305_05600_gb300 import inputs as I
-from tests.helpers import oracle_sim, periodic_delta, phys_pos
+from tests.helpers import check_diagnostics, oracle_sim, periodic_delta, phys_pos
 
 pytestmark = pytest.mark.gpu
 
@@ -88,9 +88,10 @@ def small_workload(dim, shape):
 
 
 def order_of(hvmod, ctx, p):
-    """The library's ion order (supercell-major cells) as an oracle sort key."""
+    """The library's documented ion order (supercell-major cells, tile
+    extents from hv_query) as an oracle sort key."""
     tile = hvmod.hv_query(ctx)["tile"]
-    return lambda cell: hvmod.supercell_keys(cell, p, tile)
+    return lambda cell: O.supercell_keys(cell, p["nx"], p["ny"], p["nz"], tile)
 
 
 def compare_particles(p, gpu, sp, vscale):
@@ -105,9 +106,14 @@ def compare_particles(p, gpu, sp, vscale):
     d = periodic_delta(p, pg, po)
     dl = np.array([p["dx"], p["dy"], p["dz"]])[:, None]
     assert np.abs(d / dl).max() < 1e-5
-    dv = np.abs(gpu["v"][:, og].astype(np.float64) - sp.v[:, oo])
+    vg = gpu["v"][:, og].astype(np.float64)
+    dv = np.abs(vg - sp.v[:, oo])
     vmag = np.linalg.norm(sp.v[:, oo], axis=0)
+    # per ion relative to its speed plus the thermal scale (an FP32 push
+    # rounds at the scale of the kicks, not of a near-zero velocity) ...
     assert (dv.max(axis=0) <= 1e-5 * (vmag + vscale)).all(), dv.max()
+    # ... and 1e-5 relative L2 over the whole particle velocity state
+    assert rel_l2(vg, sp.v[:, oo]) < 1e-5
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -140,10 +146,8 @@ def test_one_step_parity(hvmod, dim, shape):
     # moments, so FP32 rounding is amplified; bound 1e-4 relative L2
     assert rel_l2(m1["E"].reshape(3, -1), sim.E) < 1e-4
     d = hvmod.hv_diag(ctx)
-    od = sim.diags[-1]
-    assert abs(d["charge"] - od["charge"]) < 1e-6 * od["charge"]
-    assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
-    assert abs(d["W_B"] - od["W_B"]) < 1e-6 * od["W_B"]
+    # charge, energies, momentum P and max |div B| against the oracle
+    check_diagnostics(p, d, sim, m1["B"])
     ctx.close()
 
 
@@ -155,7 +159,7 @@ def test_smoothing_parity(hvmod):
     sim.step(2, sort_every=1, key_fn=order_of(hvmod, ctx, wl.params))
     m = hvmod.hv_moments(ctx)
     assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
-    assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+    assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
     ctx.close()
 
 
@@ -177,12 +181,10 @@ def test_field_smoothing_parity(hvmod, dim, shape):
         compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
         m = hvmod.hv_moments(ctx)
         assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
-        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
         assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
         assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
-        d = hvmod.hv_diag(ctx)
-        od = sim.diags[-1]
-        assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+        check_diagnostics(p, hvmod.hv_diag(ctx), sim, m["B"])
     ctx.close()
 
 
@@ -269,9 +271,7 @@ def test_relativistic_beam_resistive_parity(hvmod, dim):
         assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
         assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
         assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
-        d = hvmod.hv_diag(ctx)
-        od = sim.diags[-1]
-        assert abs(d["W_K"] - od["W_K"]) < 1e-5 * od["W_K"]
+        check_diagnostics(p, hvmod.hv_diag(ctx), sim, m["B"])
     ctx.close()
 
 
@@ -299,7 +299,7 @@ def test_many_smoothing_passes_parity(hvmod):
         compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
         m = hvmod.hv_moments(ctx)
         assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
-        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 2e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
         assert rel_l2(m["B"].reshape(3, -1), sim.B) < 1e-6
     ctx.close()
 
@@ -331,22 +331,32 @@ def test_quasi_1d_and_multispecies(hvmod):
 # energy histories
 # ----------------------------------------------------------------------------
 
-def test_energy_history_1000_steps(hvmod):
-    """W_K and W_B histories over 1000 steps of the uniform Alfven-wave
-    plasma (32x32 cells, 16 ppc), GPU (FP32) against the oracle (FP64),
-    within 1e-3 relative."""
-    wl = I.alfven2d(nx=32, nz=32, ppc=16, dx=0.5, seed=5, sort_every=20)
+@pytest.mark.parametrize("case", ["alfven", "harris"])
+def test_energy_history_1000_steps(hvmod, case):
+    """W_K, W_B and charge histories over 1000 steps, GPU (FP32) against the
+    oracle (FP64), compared after every step within 1e-3 relative: the
+    uniform Alfven-wave plasma (32x32 cells, 16 ppc, sorted every 20 steps)
+    and the benchmark's Harris sheet on a reduced 48x24 grid at its 100 ppc
+    (115,200 ions, X-point perturbation, sorted every 4 steps as the
+    benchmark is)."""
+    if case == "alfven":
+        wl = I.alfven2d(nx=32, nz=32, ppc=16, dx=0.5, seed=5, sort_every=20)
+    else:
+        wl = I.harris(nx=48, nz=24, ppc=100, dx=0.25, seed=1000, sort_every=4)
+    p = wl.params
     ctx = hvmod.load_workload(wl)
     sim = oracle_sim(wl)
-    worst = {"W_K": 0.0, "W_B": 0.0}
-    for chunk in range(10):
-        hvmod.hv_step(ctx, 100)
-        sim.step(100, sort_every=20)
+    key = order_of(hvmod, ctx, p)
+    worst = {"W_K": 0.0, "W_B": 0.0, "charge": 0.0}
+    for _ in range(1000):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=p["sort_every"], key_fn=key)
         d = hvmod.hv_diag(ctx)
         od = sim.diags[-1]
-        for key in worst:
-            worst[key] = max(worst[key], abs(d[key] - od[key]) / abs(od[key]))
-    assert worst["W_K"] < 1e-3 and worst["W_B"] < 1e-3, worst
+        for k in worst:
+            worst[k] = max(worst[k], abs(d[k] - od[k]) / abs(od[k]))
+    print(case, "worst relative error over 1000 steps", worst)
+    assert all(v < 1e-3 for v in worst.values()), worst
     ctx.close()
 
 

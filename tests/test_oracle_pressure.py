@@ -2,7 +2,7 @@
 R16):  dp_e/dt = -gamma div(p_e u_e) + (gamma - 1) u_e . grad p_e
 + (gamma - 1) kappa lap(T_e),  u_e = -(curl B - J_i)/n_f,  T_e = p_e / n_f,
 advanced with B in explicit-midpoint subcycles; and of the electrostatic
-model (Sec. 3, Eq. esohm; reading R17): E = -grad p_e / n_f, B not advanced.
+model (Sec. 4, Eq. esohm; reading R17): E = -grad p_e / n_f, B not advanced.
 
 Closed forms on the cell-centred grid (centred differences, Eq. 12): the
 centred derivative of exp(i k x) is i sin(k dx)/dx exp(i k x) and the
@@ -134,7 +134,7 @@ def test_ohm_uses_the_pressure_field():
 
 
 # ----------------------------------------------------------------------------
-# electrostatic model (Sec. 3, Eq. esohm; reading R17)
+# electrostatic model (Sec. 4, Eq. esohm; reading R17)
 # ----------------------------------------------------------------------------
 
 def es_grid(pe_eq=1, nsub=4):
