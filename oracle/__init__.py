@@ -53,7 +53,8 @@ class Grid(ctypes.Structure):
                 ("smooth_passes", ctypes.c_int64), ("field_smooth_passes", ctypes.c_int64),
                 ("pe_eq", ctypes.c_int64), ("kappa", ctypes.c_double),
                 ("ohm_model", ctypes.c_int64), ("relativistic", ctypes.c_int64),
-                ("c_light", ctypes.c_double)]
+                ("c_light", ctypes.c_double), ("open", ctypes.c_int64 * 3),
+                ("B0", ctypes.c_void_p)]
 
 
 class _Species(ctypes.Structure):
@@ -110,6 +111,13 @@ def lib():
             L.hvo_filter_apply.argtypes = [P, P, P, D, D, ctypes.c_int, P, P]
             L.hvo_filter_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P, P]
             L.hvo_filter_loss_grad.restype = D
+            L.hvo_ohm_open.argtypes = [P, P, P, P, P]
+            L.hvo_field_advance_open.argtypes = [P, P, P, P]
+            L.hvo_push_deposit_open.argtypes = [P, P, I64, P, P, P, P, P]
+            L.hvo_init_open.argtypes = [P, P, I64, P, P, P, P]
+            L.hvo_step_open.argtypes = [P, P, I64, P, P, P, P, P, P, P]
+            L.hvo_xcount.argtypes = [P]
+            L.hvo_xcount.restype = I64
             L.hvo_set_threads.argtypes = [ctypes.c_int]
             L.hvo_get_threads.restype = ctypes.c_int
             L.hvo_max_threads.restype = ctypes.c_int
@@ -142,11 +150,22 @@ def _f64(a) -> np.ndarray:
 def make_grid(nx, ny, nz, dx, dy, dz, dt, nsub=1, Te=0.0, gamma_e=1.0, eta=0.0,
               eta_h=0.0, n_floor=0.0, shape="qs", smooth_passes=0,
               field_smooth_passes=0, pe_eq=0, kappa=0.0, ohm_model=0, relativistic=0,
-              c_light=0.0) -> Grid:
+              c_light=0.0, open_axes=(0, 0, 0), B0ext=None) -> Grid:
+    """Grid and physics parameters.  open_axes: 1 per axis with open faces
+    (Sec. 2.3).  B0ext: a fixed external field [3][ncell] (the B0 of the
+    B = B0 + B1 split, Sec. 2.3) or None; the grid keeps a reference."""
     s = SHAPES[shape] if isinstance(shape, str) else int(shape)
-    return Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
-                smooth_passes, field_smooth_passes, int(pe_eq), float(kappa), int(ohm_model),
-                int(relativistic), float(c_light))
+    g = Grid(nx, ny, nz, dx, dy, dz, dt, nsub, Te, gamma_e, eta, eta_h, n_floor, s,
+             smooth_passes, field_smooth_passes, int(pe_eq), float(kappa), int(ohm_model),
+             int(relativistic), float(c_light), (ctypes.c_int64 * 3)(*[int(a) for a in open_axes]),
+             None)
+    if B0ext is not None:
+        b0 = np.ascontiguousarray(np.asarray(B0ext, dtype=np.float64).reshape(3, -1))
+        if b0.shape[1] != nx * ny * nz:
+            raise ValueError("B0ext must have 3 * ncell values")
+        g._b0_keep = b0
+        g.B0 = b0.ctypes.data
+    return g
 
 
 def ncell(g: Grid) -> int:
@@ -433,15 +452,59 @@ def filter_loss_grad(g, params, scale, m, target, round_bf16=True):
     return loss, grad
 
 
+def xcount(g: Grid) -> int:
+    """Cells of the grid extended by one ghost cell beyond every open face."""
+    return int(lib().hvo_xcount(ctypes.byref(g)))
+
+
+def xshape(g: Grid):
+    """(Nz, Ny, Nx) of the extended grid."""
+    o = [int(a) for a in g.open]
+    return (g.nz + 2 * o[2], g.ny + 2 * o[1], g.nx + 2 * o[0])
+
+
+def ohm_open(g, B1, n, Ji):
+    """E on the extended grid (open faces) from interior B1, n, Ji."""
+    B1 = _f64(B1).reshape(3, -1)
+    n = _f64(n).reshape(-1)
+    Ji = _f64(Ji).reshape(3, -1)
+    E = np.zeros(3 * xcount(g))
+    lib().hvo_ohm_open(ctypes.byref(g), _p(B1), _p(n), _p(Ji), _p(E))
+    return E.reshape(3, -1)
+
+
+def field_advance_open(g, B1, n, Ji):
+    B1 = _f64(B1).reshape(3, -1).copy()
+    lib().hvo_field_advance_open(ctypes.byref(g), _p(B1), _p(_f64(n).reshape(-1)),
+                                 _p(_f64(Ji).reshape(3, -1)))
+    return B1
+
+
+def extended_interior(g, F):
+    """Interior cells [nc][ncell] of an extended field [nc][next]."""
+    F = np.asarray(F)
+    nc = F.shape[0]
+    Nz, Ny, Nx = xshape(g)
+    o = [int(a) for a in g.open]
+    G = F.reshape(nc, Nz, Ny, Nx)[:, o[2]:o[2] + g.nz, o[1]:o[1] + g.ny, o[0]:o[0] + g.nx]
+    return np.ascontiguousarray(G).reshape(nc, -1)
+
+
 class Sim:
     """Whole-state oracle simulation: species plus B, E and the previous
-    (half-step) moments, advanced by ``hvo_step``."""
+    (half-step) moments, advanced by ``hvo_step``.  B0 is the initial
+    (total) magnetic field; with an external field on the grid (B0ext of
+    make_grid) the advanced state ``B`` is B1 = B0 - B0ext and
+    ``B_total()`` adds the external part back."""
 
     def __init__(self, g: Grid, species, B0):
         self.g = g
         self.species = [s.copy() for s in species]
         nce = ncell(g)
         self.B = _f64(B0).reshape(3, nce).copy()
+        ext = getattr(g, "_b0_keep", None)
+        if ext is not None:
+            self.B -= ext
         self.E = np.zeros((3, nce))
         self.n_prev = np.zeros(nce)
         self.J_prev = np.zeros((3, nce))
@@ -451,12 +514,23 @@ class Sim:
         self.diags: list[dict] = []
         arr = _species_array(self.species)
         self.pe = np.zeros(nce) if g.pe_eq else None
-        if g.pe_eq:
+        self.open = any(int(a) for a in g.open)
+        if self.open:
+            # E lives on the grid extended by the ghost cells of open faces
+            self.Ex = np.zeros((3, xcount(g)))
+            lib().hvo_init_open(ctypes.byref(g), arr, len(self.species), _p(self.B),
+                                _p(self.Ex), _p(self.n_prev), _p(self.J_prev))
+            self.E = extended_interior(g, self.Ex)
+        elif g.pe_eq:
             lib().hvo_init_pe(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
                               _p(self.pe), _p(self.n_prev), _p(self.J_prev))
         else:
             lib().hvo_init(ctypes.byref(g), arr, len(self.species), _p(self.B), _p(self.E),
                            _p(self.n_prev), _p(self.J_prev))
+
+    def B_total(self) -> np.ndarray:
+        ext = getattr(self.g, "_b0_keep", None)
+        return self.B + ext if ext is not None else self.B
 
     def sort(self, key_fn=None):
         """Apply the stable counting sort to every species, by cell or by
@@ -476,7 +550,16 @@ class Sim:
                 self.sort(key_fn)
             arr = _species_array(self.species)
             d = Diag()
-            if self.pe is not None:
+            if self.open:
+                lib().hvo_step_open(ctypes.byref(self.g), arr, len(self.species), _p(self.B),
+                                    _p(self.Ex), _p(self.n_prev), _p(self.J_prev),
+                                    _p(self.n_ext), _p(self.J_ext), ctypes.byref(d))
+                self.E = extended_interior(self.g, self.Ex)
+                for k, s in enumerate(self.species):  # absorbed ions were compacted out
+                    m = int(arr[k].n)
+                    s.cell, s.w = s.cell[:m].copy(), s.w[:m].copy()
+                    s.off, s.v = s.off[:, :m].copy(), s.v[:, :m].copy()
+            elif self.pe is not None:
                 lib().hvo_step_pe(ctypes.byref(self.g), arr, len(self.species), _p(self.B),
                                   _p(self.E), _p(self.pe), _p(self.n_prev), _p(self.J_prev),
                                   _p(self.n_ext), _p(self.J_ext), ctypes.byref(d))

@@ -68,6 +68,22 @@
  *      n^{n+1/2}, J^{n+1/2} during the subcycle B^n -> B^{n+1}.
  *   R8 start-up: loaded velocities are v^{-1/2}; the previous moments are the
  *      deposit at x^0; E^0 = Ohm(B^0, those moments).
+ *   R20 the optional split B = B0 + B1 (Sec. 2.3): B0 is a fixed external
+ *      field given on the cells; only B1 is advanced by Faraday's law; the
+ *      current in Ohm's law (Hall, resistive and hyper-resistive terms) is
+ *      J = curl B1, the cross products with B and the push use the total
+ *      B0 + B1; W_B is taken of the total field and max |div B| of B1 (the
+ *      advanced part, whose discrete divergence Faraday's law keeps).
+ *   R21 open faces (Sec. 2.3): the part of an ion's shape that falls beyond
+ *      an open face is deposited in the interior cell next to the face, so
+ *      the deposited charge stays the sum of q w over the ions inside.
+ *   R22 open faces: one ghost cell beyond each open face; B1, B0 and the
+ *      moments there equal those of the interior neighbour; J, lap J,
+ *      grad p_e and so E are evaluated in the ghost cell with derivatives
+ *      normal to the face set to zero; an ion ending a step beyond an open
+ *      face is removed.
+ *   R23 open faces are built for the hybrid Ohm's law with the equation of
+ *      state and without smoothing.
  *   R9 an axis with one cell (2D runs use ny = 1) is periodic with period one
  *      cell, so shapes fold onto the same cell and centred differences along
  *      it vanish.  Offsets along such an axis are never moved.
@@ -118,6 +134,8 @@ typedef struct {
                                    2 resistive background (R18) */
   int64_t relativistic;         /* R19: relativistic Boris push */
   double c_light;               /* R19: speed of light */
+  int64_t open[3];              /* R22: 1 = the axis has open faces (Sec. 2.3) */
+  const double *B0;             /* R20: fixed external field [3][ncell] or NULL */
 } hvo_grid;
 
 typedef struct {
@@ -488,7 +506,9 @@ void hvo_lap(const hvo_grid *g, const double *A, int64_t nc, double *out) {
  * (Eq. 3), J = curl B (Eq. 4, mu_0 = 1), p_e = Te n^gamma (Eq. 6, p_0 = n_0
  * Te, n_0 = 1) and the density floor n_f = max(n, n_floor) (Sec. 2.1):
  *   E = -grad p_e / n_f - (J_i / n_f) x B + (J x B) / n_f + eta J - eta_H lap J
- * Inputs: B [3][ncell], n [ncell], Ji [3][ncell]; output E [3][ncell]. */
+ * Inputs: B [3][ncell], n [ncell], Ji [3][ncell]; output E [3][ncell].
+ * With an external field (R20) B is B1: J = curl B1 and the cross products
+ * take B0 + B1. */
 static void ohm_with(const hvo_grid *g, const double *B, const double *n, const double *Ji,
                      const double *pe_field, double *E) {
   int64_t nce = ncell_of(g);
@@ -517,6 +537,8 @@ static void ohm_with(const hvo_grid *g, const double *B, const double *n, const 
       continue;
     }
     double b[3] = {B[c], B[nce + c], B[2 * nce + c]};
+    if (g->B0) /* R20: B holds B1; the cross products take B0 + B1 */
+      for (int a = 0; a < 3; ++a) b[a] += g->B0[a * nce + c];
     double jt[3] = {J[c], J[nce + c], J[2 * nce + c]};
     double ui[3] = {Ji[c] / nf[c], Ji[nce + c] / nf[c], Ji[2 * nce + c] / nf[c]};
     double uixb[3] = {ui[1] * b[2] - ui[2] * b[1], ui[2] * b[0] - ui[0] * b[2], ui[0] * b[1] - ui[1] * b[0]};
@@ -736,18 +758,26 @@ static void step_impl(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B
   double *ne = (double *)malloc(sizeof(double) * nce);
   double *Je = (double *)malloc(sizeof(double) * 3 * nce);
   double kin[4];
+  /* the ions feel the total field: B0 + B1 with an external field (R20) */
+  double *Bt = NULL;
+  const double *Bg = B;
+  if (g->B0) {
+    Bt = (double *)malloc(sizeof(double) * 3 * nce);
+    for (int64_t c = 0; c < 3 * nce; ++c) Bt[c] = B[c] + g->B0[c];
+    Bg = Bt;
+  }
   if (g->field_smooth_passes > 0) {
     double *Eg = (double *)malloc(sizeof(double) * 3 * nce);
-    double *Bg = (double *)malloc(sizeof(double) * 3 * nce);
+    double *Bs = (double *)malloc(sizeof(double) * 3 * nce);
     memcpy(Eg, E, sizeof(double) * 3 * nce);
-    memcpy(Bg, B, sizeof(double) * 3 * nce);
+    memcpy(Bs, Bg, sizeof(double) * 3 * nce);
     hvo_smooth(g, Eg, 3, g->field_smooth_passes);
-    hvo_smooth(g, Bg, 3, g->field_smooth_passes);
-    hvo_push_deposit(g, sp, nsp, Eg, Bg, nh, Jh, kin);
+    hvo_smooth(g, Bs, 3, g->field_smooth_passes);
+    hvo_push_deposit(g, sp, nsp, Eg, Bs, nh, Jh, kin);
     free(Eg);
-    free(Bg);
+    free(Bs);
   } else {
-    hvo_push_deposit(g, sp, nsp, E, B, nh, Jh, kin);
+    hvo_push_deposit(g, sp, nsp, E, Bg, nh, Jh, kin);
   }
   double charge_raw = 0.0, vc = g->dx * g->dy * g->dz;
   for (int64_t c = 0; c < nce; ++c) charge_raw += nh[c] * vc;
@@ -769,6 +799,12 @@ static void step_impl(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B
   if (dg) {
     double wb, ch, md;
     hvo_diag_grid(g, B, nh, &wb, &ch, &md);
+    if (Bt) { /* R20: W_B of the total field, max |div B| of B1 */
+      double md1 = md;
+      for (int64_t c = 0; c < 3 * nce; ++c) Bt[c] = B[c] + g->B0[c];
+      hvo_diag_grid(g, Bt, nh, &wb, &ch, &md);
+      md = md1;
+    }
     dg->W_K = kin[0];
     dg->P[0] = kin[1];
     dg->P[1] = kin[2];
@@ -777,6 +813,7 @@ static void step_impl(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B
     dg->W_B = wb;
     dg->max_divB = md;
   }
+  free(Bt);
   free(nh);
   free(Jh);
   free(ne);
@@ -813,6 +850,394 @@ int hvo_sort_stable(const int64_t *key, int64_t n, int64_t nkeys, int64_t *perm,
   for (int64_t p = 0; p < n; ++p) perm[next[key[p]]++] = p;
   free(next);
   return 0;
+}
+
+/* ======================================================================== */
+/* Open boundaries (Sec. 2.3; readings R21-R23).                            */
+/*                                                                          */
+/* An axis with open faces carries one ghost cell beyond each face (the     */
+/* paper's single ghost layer).  In a ghost cell                            */
+/*  - B1, B0 and the moments n, J_i equal those of the interior cell next   */
+/*    to it (no normal gradient, Sec. 2.3), and                             */
+/*  - the derived quantities of Ohm's law (J = curl B1, lap J, grad p_e and */
+/*    so E) are evaluated with every derivative normal to that face set to  */
+/*    zero, the tangential ones kept (Sec. 2.3: no normal gradients in the  */
+/*    ghost-cell Ohm's law).                                                */
+/* Interior cells next to a face take their centred differences across it   */
+/* from the ghost values.  Faraday's law advances the interior B1 only.     */
+/* The part of a deposit that falls beyond an open face is added to the     */
+/* interior cell next to it (R21), and an ion that ends a step beyond an    */
+/* open face leaves the simulation (absorbed, Sec. 2.3).  Periodic axes     */
+/* wrap as before.  These routines cover the hybrid Ohm's law with the      */
+/* equation of state, without smoothing (R23).                              */
+/* ======================================================================== */
+
+typedef struct {
+  int64_t n[3]; /* interior cells per axis */
+  int64_t o[3]; /* ghost cells per side: 1 on an open axis, 0 on a periodic one */
+  int64_t N[3]; /* extended extent n + 2 o */
+  double d[3];  /* cell sizes */
+} xgrid;
+
+static xgrid xgrid_of(const hvo_grid *g) {
+  xgrid x;
+  int64_t n[3] = {g->nx, g->ny, g->nz};
+  double d[3] = {g->dx, g->dy, g->dz};
+  for (int a = 0; a < 3; ++a) {
+    x.n[a] = n[a];
+    x.o[a] = g->open[a] ? 1 : 0;
+    x.N[a] = n[a] + 2 * x.o[a];
+    x.d[a] = d[a];
+  }
+  return x;
+}
+
+static int64_t xcount(const xgrid *x) { return x->N[0] * x->N[1] * x->N[2]; }
+
+/* coordinate along axis a as an extended-grid position: shifted by the ghost
+ * width on an open axis (the caller keeps it within the ghost layer),
+ * wrapped on a periodic one */
+static int64_t xcoord(const xgrid *x, int a, int64_t c) {
+  return x->o[a] ? c + x->o[a] : wrapi(c, x->n[a]);
+}
+
+static int64_t xidx(const xgrid *x, int64_t i, int64_t j, int64_t k) {
+  return xcoord(x, 0, i) + x->N[0] * (xcoord(x, 1, j) + x->N[1] * xcoord(x, 2, k));
+}
+
+/* interior coordinates of extended cell e */
+static void xdecode(const xgrid *x, int64_t e, int64_t *c) {
+  int64_t r = e;
+  for (int a = 0; a < 3; ++a) {
+    c[a] = r % x->N[a] - x->o[a];
+    r /= x->N[a];
+  }
+}
+
+/* interior cell nearest to (i, j, k): clamped on open axes, wrapped on
+ * periodic ones (the ghost-cell copy rule and the deposit fold, R21) */
+static int64_t cidx_near(const hvo_grid *g, const xgrid *x, int64_t i, int64_t j, int64_t k) {
+  int64_t c[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (x->o[a]) c[a] = c[a] < 0 ? 0 : (c[a] >= x->n[a] ? x->n[a] - 1 : c[a]);
+    else c[a] = wrapi(c[a], x->n[a]);
+  }
+  return c[0] + g->nx * (c[1] + g->ny * c[2]);
+}
+
+static int xghost(const xgrid *x, int a, int64_t c) { return x->o[a] && (c < 0 || c >= x->n[a]); }
+
+/* extended copy of nc interior fields (ghost = nearest interior cell) */
+static void xfill(const hvo_grid *g, const xgrid *x, const double *src, int64_t nc, double *dst) {
+  int64_t nce = ncell_of(g), ne = xcount(x);
+  for (int64_t e = 0; e < ne; ++e) {
+    int64_t c[3];
+    xdecode(x, e, c);
+    int64_t s = cidx_near(g, x, c[0], c[1], c[2]);
+    for (int64_t m = 0; m < nc; ++m) dst[m * ne + e] = src[m * nce + s];
+  }
+}
+
+/* centred derivative along axis a of extended field f at extended cell with
+ * interior coordinates c: zero in a cell that is a ghost along a (no normal
+ * gradient there), a centred difference otherwise */
+static double xd(const xgrid *x, const double *f, int a, const int64_t *c) {
+  if (xghost(x, a, c[a])) return 0.0;
+  int64_t p[3] = {c[0], c[1], c[2]}, m[3] = {c[0], c[1], c[2]};
+  p[a] += 1;
+  m[a] -= 1;
+  return (f[xidx(x, p[0], p[1], p[2])] - f[xidx(x, m[0], m[1], m[2])]) / (2.0 * x->d[a]);
+}
+
+static double xd2(const xgrid *x, const double *f, int a, const int64_t *c) {
+  if (xghost(x, a, c[a])) return 0.0;
+  int64_t p[3] = {c[0], c[1], c[2]}, m[3] = {c[0], c[1], c[2]};
+  p[a] += 1;
+  m[a] -= 1;
+  return (f[xidx(x, p[0], p[1], p[2])] - 2.0 * f[xidx(x, c[0], c[1], c[2])] +
+          f[xidx(x, m[0], m[1], m[2])]) / (x->d[a] * x->d[a]);
+}
+
+/* Ohm's law (Eq. 2, as ohm_with) on every extended cell from extended B1,
+ * the external field (extended, or NULL), moments and their floor. */
+static void xohm(const hvo_grid *g, const xgrid *x, const double *B1, const double *B0,
+                 const double *n, const double *Ji, double *E) {
+  int64_t ne = xcount(x);
+  double *J = (double *)malloc(sizeof(double) * 3 * ne);
+  double *pe = (double *)malloc(sizeof(double) * ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    int64_t c[3];
+    xdecode(x, e, c);
+    J[e] = xd(x, B1 + 2 * ne, 1, c) - xd(x, B1 + ne, 2, c);
+    J[ne + e] = xd(x, B1, 2, c) - xd(x, B1 + 2 * ne, 0, c);
+    J[2 * ne + e] = xd(x, B1 + ne, 0, c) - xd(x, B1, 1, c);
+    double nf = n[e] > g->n_floor ? n[e] : g->n_floor;
+    pe[e] = g->Te * pow(nf, g->gamma_e);
+  }
+  for (int64_t e = 0; e < ne; ++e) {
+    int64_t c[3];
+    xdecode(x, e, c);
+    double nf = n[e] > g->n_floor ? n[e] : g->n_floor;
+    double b[3], jt[3], ui[3], lj[3], gp[3];
+    for (int a = 0; a < 3; ++a) {
+      b[a] = B1[a * ne + e] + (B0 ? B0[a * ne + e] : 0.0);
+      jt[a] = J[a * ne + e];
+      ui[a] = Ji[a * ne + e] / nf;
+      lj[a] = xd2(x, J + a * ne, 0, c) + xd2(x, J + a * ne, 1, c) + xd2(x, J + a * ne, 2, c);
+      gp[a] = xd(x, pe, a, c);
+    }
+    double uixb[3] = {ui[1] * b[2] - ui[2] * b[1], ui[2] * b[0] - ui[0] * b[2], ui[0] * b[1] - ui[1] * b[0]};
+    double jxb[3] = {jt[1] * b[2] - jt[2] * b[1], jt[2] * b[0] - jt[0] * b[2], jt[0] * b[1] - jt[1] * b[0]};
+    for (int a = 0; a < 3; ++a)
+      E[a * ne + e] = -gp[a] / nf - uixb[a] + jxb[a] / nf + g->eta * jt[a] - g->eta_h * lj[a];
+  }
+  free(J);
+  free(pe);
+}
+
+/* E on the extended grid from interior B1 [3][ncell], n, Ji; Eext [3][next] */
+void hvo_ohm_open(const hvo_grid *g, const double *B1, const double *n, const double *Ji,
+                  double *Eext) {
+  xgrid x = xgrid_of(g);
+  int64_t ne = xcount(&x);
+  double *Bx = (double *)malloc(sizeof(double) * 3 * ne);
+  double *B0x = g->B0 ? (double *)malloc(sizeof(double) * 3 * ne) : NULL;
+  double *nx = (double *)malloc(sizeof(double) * ne);
+  double *Jx = (double *)malloc(sizeof(double) * 3 * ne);
+  xfill(g, &x, B1, 3, Bx);
+  if (B0x) xfill(g, &x, g->B0, 3, B0x);
+  xfill(g, &x, n, 1, nx);
+  xfill(g, &x, Ji, 3, Jx);
+  xohm(g, &x, Bx, B0x, nx, Jx, Eext);
+  free(Bx);
+  free(B0x);
+  free(nx);
+  free(Jx);
+}
+
+/* curl of extended E at the interior cells, out [3][ncell] */
+static void xcurl_interior(const hvo_grid *g, const xgrid *x, const double *E, double *out) {
+  int64_t nce = ncell_of(g), ne = xcount(x);
+  for (int64_t q = 0; q < nce; ++q) {
+    int64_t c[3];
+    cdecode(g, q, &c[0], &c[1], &c[2]);
+    out[q] = xd(x, E + 2 * ne, 1, c) - xd(x, E + ne, 2, c);
+    out[nce + q] = xd(x, E, 2, c) - xd(x, E + 2 * ne, 0, c);
+    out[2 * nce + q] = xd(x, E + ne, 0, c) - xd(x, E, 1, c);
+  }
+}
+
+/* The subcycled Faraday advance of B1 (as hvo_field_advance, reading R7)
+ * with the open-boundary Ohm's law. */
+void hvo_field_advance_open(const hvo_grid *g, double *B1, const double *n, const double *Ji) {
+  xgrid x = xgrid_of(g);
+  int64_t nce = ncell_of(g), ne = xcount(&x);
+  double h = g->dt / (double)g->nsub;
+  double *E = (double *)malloc(sizeof(double) * 3 * ne);
+  double *cE = (double *)malloc(sizeof(double) * 3 * nce);
+  double *Bs = (double *)malloc(sizeof(double) * 3 * nce);
+  for (int64_t s = 0; s < g->nsub; ++s) {
+    hvo_ohm_open(g, B1, n, Ji, E);
+    xcurl_interior(g, &x, E, cE);
+    for (int64_t c = 0; c < 3 * nce; ++c) Bs[c] = B1[c] - 0.5 * h * cE[c];
+    hvo_ohm_open(g, Bs, n, Ji, E);
+    xcurl_interior(g, &x, E, cE);
+    for (int64_t c = 0; c < 3 * nce; ++c) B1[c] = B1[c] - h * cE[c];
+  }
+  free(E);
+  free(cE);
+  free(Bs);
+}
+
+/* A move without the wrap on open axes: raw cell coordinates c[3] (which may
+ * leave [0, n) on an open axis), offsets d updated; periodic axes wrap. */
+static void move_raw(const hvo_grid *g, const xgrid *x, int64_t *c, double *d, const double *v,
+                     double frac) {
+  for (int a = 0; a < 3; ++a) {
+    if (x->n[a] == 1) continue;
+    double y = d[a] + 2.0 * v[a] * frac * g->dt / x->d[a];
+    double m = floor((y + 1.0) / 2.0);
+    y -= 2.0 * m;
+    if (y >= 1.0) { y -= 2.0; m += 1.0; }
+    if (y < -1.0) { y += 2.0; m -= 1.0; }
+    d[a] = y;
+    c[a] += (int64_t)m;
+    if (!x->o[a]) c[a] = wrapi(c[a], x->n[a]);
+  }
+}
+
+/* gather of extended fields at a particle in interior cell c with offsets d:
+ * shape targets one cell beyond a face read the ghost cell */
+static void xgather(const hvo_grid *g, const xgrid *x, const double *F, int64_t nc, const int64_t *c,
+                    const double *d, double *out) {
+  int32_t si[8], sj[8], sk[8];
+  double wt[8];
+  int64_t ne = xcount(x);
+  int nt = hvo_shape(g->shape, d[0], d[1], d[2], si, sj, sk, wt);
+  for (int64_t m = 0; m < nc; ++m) out[m] = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    int64_t e = xidx(x, c[0] + si[t], c[1] + sj[t], c[2] + sk[t]);
+    for (int64_t m = 0; m < nc; ++m) out[m] += wt[t] * F[m * ne + e];
+  }
+}
+
+/* deposit at raw position (c, d): targets beyond an open face fold onto the
+ * interior cell next to it (R21) */
+static void deposit_near(const hvo_grid *g, const xgrid *x, const int64_t *c, const double *d,
+                         const double *v, double qw, double *n, double *J) {
+  int32_t si[8], sj[8], sk[8];
+  double wt[8];
+  int64_t nce = ncell_of(g);
+  double vc = g->dx * g->dy * g->dz;
+  int nt = hvo_shape(g->shape, d[0], d[1], d[2], si, sj, sk, wt);
+  for (int t = 0; t < nt; ++t) {
+    int64_t q = cidx_near(g, x, c[0] + si[t], c[1] + sj[t], c[2] + sk[t]);
+    double s = qw * wt[t] / vc;
+    n[q] += s;
+    J[q] += s * v[0];
+    J[nce + q] += s * v[1];
+    J[2 * nce + q] += s * v[2];
+  }
+}
+
+static int outside(const xgrid *x, const int64_t *c) {
+  for (int a = 0; a < 3; ++a)
+    if (xghost(x, a, c[a])) return 1;
+  return 0;
+}
+
+/* The particle part of a step with open faces: every ion gathers E and the
+ * total B at x^n from the extended fields (Eext, Btx), is pushed (Boris,
+ * non-relativistic), deposits at its half-step position (folded, R21) and
+ * moves; an ion whose new cell lies beyond an open face is absorbed.  The
+ * survivors are compacted in order; sp[s].n is updated.  kin as in
+ * hvo_push_deposit (absorbed ions included: they were pushed). */
+void hvo_push_deposit_open(const hvo_grid *g, hvo_species *sp, int64_t nsp, const double *Eext,
+                           const double *Btx, double *n_acc, double *J_acc, double *kin) {
+  xgrid x = xgrid_of(g);
+  for (int a = 0; a < 4; ++a) kin[a] = 0.0;
+  for (int64_t s = 0; s < nsp; ++s) {
+    double qmdt = sp[s].q / sp[s].m * g->dt;
+    int64_t kept = 0;
+    for (int64_t p = 0; p < sp[s].n; ++p) {
+      int64_t c[3];
+      cdecode(g, sp[s].cell[p], &c[0], &c[1], &c[2]);
+      double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
+      double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
+      double Ep[3], Bp[3];
+      xgather(g, &x, Eext, 3, c, d, Ep);
+      xgather(g, &x, Btx, 3, c, d, Bp);
+      hvo_boris(qmdt, Ep, Bp, v);
+      int64_t ch[3] = {c[0], c[1], c[2]};
+      double dh[3] = {d[0], d[1], d[2]};
+      move_raw(g, &x, ch, dh, v, 0.5);
+      deposit_near(g, &x, ch, dh, v, sp[s].q * sp[s].w[p], n_acc, J_acc);
+      move_raw(g, &x, c, d, v, 1.0);
+      double mw = sp[s].m * sp[s].w[p];
+      kin[0] += 0.5 * mw * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      kin[1] += mw * v[0];
+      kin[2] += mw * v[1];
+      kin[3] += mw * v[2];
+      if (outside(&x, c)) continue; /* absorbed at an open face */
+      sp[s].cell[kept] = c[0] + g->nx * (c[1] + g->ny * c[2]);
+      sp[s].ox[kept] = d[0];
+      sp[s].oy[kept] = d[1];
+      sp[s].oz[kept] = d[2];
+      sp[s].vx[kept] = v[0];
+      sp[s].vy[kept] = v[1];
+      sp[s].vz[kept] = v[2];
+      sp[s].w[kept] = sp[s].w[p];
+      ++kept;
+    }
+    sp[s].n = kept;
+  }
+}
+
+/* Start-up with open faces (R8): deposit at x^0 (folded), E^0 on the
+ * extended grid. */
+void hvo_init_open(const hvo_grid *g, const hvo_species *sp, int64_t nsp, const double *B1,
+                   double *Eext, double *n_prev, double *J_prev) {
+  xgrid x = xgrid_of(g);
+  int64_t nce = ncell_of(g);
+  memset(n_prev, 0, sizeof(double) * nce);
+  memset(J_prev, 0, sizeof(double) * 3 * nce);
+  for (int64_t s = 0; s < nsp; ++s)
+    for (int64_t p = 0; p < sp[s].n; ++p) {
+      int64_t c[3];
+      cdecode(g, sp[s].cell[p], &c[0], &c[1], &c[2]);
+      double d[3] = {sp[s].ox[p], sp[s].oy[p], sp[s].oz[p]};
+      double v[3] = {sp[s].vx[p], sp[s].vy[p], sp[s].vz[p]};
+      deposit_near(g, &x, c, d, v, sp[s].q * sp[s].w[p], n_prev, J_prev);
+    }
+  hvo_ohm_open(g, B1, n_prev, J_prev, Eext);
+}
+
+/* One step with open faces, in the order of step_impl: push + half-step
+ * deposit (absorbing), extrapolation (Eq. 11), subcycled advance of B1 with
+ * the half-step moments, E^{n+1} on the extended grid from the extrapolated
+ * moments.  Diagnostics: W_B of the total interior field, the deposited
+ * charge, max |div B1| over interior cells (ghosts by the copy rule). */
+void hvo_step_open(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B1, double *Eext,
+                   double *n_prev, double *J_prev, double *n_ext, double *J_ext, hvo_diag *dg) {
+  xgrid x = xgrid_of(g);
+  int64_t nce = ncell_of(g), ne = xcount(&x);
+  double *nh = (double *)calloc((size_t)nce, sizeof(double));
+  double *Jh = (double *)calloc((size_t)(3 * nce), sizeof(double));
+  double *ne_ = (double *)malloc(sizeof(double) * nce);
+  double *Je = (double *)malloc(sizeof(double) * 3 * nce);
+  double *Bt = (double *)malloc(sizeof(double) * 3 * nce);
+  double *Btx = (double *)malloc(sizeof(double) * 3 * ne);
+  double kin[4];
+  for (int64_t c = 0; c < 3 * nce; ++c) Bt[c] = B1[c] + (g->B0 ? g->B0[c] : 0.0);
+  xfill(g, &x, Bt, 3, Btx);
+  hvo_push_deposit_open(g, sp, nsp, Eext, Btx, nh, Jh, kin);
+  double charge_raw = 0.0, vc = g->dx * g->dy * g->dz;
+  for (int64_t c = 0; c < nce; ++c) charge_raw += nh[c] * vc;
+  hvo_extrapolate(nce, nh, n_prev, ne_);
+  hvo_extrapolate(3 * nce, Jh, J_prev, Je);
+  hvo_field_advance_open(g, B1, nh, Jh);
+  hvo_ohm_open(g, B1, ne_, Je, Eext);
+  memcpy(n_prev, nh, sizeof(double) * nce);
+  memcpy(J_prev, Jh, sizeof(double) * 3 * nce);
+  if (n_ext) memcpy(n_ext, ne_, sizeof(double) * nce);
+  if (J_ext) memcpy(J_ext, Je, sizeof(double) * 3 * nce);
+  if (dg) {
+    double wb = 0.0, md = 0.0;
+    double *B1x = (double *)malloc(sizeof(double) * 3 * ne);
+    xfill(g, &x, B1, 3, B1x);
+    for (int64_t q = 0; q < nce; ++q) {
+      double bt2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double b = B1[a * nce + q] + (g->B0 ? g->B0[a * nce + q] : 0.0);
+        bt2 += b * b;
+      }
+      wb += 0.5 * bt2 * vc;
+      int64_t c[3];
+      cdecode(g, q, &c[0], &c[1], &c[2]);
+      double dv = xd(&x, B1x, 0, c) + xd(&x, B1x + ne, 1, c) + xd(&x, B1x + 2 * ne, 2, c);
+      if (fabs(dv) > md) md = fabs(dv);
+    }
+    free(B1x);
+    dg->W_K = kin[0];
+    dg->P[0] = kin[1];
+    dg->P[1] = kin[2];
+    dg->P[2] = kin[3];
+    dg->charge = charge_raw;
+    dg->W_B = wb;
+    dg->max_divB = md;
+  }
+  free(nh);
+  free(Jh);
+  free(ne_);
+  free(Je);
+  free(Bt);
+  free(Btx);
+}
+
+/* Number of cells of the extended grid (for the caller's Eext). */
+int64_t hvo_xcount(const hvo_grid *g) {
+  xgrid x = xgrid_of(g);
+  return xcount(&x);
 }
 
 /* ------------------------------------------------------------------------ */
