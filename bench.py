@@ -75,10 +75,10 @@ def make_workload(name, shape, seed_offset=0):
         return I.beam3d(shape=shape, seed=2000 + seed_offset)
     if name == "beam3d_2ppc":  # the beam grid with 1 core + 1 beam ion per cell (field kernels)
         return I.beam3d(n_core=1, n_beam=1, shape=shape, seed=2000 + seed_offset)
-    if name == "harris3d":  # 512x256x256 cells, 32 ppc, 1.07e9 ions (slow to generate)
-        return I.harris3d(shape=shape, seed=3000 + seed_offset)
-    if name == "harris3d_quarter":  # 256x128x128 cells, 32 ppc, 134M ions
-        return I.harris3d(nx=256, ny=128, nz=128, shape=shape, seed=3000 + seed_offset)
+    if name == "harris3d":  # 512x256x256 cells, 32 ppc, 1.07e9 ions, generated on the GPU
+        return I.harris_device(shape=shape, seed=3000 + seed_offset)
+    if name == "harris3d_quarter":  # 256x128x128 cells, 32 ppc, 134M ions, generated on the GPU
+        return I.harris_device(nx=256, ny=128, nz=128, shape=shape, seed=3000 + seed_offset)
     if name == "ebeam2d":  # relativistic electron beam, resistive background, 640x320, 13.1M
         return I.ebeam2d(shape=shape, seed=8000 + seed_offset)
     raise ValueError(name)
@@ -271,6 +271,12 @@ def oracle_strip_rate(wl, rows: int, steps: int, threads: int = 1):
         O.set_threads(1)
 
 
+def _host(a):
+    """numpy copy of a species array (from the GPU for device-generated
+    workloads)."""
+    return a.cpu().numpy() if hasattr(a, "cpu") else a
+
+
 def _strip_rate(O, wl, rows, steps):
     p = dict(wl.params)
     nx, nz = p["nx"], p["nz"]
@@ -278,8 +284,8 @@ def _strip_rate(O, wl, rows, steps):
     s = wl.species[0]
     k = s.cell // (nx * p["ny"])
     sel = (k >= k0) & (k < k0 + rows)
-    cell = (s.cell[sel] - k0 * nx * p["ny"]).astype(np.int64)
-    sp = O.Species(s.q, s.m, cell, s.off[:, sel], s.v[:, sel], s.w[sel])
+    cell = _host(s.cell[sel]).astype(np.int64) - k0 * nx * p["ny"]
+    sp = O.Species(s.q, s.m, cell, _host(s.off[:, sel]), _host(s.v[:, sel]), _host(s.w[sel]))
     B = wl.B0[:, k0:k0 + rows].astype(np.float64).reshape(3, -1)
     g = O.make_grid(nx, p["ny"], rows, p["dx"], p["dy"], p["dz"], p["dt"], p["nsub"], p["Te"],
                     p["gamma_e"], p["eta"], p["eta_h"], p["n_floor"], p["shape"],
@@ -444,6 +450,10 @@ def run_e2e(args, wl, world, dev, stream):
     import torch
 
     from paper_2305_05600_gb300 import hv
+
+    if any(hasattr(s.cell, "is_cuda") for s in wl.species):
+        return {"value": None, "unit": UNIT,
+                "skipped": "workload generated on the GPU (no host copy of its ions)"}
 
     def pinned(a):
         t = torch.empty(a.shape, dtype={np.float32: torch.float32,

@@ -108,8 +108,9 @@ typedef struct {
                         m w (gamma - 1) c^2) */
   double P[3];       /* sum over ions of m w v^{n+1/2} (relativistic: m w u) */
   double charge;     /* sum over cells of n^{n+1/2} V_c (= sum q w) */
-  double W_B;        /* sum over cells of 1/2 |B^{n+1}|^2 V_c */
-  double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12) */
+  double W_B;        /* sum over cells of 1/2 |B^{n+1}|^2 V_c (total field) */
+  double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12;
+                        of B1 when an external field is set) */
   int32_t err_word;  /* device error bits: 1 CFL, 2 non-finite particle,
                         4 corrupt cell index, 8 bounded wait gave up */
   int32_t pad;
@@ -161,6 +162,18 @@ hv_status hv_set_allocator(hv_alloc_fn alloc, hv_free_fn free_fn, void *user);
  * device state. */
 hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stream,
                        hv_ctx **out);
+
+/* Split the magnetic field as B = B0 + B1 (Sec. 2.3): B0_host [3][nz][ny][nx]
+ * (host memory) is a fixed external field, for example the vacuum field of
+ * coils or of a planet.  The field given to hv_init_grid stays the initial
+ * total field; from this call on the library advances only B1 = B - B0 with
+ * Faraday's law and takes the current in Ohm's law (Hall, resistive and
+ * hyper-resistive terms) from J = curl B1, while the cross products of Ohm's
+ * law and the push use the total field.  hv_moments reports the total
+ * field; hv_diag reports W_B of the total field and max |div B1|.  Only
+ * before the first step and once per context (HV_ESTATE otherwise);
+ * HV_EINVAL for a non-finite value.  Synchronises. */
+hv_status hv_set_external_field(hv_ctx *ctx, const float *B0_host);
 
 /* Append ion species number `species` (must equal the number of species
  * already loaded; up to 8) with charge q and mass m (q_s = Z_s e, m_s; Sec.

@@ -116,6 +116,11 @@ def lib():
             L.hvo_push_deposit_open.argtypes = [P, P, I64, P, P, P, P, P]
             L.hvo_init_open.argtypes = [P, P, I64, P, P, P, P]
             L.hvo_step_open.argtypes = [P, P, I64, P, P, P, P, P, P, P]
+            L.hvo_philox4x32_10.argtypes = [P, P, P]
+            L.hvo_inject_nfix.argtypes = [P, D, P]
+            L.hvo_inject_nfix.restype = ctypes.c_uint64
+            L.hvo_inject.argtypes = [P, I64, D, P, ctypes.c_uint64, I64, P, P, P, I64]
+            L.hvo_inject.restype = I64
             L.hvo_xcount.argtypes = [P]
             L.hvo_xcount.restype = I64
             L.hvo_set_threads.argtypes = [ctypes.c_int]
@@ -490,6 +495,44 @@ def extended_interior(g, F):
     return np.ascontiguousarray(G).reshape(nc, -1)
 
 
+class InjectFace(ctypes.Structure):
+    """Drifting Maxwellian injected through an open face (face 0 -x, 1 +x,
+    2 -y, 3 +y, 4 -z, 5 +z): density n, flow u, temperature T, weight w."""
+    _fields_ = [("face", ctypes.c_int64), ("n", ctypes.c_double), ("u", ctypes.c_double * 3),
+                ("T", ctypes.c_double), ("w", ctypes.c_double)]
+
+
+def inject_face(face, n, u, T, w) -> InjectFace:
+    return InjectFace(int(face), float(n), (ctypes.c_double * 3)(*[float(a) for a in u]),
+                      float(T), float(w))
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().hvo_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def inject_nfix(g, m, f: InjectFace) -> int:
+    return int(lib().hvo_inject_nfix(ctypes.byref(g), float(m), ctypes.byref(f)))
+
+
+def inject(g, s_idx, m, f: InjectFace, seed, step):
+    """Ions injected through one face at one step: (cell, off [3][k], v [3][k])."""
+    L = lib()
+    k = int(L.hvo_inject(ctypes.byref(g), int(s_idx), float(m), ctypes.byref(f),
+                         int(seed), int(step), None, None, None, 0))
+    cell = np.zeros(k, np.int64)
+    off = np.zeros((3, k))
+    v = np.zeros((3, k))
+    if k:
+        L.hvo_inject(ctypes.byref(g), int(s_idx), float(m), ctypes.byref(f), int(seed),
+                     int(step), _p(cell), _p(off), _p(v), k)
+    return cell, off, v
+
+
 class Sim:
     """Whole-state oracle simulation: species plus B, E and the previous
     (half-step) moments, advanced by ``hvo_step``.  B0 is the initial
@@ -497,8 +540,12 @@ class Sim:
     make_grid) the advanced state ``B`` is B1 = B0 - B0ext and
     ``B_total()`` adds the external part back."""
 
-    def __init__(self, g: Grid, species, B0):
+    def __init__(self, g: Grid, species, B0, inject=None, seed=0):
+        """inject: list of (species index, InjectFace) for open faces; seed
+        keys the injection's random numbers."""
         self.g = g
+        self.inject = list(inject or [])
+        self.seed = int(seed)
         self.species = [s.copy() for s in species]
         nce = ncell(g)
         self.B = _f64(B0).reshape(3, nce).copy()
@@ -559,6 +606,15 @@ class Sim:
                     m = int(arr[k].n)
                     s.cell, s.w = s.cell[:m].copy(), s.w[:m].copy()
                     s.off, s.v = s.off[:, :m].copy(), s.v[:, :m].copy()
+                # injected ions appended after the push, species by species,
+                # faces in the order given (they deposit from the next step)
+                for s_idx, f in self.inject:
+                    sp = self.species[s_idx]
+                    c, o, vv = inject(self.g, s_idx, sp.m, f, self.seed, self.step_count)
+                    sp.cell = np.concatenate([sp.cell, c])
+                    sp.off = np.ascontiguousarray(np.concatenate([sp.off, o], axis=1))
+                    sp.v = np.ascontiguousarray(np.concatenate([sp.v, vv], axis=1))
+                    sp.w = np.concatenate([sp.w, np.full(c.shape[0], f.w)])
             elif self.pe is not None:
                 lib().hvo_step_pe(ctypes.byref(self.g), arr, len(self.species), _p(self.B),
                                   _p(self.E), _p(self.pe), _p(self.n_prev), _p(self.J_prev),

@@ -84,6 +84,14 @@
  *      face is removed.
  *   R23 open faces are built for the hybrid Ohm's law with the equation of
  *      state and without smoothing.
+ *   R24 injection through an open face (Sec. 2.3, after Daughton et al.
+ *      2006): a drifting Maxwellian (n, u, T) and a weight w per species
+ *      and face; per face cell and step the count is N = Gamma A dt / w
+ *      rounded stochastically, each ion's inward speed follows the
+ *      flux-weighted distribution, its tangential velocity the Maxwellian,
+ *      it enters at a uniform time within the step and is appended after
+ *      the push (it deposits from the next step on); random numbers from
+ *      Philox4x32-10 keyed by the run's seed.
  *   R9 an axis with one cell (2D runs use ny = 1) is periodic with period one
  *      cell, so shapes fold onto the same cell and centred differences along
  *      it vanish.  Offsets along such an axis are never moved.
@@ -1232,6 +1240,152 @@ void hvo_step_open(const hvo_grid *g, hvo_species *sp, int64_t nsp, double *B1, 
   free(Je);
   free(Bt);
   free(Btx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Injection through open faces (Sec. 2.3: particles re-injected with the   */
+/* flux of a drifting Maxwellian; reading R24).                             */
+/*                                                                          */
+/* Random numbers come from the counter-based generator Philox4x32-10       */
+/* (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1,  */
+/* 2, 3", SC 2011): 10 rounds of two 32x32 -> 64-bit products of the        */
+/* counter words with fixed multipliers, the key added back each round and  */
+/* bumped by two Weyl constants between rounds.  The GPU path implements    */
+/* the same generator; both draw the same words for the same counter.       */
+/* ------------------------------------------------------------------------ */
+
+void hvo_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  for (int a = 0; a < 4; ++a) out[a] = c[a];
+}
+
+/* a 32-bit word as a uniform in [0, 1) with 24 bits (exact in float) */
+#define HVO_PI 3.14159265358979323846
+
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+typedef struct {
+  int64_t face;     /* 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z (must be an open axis) */
+  double n;         /* density of the drifting Maxwellian */
+  double u[3];      /* its flow */
+  double T;         /* its temperature (thermal speed sqrt(T / m)) */
+  double w;         /* weight of every injected ion */
+} hvo_inject_face;
+
+/* Expected injected ions per face cell and step, N = Gamma A dt / w, with
+ * the one-sided flux Gamma = n [vt/sqrt(2 pi) exp(-U^2/2vt^2) +
+ * U/2 (1 + erf(U/(sqrt2 vt)))] of the drifting Maxwellian (U the inward
+ * flow), as a 40.24 fixed-point number (the count decision is integer
+ * arithmetic on both sides). */
+uint64_t hvo_inject_nfix(const hvo_grid *g, double m, const hvo_inject_face *f) {
+  int ax = (int)(f->face / 2);
+  double sgn = (f->face % 2 == 0) ? 1.0 : -1.0;
+  double vt = sqrt(f->T / m), U = sgn * f->u[ax];
+  double flux;
+  if (vt > 0.0)
+    flux = f->n * (vt / sqrt(2.0 * HVO_PI) * exp(-U * U / (2.0 * vt * vt)) +
+                   0.5 * U * (1.0 + erf(U / (sqrt(2.0) * vt))));
+  else
+    flux = f->n * (U > 0.0 ? U : 0.0);
+  double d[3] = {g->dx, g->dy, g->dz};
+  double area = d[(ax + 1) % 3] * d[(ax + 2) % 3];
+  double N = flux * area * g->dt / f->w;
+  return (uint64_t)floor(N * 16777216.0 + 0.5);
+}
+
+/* Inverse of the flux-weighted CDF of the inward speed, in units of vt:
+ * F(t) = g(t) / g(inf), g(t) = exp(-a^2/2) - exp(-(t-a)^2/2)
+ *        + a sqrt(pi/2) [erf((t-a)/sqrt2) + erf(a/sqrt2)],  a = U / vt,
+ * by 40 bisections of [0, max(a, 0) + 12]. */
+static double flux_speed(double a, double u) {
+  double ginf = exp(-0.5 * a * a) + a * sqrt(HVO_PI / 2.0) * (1.0 + erf(a / sqrt(2.0)));
+  double lo = 0.0, hi = (a > 0.0 ? a : 0.0) + 12.0;
+  for (int it = 0; it < 40; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double gm = exp(-0.5 * a * a) - exp(-0.5 * (mid - a) * (mid - a)) +
+                a * sqrt(HVO_PI / 2.0) * (erf((mid - a) / sqrt(2.0)) + erf(a / sqrt(2.0)));
+    if (gm < u * ginf) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Ions injected through face f of species s_idx at step `step`: for every
+ * face cell c (the tangential cell index, x before y before z), in order,
+ * count = (nfix + (r >> 8)) >> 24 with r word 0 of Philox at counter
+ * (step, c, 0xffffffff, tag), tag = s_idx << 8 | face << 4; ion k of the
+ * cell takes words (u0..u3) at (step, c, k, tag) and (u4..u7) at
+ * (step, c, k, tag | 1): inward speed from u0 (flux_speed), tangential
+ * velocities by Box-Muller from u1, u2 (first tangential axis cos, second
+ * sin), tangential offsets 2 u4 - 1, 2 u5 - 1 (axes with one cell: 0), depth
+ * v_n dt u6 from the face (entered at a uniform time in the step).  An ion
+ * whose depth reaches beyond the grid is not placed.  Returns the number of
+ * ions; fills cell/off/v (cap entries at most) when cell != NULL. */
+int64_t hvo_inject(const hvo_grid *g, int64_t s_idx, double m, const hvo_inject_face *f,
+                   uint64_t seed, int64_t step, int64_t *cell, double *off, double *v,
+                   int64_t cap) {
+  int ax = (int)(f->face / 2), low = f->face % 2 == 0;
+  int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2; /* tangential axes, ascending */
+  int64_t n[3] = {g->nx, g->ny, g->nz};
+  double d[3] = {g->dx, g->dy, g->dz};
+  double vt = sqrt(f->T / m), sgn = low ? 1.0 : -1.0;
+  double a = vt > 0.0 ? sgn * f->u[ax] / vt : 0.0;
+  uint64_t nfix = hvo_inject_nfix(g, m, f);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t tag = ((uint32_t)s_idx << 8) | ((uint32_t)f->face << 4);
+  int64_t count = 0;
+  for (int64_t c = 0; c < n[t1] * n[t2]; ++c) {
+    int64_t i1 = c % n[t1], i2 = c / n[t1];
+    uint32_t ctr[4] = {(uint32_t)step, (uint32_t)c, 0xffffffffu, tag}, r[4];
+    hvo_philox4x32_10(ctr, key, r);
+    uint64_t k_n = (nfix + (uint64_t)(r[0] >> 8)) >> 24;
+    for (uint64_t k = 0; k < k_n; ++k) {
+      uint32_t ca[4] = {(uint32_t)step, (uint32_t)c, (uint32_t)k, tag}, ra[4];
+      uint32_t cb[4] = {(uint32_t)step, (uint32_t)c, (uint32_t)k, tag | 1u}, rb[4];
+      hvo_philox4x32_10(ca, key, ra);
+      hvo_philox4x32_10(cb, key, rb);
+      double vn = vt > 0.0 ? vt * flux_speed(a, u24(ra[0])) : sgn * f->u[ax];
+      double rr = sqrt(-2.0 * log(1.0 - u24(ra[1]))), th = 2.0 * HVO_PI * u24(ra[2]);
+      double depth = vn * g->dt * u24(rb[2]) / d[ax]; /* cells from the face */
+      double xr = low ? depth : (double)n[ax] - depth;
+      double fl = floor(xr);
+      if (fl < 0.0 || fl >= (double)n[ax]) continue;
+      if (cell && count < cap) {
+        int64_t ci[3];
+        double o[3], vv[3];
+        ci[ax] = (int64_t)fl;
+        o[ax] = 2.0 * (xr - fl) - 1.0;
+        vv[ax] = sgn * vn;
+        ci[t1] = i1;
+        ci[t2] = i2;
+        o[t1] = n[t1] > 1 ? 2.0 * u24(rb[0]) - 1.0 : 0.0;
+        o[t2] = n[t2] > 1 ? 2.0 * u24(rb[1]) - 1.0 : 0.0;
+        vv[t1] = f->u[t1] + vt * rr * cos(th);
+        vv[t2] = f->u[t2] + vt * rr * sin(th);
+        cell[count] = ci[0] + g->nx * (ci[1] + g->ny * ci[2]);
+        for (int q = 0; q < 3; ++q) {
+          off[q * cap + count] = o[q];
+          v[q * cap + count] = vv[q];
+        }
+      }
+      ++count;
+    }
+  }
+  return count;
 }
 
 /* Number of cells of the extended grid (for the caller's Eext). */

@@ -239,6 +239,28 @@ __global__ void unpack4_kernel(int ncell, const float4 *in, int ncomp, int first
   }
 }
 
+// B component-major, with the external field added back (the total field)
+__global__ void unpack_B_kernel(int ncell, const float4 *B, const float4 *B0, float *out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    float4 v = B[c];
+    if (B0) {
+      const float4 e = B0[c];
+      v = make_float4(v.x + e.x, v.y + e.y, v.z + e.z, 0.f);
+    }
+    out[c] = v.x;
+    out[(size_t)ncell + c] = v.y;
+    out[(size_t)2 * ncell + c] = v.z;
+  }
+}
+
+// B1 = B - B0 when an external field is set
+__global__ void sub_ext_kernel(int ncell, float4 *B, const float4 *B0) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const float4 v = B[c], e = B0[c];
+    B[c] = make_float4(v.x - e.x, v.y - e.y, v.z - e.z, 0.f);
+  }
+}
+
 __global__ void unpack_E_kernel(Geom g, const float4 *EB, float *out) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     const int i = c % g.nx;
@@ -446,6 +468,31 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
     return cuda_fail(e, "hv_init_grid upload");
   }
   *out = c;
+  return HV_OK;
+}
+
+hv_status hv_set_external_field(hv_ctx *c, const float *B0_host) {
+  if (!c || !B0_host) return fail(HV_EINVAL, "ctx or B0 is NULL");
+  if (c->started) return fail(HV_ESTATE, "the external field must be set before the first step");
+  if (c->B0ext) return fail(HV_ESTATE, "the external field is already set");
+  const size_t nc = (size_t)c->g.ncell;
+  std::vector<float4> hb(nc);
+  for (size_t i = 0; i < nc; ++i) {
+    hb[i] = make_float4(B0_host[i], B0_host[nc + i], B0_host[2 * nc + i], 0.f);
+    if (!std::isfinite(hb[i].x) || !std::isfinite(hb[i].y) || !std::isfinite(hb[i].z))
+      return fail(HV_EINVAL, "the external field has a non-finite value");
+  }
+  float4 *d = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
+  if (!d) return fail(HV_ENOMEM, "external field allocation failed");
+  cudaError_t e = cudaMemcpyAsync(d, hb.data(), sizeof(float4) * nc, cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess) {
+    sub_ext_kernel<<<eblocks(nc), 256, 0, c->stream>>>(c->g.ncell, c->B, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_set_external_field");
+  c->B0ext = d;
   return HV_OK;
 }
 
@@ -694,7 +741,8 @@ hv_status hv_moments(hv_ctx *c, float *n_out, float *J_out, float *E_out, float 
     if (jb.kind == 0) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->mprev, 1, 0, tmp);
     if (jb.kind == 1) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->mprev, 3, 1, tmp);
     if (jb.kind == 2) unpack_E_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g, c->EB, tmp);
-    if (jb.kind == 3) unpack4_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->B, 3, 0, tmp);
+    if (jb.kind == 3)
+      unpack_B_kernel<<<eblocks(nc), 256, 0, c->stream>>>(g.ncell, c->B, c->B0ext, tmp);
     e = cudaGetLastError();
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(jb.dst, tmp, sizeof(float) * ncomp * nc,

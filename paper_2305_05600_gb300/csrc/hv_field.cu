@@ -287,6 +287,7 @@ struct StageArgs {
   const float *pin, *pbase;
   float *pout;
   float pcoef;
+  const float4 *B0;   // external field (interior) or null: B arrays hold B1
 };
 
 // Output tile and halos.  FINAL = 0: stage (E on halo 1, B on halo 3);
@@ -398,9 +399,16 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     const int lz = r / (RE::X * RE::Y) - T::HE;
     const int jc = (lx + T::HJ) + (ly + T::HJ * T::HY) * sJy + (lz + T::HJ) * sJz;
     const int b = (lx + T::HB) + (ly + T::HB * T::HY) * sBy + (lz + T::HB) * sBz;
-    const float4 mi = a.mom[gidx(lx, ly, lz)];
+    const int gE = gidx(lx, ly, lz);
+    const float4 mi = a.mom[gE];
     const float inv = 1.f / nf[jc];
-    const float bx = Bx[b], by = By[b], bz = Bz[b];
+    float bx = Bx[b], by = By[b], bz = Bz[b];
+    if (a.B0) {  // the total field B0 + B1 in the cross products (and for the push)
+      const float4 b0 = __ldg(a.B0 + gE);
+      bx += b0.x;
+      by += b0.y;
+      bz += b0.z;
+    }
     const float jx = Jx[jc], jy = Jy[jc], jz = Jz[jc];
     const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
     const float gpx = (pe[jc + 1] - pe[jc - 1]) * k.idx2;
@@ -740,7 +748,13 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
         const int c = E0 + r;
         const float4 mi = m0[c];
         const float inv = __frcp_rn(fmaxf(mi.x, k.n_floor));
-        const float bxv = b0[c], byv = b0[NP + c], bzv = b0[2 * NP + c];
+        float bxv = b0[c], byv = b0[NP + c], bzv = b0[2 * NP + c];
+        if (a.B0) {  // total field B0 + B1 in the cross products
+          const float4 ext = __ldg(a.B0 + xe[u] + zoff(ze));
+          bxv += ext.x;
+          byv += ext.y;
+          bzv += ext.z;
+        }
         const float jx = j0[c], jy = j0[NP + c], jz = j0[2 * NP + c];
         const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
         const float gpx = (p0[c + 1] - p0[c - 1]) * k.idx2;
@@ -810,13 +824,18 @@ struct SubArgs {
   const float4 *B;
   float4 *Bout;
   const float4 *mom;
+  const float4 *B0;  // external field (interior) or null
   float h;
 };
 
 // E from Ohm's law at tile point (x, z), with B, J on their own regions and
 // p_e, 1/n_f and J_i per cell on R5 (computed once per cell at load).
+// With an external field (B = B0 + B1 split, Sec. 2.3) Bp holds B1 and
+// (b0x, b0y, b0z) is B0 at the point: J = curl B1, the cross products take
+// the total field.
 __device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int x, int z,
                                       const float *Bp, int rb, const float *Jp, int rj,
+                                      float b0x, float b0y, float b0z,
                                       float &ex, float &ey, float &ez) {
   using namespace sub2d;
   const int nb = N(rb), nj = N(rj), nm = N(5);
@@ -831,7 +850,7 @@ __device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int
   const float ly = (Jy[ij + 1] + Jy[ij - 1] - 2.f * jy) * k.ilx + (Jy[ij + wj] + Jy[ij - wj] - 2.f * jy) * k.ilz;
   const float lz = (Jz[ij + 1] + Jz[ij - 1] - 2.f * jz) * k.ilx + (Jz[ij + wj] + Jz[ij - wj] - 2.f * jz) * k.ilz;
   const int ib = at(rb, x, z);
-  const float bx = Bp[ib], by = Bp[nb + ib], bz = Bp[2 * nb + ib];
+  const float bx = Bp[ib] + b0x, by = Bp[nb + ib] + b0y, bz = Bp[2 * nb + ib] + b0z;
   const float ux = jx - mjx[im], uy = jy - mjy[im], uz = jz - mjz[im];
   const float inv = invn[im];
   ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx;
@@ -922,7 +941,9 @@ __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
   for (int t_ = (int)threadIdx.x; t_ < N(4); t_ += blockDim.x) {
       const int x = t_ % W(4) - 4, z = t_ / W(4) - 4;
       float ex, ey, ez;
-      ohm2d(sm, k, x, z, Bp, 6, Jp, 5, ex, ey, ez);
+      float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.B0) b0 = __ldg(a.B0 + gidx(x, z));
+      ohm2d(sm, k, x, z, Bp, 6, Jp, 5, b0.x, b0.y, b0.z, ex, ey, ez);
       const int i = at(4, x, z);
       Ep[i] = ex;
       Ep[N(4) + i] = ey;
@@ -948,7 +969,9 @@ __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
   for (int t_ = (int)threadIdx.x; t_ < N(1); t_ += blockDim.x) {
       const int x = t_ % W(1) - 1, z = t_ / W(1) - 1;
       float ex, ey, ez;
-      ohm2d(sm, k, x, z, Sp, 3, Jp, 2, ex, ey, ez);
+      float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.B0) b0 = __ldg(a.B0 + gidx(x, z));
+      ohm2d(sm, k, x, z, Sp, 3, Jp, 2, b0.x, b0.y, b0.z, ex, ey, ez);
       const int i = at(1, x, z);
       Ep[i] = ex;
       Ep[N(1) + i] = ey;
@@ -1006,14 +1029,20 @@ cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
 // diagnostics
 // ----------------------------------------------------------------------------
 
+// W_B of the total field (B0 + B1 with an external field), max |div| of the
+// advanced field B (B1 with an external field), charge of the moments.
 __global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, float vc,
-                                                        const float4 *B, const float4 *mom,
-                                                        double *part) {
+                                                        const float4 *B, const float4 *B0,
+                                                        const float4 *mom, double *part) {
   double wb = 0.0, ch = 0.0, md = 0.0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, kk;
     decode(g, c, i, j, kk);
-    const float4 b = B[c];
+    float4 b = B[c];
+    if (B0) {
+      const float4 e = B0[c];
+      b = make_float4(b.x + e.x, b.y + e.y, b.z + e.z, 0.f);
+    }
     wb += 0.5 * ((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) * vc;
     ch += (double)mom[c].x * vc;
     const int xp = wrapn(i + 1, g.nx) + g.nx * (j + g.ny * kk);
@@ -1170,6 +1199,7 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   a.pin = a.pbase = nullptr;
   a.pout = nullptr;
   a.pcoef = 0.f;
+  a.B0 = c->B0ext;
   c->launches++;
   if (c->g.dim2) return launch_stage_t<2, 0>(c, a);
   const size_t smem = st3d::kFloats * sizeof(float);
@@ -1186,6 +1216,7 @@ bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0; }
 
 cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) {
   SubArgs a;
+  a.B0 = c->B0ext;
   a.g = c->g;
   a.k = field_consts(c);
   a.B = Bin;
@@ -1277,6 +1308,7 @@ cudaError_t launch_field_stage_pe(hv_ctx *c, const float4 *Bin, const float4 *Bb
   a.pbase = pbase;
   a.pout = pout;
   a.pcoef = coef;
+  a.B0 = c->B0ext;
   c->launches++;
   return c->g.dim2 ? launch_stage_t<2, 0, 1>(c, a) : launch_stage_t<3, 0, 1>(c, a);
 }
@@ -1297,6 +1329,7 @@ cudaError_t launch_field_stage_tiled(hv_ctx *c, const float4 *Bin, const float4 
   a.pin = a.pbase = nullptr;
   a.pout = nullptr;
   a.pcoef = 0.f;
+  a.B0 = c->B0ext;
   c->launches++;
   return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
 }
@@ -1326,6 +1359,7 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
   a.pbase = nullptr;
   a.pout = nullptr;
   a.pcoef = 0.f;
+  a.B0 = c->B0ext;
   c->launches++;
   cudaError_t e;
   if (c->p.pe_eq)
@@ -1339,8 +1373,8 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
 cudaError_t launch_diag(hv_ctx *c) {
   FieldConsts k = field_consts(c);
   c->launches += 2;
-  grid_diag_kernel<<<c->grid_blocks, 256, 0, c->stream>>>(c->g, k, (float)c->vc, c->B, c->mprev,
-                                                          c->gridpart);
+  grid_diag_kernel<<<c->grid_blocks, 256, 0, c->stream>>>(c->g, k, (float)c->vc, c->B, c->B0ext,
+                                                          c->mprev, c->gridpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   diag_final_kernel<<<1, 256, 0, c->stream>>>(c->gridpart, c->grid_blocks, c->pushpart,

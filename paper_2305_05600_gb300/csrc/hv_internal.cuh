@@ -256,7 +256,10 @@ struct hv_ctx {
   __nv_bfloat16 *tr_wt;
   double *tr_loss;
   int tr_step;
-  float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}
+  float4 *B, *Bs;       // interior [ncell] {Bx,By,Bz,0}; B1 when an external
+                        // field is set
+  float4 *B0ext;        // interior [ncell] fixed external field B0 of the
+                        // B = B0 + B1 split (Sec. 2.3), or null
   float *pe, *pes;      // interior [ncell] electron pressure and its stage
                         // value (pe_eq = 1 only, else null)
   float4 *mhalf, *mext, *mprev, *mtmp;  // interior moments {n,Jx,Jy,Jz}

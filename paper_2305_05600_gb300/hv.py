@@ -86,7 +86,7 @@ EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_mo
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
            "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
            "hv_filter_get_params", "hv_electron_pressure", "hv_get_tile_offsets",
-           "hv_inject_error", "hv_error_status", "hv_last_error"]
+           "hv_inject_error", "hv_error_status", "hv_set_external_field", "hv_last_error"]
 
 
 def library_path() -> str:
@@ -116,6 +116,7 @@ def lib():
         L.hv_get_tile_offsets.argtypes = [P, I32, P]
         L.hv_inject_error.argtypes = [P, I32]
         L.hv_error_status.argtypes = [I32]
+        L.hv_set_external_field.argtypes = [P, P]
         L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
         L.hv_filter_moments.argtypes = [P, P, P, ctypes.c_int]
         L.hv_filter_train_init.argtypes = [P, P, P]
@@ -241,6 +242,15 @@ def hv_init_grid(params, B0=None, stream=None) -> Ctx:
     _check(lib().hv_init_grid(ctypes.byref(p), b.ctypes.data if b is not None else None,
                               _stream_handle(stream), ctypes.byref(out)))
     return Ctx(out.value, p)
+
+
+def hv_set_external_field(ctx: Ctx, B0ext):
+    """Fixed external field B0 [3][nz][ny][nx] of the B = B0 + B1 split."""
+    p = ctx.params
+    b = np.ascontiguousarray(np.asarray(B0ext, dtype=np.float32).reshape(-1))
+    if b.size != 3 * p.nx * p.ny * p.nz:
+        raise ValueError("the external field must have 3*nx*ny*nz values")
+    _check(lib().hv_set_external_field(ctx.handle, b.ctypes.data))
 
 
 def hv_load_ions(ctx: Ctx, species: int, q: float, m: float, cell, off3, v3, w):

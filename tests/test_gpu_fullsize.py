@@ -24,6 +24,8 @@ The same check runs on the 3D Harris sheet (guide field, 32 ppc) on a
 periodic 64^3 subdomain and on the ion-ion beam on 64x32x32 cells.  The
 oracle step of the full 2D workload takes tens of seconds on one host
 core."""
+import json
+
 import numpy as np
 import pytest
 
@@ -165,6 +167,17 @@ def one_step_check(hvmod, wl, nsample=NSAMPLE, seed=2024):
     assert abs(d["charge"] - qw) < 1e-6 * qw
     check_diagnostics(p, d, sim, m["B"])
     print(f"face-ambiguous ions {int(amb.sum())}, cells they can reach {taint.mean():.2e}")
+    err = {"workload": wl.name, "cells": [p["nx"], p["ny"], p["nz"]], "ions": int(s.n),
+           "n_rel_l2": rel_l2(n, sim.n_prev), "n_rel_l2_clean": rel_l2(n[clean], sim.n_prev[clean]),
+           "J_rel_l2": rel_l2(J, sim.J_prev),
+           "J_rel_l2_clean": rel_l2(J[:, clean], sim.J_prev[:, clean]),
+           "B_rel_l2": rel_l2(m["B"].reshape(3, -1), sim.B),
+           "E_rel_l2_clean": rel_l2(m["E"].reshape(3, -1)[:, clean_e], sim.E[:, clean_e]),
+           "W_K_rel": abs(d["W_K"] - od["W_K"]) / od["W_K"],
+           "W_B_rel": abs(d["W_B"] - od["W_B"]) / od["W_B"],
+           "charge_rel": abs(d["charge"] - od["charge"]) / abs(od["charge"]),
+           "P_abs": [abs(d["P"][a] - od["P"][a]) for a in range(3)],
+           "max_divB_gpu": d["max_divB"], "max_divB_oracle": od["max_divB"]}
 
     # the sampled ions, located on both sides by their marker weights
     marks = w[idx]
@@ -182,6 +195,10 @@ def one_step_check(hvmod, wl, nsample=NSAMPLE, seed=2024):
     dv = np.abs(g["v"][:, gi].astype(np.float64) - sp.v[:, idx])
     vmag = np.linalg.norm(sp.v[:, idx], axis=0)
     assert (dv.max(axis=0) <= 1e-5 * (vmag + vscale)).all(), dv.max()
+    err["sampled_ions"] = int(nsample)
+    err["ion_pos_max_cells"] = float(np.abs(dpos / dl).max())
+    err["ion_v_rel_l2"] = rel_l2(g["v"][:, gi], sp.v[:, idx])
+    print("FP32-vs-FP64 errors " + json.dumps(err))
 
 
 def test_full_size_harris2d_one_step(hvmod):

@@ -188,6 +188,53 @@ def test_field_smoothing_parity(hvmod, dim, shape):
     ctx.close()
 
 
+def external_field(p):
+    """A fixed field with a non-zero centred curl: B0 = (1, 0.1 cos(2 pi z/Lz),
+    0.2 sin(2 pi x / Lx))."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    x = (np.arange(nx) + 0.5) * p["dx"]
+    z = (np.arange(nz) + 0.5) * p["dz"]
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = 1.0
+    b[1] = 0.1 * np.cos(2 * np.pi * z / (nz * p["dz"]))[:, None, None]
+    b[2] = 0.2 * np.sin(2 * np.pi * x / (nx * p["dx"]))[None, None, :]
+    return b.astype(np.float32).reshape(3, -1)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_external_field_split_parity(hvmod, dim):
+    """B = B0 + B1 split (Sec. 2.3): a fixed external field with a non-zero
+    discrete curl, only B1 advanced, J = curl B1, total field in the cross
+    products and the push; two steps against the oracle."""
+    wl = small_workload(dim, "qs")
+    p = wl.params
+    b0 = external_field(p)
+    wl.B0 = (wl.B0.reshape(3, -1) + b0).astype(np.float32).reshape(wl.B0.shape)
+    ctx = hvmod.hv_init_grid(p, wl.B0)
+    hvmod.hv_set_external_field(ctx, b0)
+    for s_idx, s in enumerate(wl.species):
+        hvmod.hv_load_ions(ctx, s_idx, s.q, s.m, s.cell, s.off, s.v, s.w)
+    with pytest.raises(hvmod.HVError):
+        hvmod.hv_set_external_field(ctx, b0)  # once per context
+    sim = oracle_sim(wl, B0ext=b0.astype(np.float64))
+    vscale = float(np.sqrt(np.mean(wl.species[0].v.astype(np.float64) ** 2)))
+    m0 = hvmod.hv_moments(ctx)
+    assert rel_l2(m0["E"].reshape(3, -1), sim.E) < 1e-4
+    for _ in range(2):
+        hvmod.hv_step(ctx, 1)
+        sim.step(1, sort_every=1, key_fn=order_of(hvmod, ctx, p))
+        compare_particles(p, hvmod.hv_get_ions(ctx, 0), sim.species[0], vscale)
+        m = hvmod.hv_moments(ctx)
+        assert rel_l2(m["n"].reshape(-1), sim.n_prev) < 1e-5
+        assert rel_l2(m["J"].reshape(3, -1), sim.J_prev) < 1e-5
+        assert rel_l2(m["B"].reshape(3, -1), sim.B_total()) < 1e-6
+        B1 = m["B"].reshape(3, -1).astype(np.float64) - b0
+        assert rel_l2(B1 - (wl.B0.reshape(3, -1) - b0), sim.B - (wl.B0.reshape(3, -1) - b0)) < 1e-4
+        assert rel_l2(m["E"].reshape(3, -1), sim.E) < 1e-4
+        check_diagnostics(p, hvmod.hv_diag(ctx), sim, m["B"], B0ext=b0)
+    ctx.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_electron_energy_equation_parity(hvmod, dim):
     """p_e advanced with the electron energy equation (adiabatic gamma =
