@@ -79,7 +79,8 @@ typedef struct {
                            B^n that the push gathers (the self-consistent
                            field smoothing of Sec. 2.2); the field state is
                            not smoothed; 0 off, at most 64 */
-  uint64_t seed;        /* reserved for stochastic extensions */
+  uint64_t seed;        /* key of the random numbers of injection through
+                           open faces (hv_set_injection) */
   int32_t pe_eq;        /* 1: the electron pressure is a field advanced with
                            the electron energy equation (Sec. 2.1, Eq. dpdt)
                            in the field subcycles; 0: p_e = Te n^gamma_e */
@@ -95,7 +96,17 @@ typedef struct {
   int32_t relativistic; /* 1: the particles carry u = gamma v (loaded and
                            returned in place of v) and move with the
                            relativistic Boris push (App. A) */
-  int32_t reserved;     /* must be 0 */
+  int32_t open_faces;   /* bit a set (a = 0 x, 1 y, 2 z): both faces of axis a
+                           are open (Sec. 2.3) instead of periodic: one ghost
+                           cell beyond each face copies B1, B0 and the
+                           moments of its interior neighbour, Ohm's law there
+                           drops the derivatives normal to the face, deposits
+                           beyond the face fold onto the cell next to it, and
+                           an ion that ends a step beyond it leaves the run;
+                           ions enter through hv_set_injection.  Only with
+                           ohm_model = 0, pe_eq = 0, no smoothing, no
+                           relativistic push and more than one cell along the
+                           axis (HV_EINVAL otherwise); 0: all periodic */
   double c_light;       /* speed of light in the velocity unit, > 0 when
                            relativistic (ignored otherwise) */
 } hv_params;
@@ -112,7 +123,8 @@ typedef struct {
   double max_divB;   /* max over cells of |div_c B^{n+1}| (centred, Eq. 12;
                         of B1 when an external field is set) */
   int32_t err_word;  /* device error bits: 1 CFL, 2 non-finite particle,
-                        4 corrupt cell index, 8 bounded wait gave up */
+                        4 corrupt cell index, 8 bounded wait gave up,
+                        16 no free slot for injected ions */
   int32_t pad;
 } hv_diag_t;
 
@@ -136,7 +148,8 @@ typedef struct {
   int32_t ntiles;
   int32_t nspecies;
   int32_t pad;
-  int64_t n[8];       /* ions per species */
+  int64_t n[8];       /* ions per species (with open faces: particle slots,
+                         live and free; hv_get_ions counts the live ions) */
   int64_t step;       /* completed steps */
 } hv_info_t;
 
@@ -174,6 +187,33 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
  * before the first step and once per context (HV_ESTATE otherwise);
  * HV_EINVAL for a non-finite value.  Synchronises. */
 hv_status hv_set_external_field(hv_ctx *ctx, const float *B0_host);
+
+/* Contexts with open faces (hv_params.open_faces): grow the particle slots
+ * of species `species` to `capacity` (at least its loaded ions, below
+ * 2^31 - 4) so that ions injected through open faces (hv_set_injection)
+ * find free slots; a step that runs out of slots latches error bit 16
+ * (HV_ENOMEM at the next synchronising call).  Slots of absorbed ions are
+ * freed at each sort.  After hv_load_ions, before the first step
+ * (HV_ESTATE otherwise); HV_EINVAL for a periodic context or a bad size. */
+hv_status hv_reserve_ions(hv_ctx *ctx, int32_t species, int64_t capacity);
+
+/* Inject ions of species `species` through open face `face` (0 -x, 1 +x,
+ * 2 -y, 3 +y, 4 -z, 5 +z) every step, as the paper re-injects particles at
+ * open boundaries (Sec. 2.3): the flux of a drifting Maxwellian with density
+ * n, flow u[3] (velocity units) and temperature T (thermal speed
+ * sqrt(T / m)), ions of weight w.  Per face cell and step the expected count
+ * is N = Gamma A dt / w, Gamma = n [vt/sqrt(2 pi) exp(-U^2/2vt^2) +
+ * U/2 (1 + erf(U/(sqrt2 vt)))] with U the inward flow and A the face cell
+ * area, rounded stochastically; each ion's inward speed follows the
+ * flux-weighted distribution and its tangential velocity the Maxwellian,
+ * it enters at a uniform time within the step (uniform tangential
+ * position), is appended after the push and deposits from the next step on.
+ * The random numbers are Philox4x32-10 words keyed by hv_params.seed at
+ * counters (step, face cell, ion, species and face), so runs repeat
+ * exactly.  Before the first step, up to 6 faces per species; HV_EINVAL for
+ * a face of a periodic axis or bad values. */
+hv_status hv_set_injection(hv_ctx *ctx, int32_t species, int32_t face, double n,
+                           const double *u, double T, double w);
 
 /* Append ion species number `species` (must equal the number of species
  * already loaded; up to 8) with charge q and mass m (q_s = Z_s e, m_s; Sec.
@@ -287,7 +327,7 @@ hv_status hv_query(const hv_ctx *ctx, hv_info_t *out);
 hv_status hv_get_tile_offsets(hv_ctx *ctx, int32_t species, int32_t *tile_off);
 
 /* Fault injection for testing the failure path: OR `bits` (a non-empty
- * combination of the hv_diag_t err_word bits 1, 2, 4, 8) into the context's
+ * combination of the hv_diag_t err_word bits 1, 2, 4, 8, 16) into the context's
  * device error word, as a kernel that detected the fault would.  The next
  * synchronising call reports it (hv_error_status gives the mapping).
  * HV_EINVAL for other bits.  Nothing on the GPU faults or waits. */
@@ -296,7 +336,7 @@ hv_status hv_inject_error(hv_ctx *ctx, int32_t bits);
 /* The status that a synchronising call returns for device error word
  * `err_word` (hv_last_error() then names the cause), without a context or a
  * GPU: bit 2 non-finite -> HV_ENAN, else bit 1 -> HV_ECFL, else bit 4 ->
- * HV_ECUDA, else bit 8 -> HV_ETIMEOUT, else HV_OK. */
+ * HV_ECUDA, else bit 8 -> HV_ETIMEOUT, else bit 16 -> HV_ENOMEM, else HV_OK. */
 hv_status hv_error_status(int32_t err_word);
 
 /* Turn per-phase CUDA-event timing on (1) or off (0); turning it on resets

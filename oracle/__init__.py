@@ -121,6 +121,8 @@ def lib():
             L.hvo_inject_nfix.restype = ctypes.c_uint64
             L.hvo_inject.argtypes = [P, I64, D, P, ctypes.c_uint64, I64, P, P, P, I64]
             L.hvo_inject.restype = I64
+            L.hvo_max_div.argtypes = [P, P]
+            L.hvo_max_div.restype = D
             L.hvo_xcount.argtypes = [P]
             L.hvo_xcount.restype = I64
             L.hvo_set_threads.argtypes = [ctypes.c_int]
@@ -476,6 +478,12 @@ def ohm_open(g, B1, n, Ji):
     E = np.zeros(3 * xcount(g))
     lib().hvo_ohm_open(ctypes.byref(g), _p(B1), _p(n), _p(Ji), _p(E))
     return E.reshape(3, -1)
+
+
+def max_div(g, B) -> float:
+    """max |div B| over the interior (open faces: ghost copies)."""
+    B = _f64(B).reshape(3, -1)
+    return float(lib().hvo_max_div(ctypes.byref(g), _p(B)))
 
 
 def field_advance_open(g, B1, n, Ji):

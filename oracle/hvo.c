@@ -1388,6 +1388,24 @@ int64_t hvo_inject(const hvo_grid *g, int64_t s_idx, double m, const hvo_inject_
   return count;
 }
 
+/* max |div B| over the interior cells, with the ghost copies of open faces
+ * (the same rule as the open-face diagnostics) or periodic neighbours. */
+double hvo_max_div(const hvo_grid *g, const double *B) {
+  xgrid x = xgrid_of(g);
+  int64_t nce = ncell_of(g), ne = xcount(&x);
+  double *Bx = (double *)malloc(sizeof(double) * 3 * ne);
+  xfill(g, &x, B, 3, Bx);
+  double md = 0.0;
+  for (int64_t q = 0; q < nce; ++q) {
+    int64_t c[3];
+    cdecode(g, q, &c[0], &c[1], &c[2]);
+    double dv = xd(&x, Bx, 0, c) + xd(&x, Bx + ne, 1, c) + xd(&x, Bx + 2 * ne, 2, c);
+    if (fabs(dv) > md) md = fabs(dv);
+  }
+  free(Bx);
+  return md;
+}
+
 /* Number of cells of the extended grid (for the caller's Eext). */
 int64_t hvo_xcount(const hvo_grid *g) {
   xgrid x = xgrid_of(g);

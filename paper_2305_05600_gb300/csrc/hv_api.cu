@@ -106,7 +106,17 @@ hv_status check_params(const hv_params *p) {
     return fail(HV_EINVAL, "relativistic must be 0 or 1");
   if (p->relativistic && !finite_pos(p->c_light))
     return fail(HV_EINVAL, "c_light must be finite and > 0 for the relativistic push");
-  if (p->reserved != 0) return fail(HV_EINVAL, "reserved must be 0");
+  if (p->open_faces & ~7) return fail(HV_EINVAL, "open_faces takes bits 1 (x), 2 (y), 4 (z)");
+  if (p->open_faces) {
+    const int32_t n3[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a)
+      if ((p->open_faces >> a & 1) && n3[a] < 2)
+        return fail(HV_EINVAL, "an open axis needs more than one cell");
+    if (p->ohm_model != 0 || p->pe_eq || p->smooth_passes || p->field_smooth_passes ||
+        p->relativistic)
+      return fail(HV_EINVAL, "open faces are built for the hybrid Ohm's law with the equation "
+                             "of state, without smoothing and without the relativistic push");
+  }
   if (!std::isfinite(p->kappa) || p->kappa < 0) return fail(HV_EINVAL, "kappa must be finite and >= 0");
   if (p->pe_eq && p->kappa > 0) {
     // explicit heat conduction at the density floor: the explicit-midpoint
@@ -180,6 +190,8 @@ Geom make_geom(const hv_params *p) {
   g.ntiles = g.ntx * g.nty * g.ntz;
   g.tlog = 0;
   while ((1 << g.tlog) < g.tx * g.ty * g.tz) ++g.tlog;
+  for (int a = 0; a < 3; ++a) g.open[a] = (p->open_faces >> a) & 1;
+  g.any_open = p->open_faces != 0;
   return g;
 }
 
@@ -284,6 +296,8 @@ hv_status status_of_word(int e) {
   if (e & kErrCfl) return fail(HV_ECFL, "a particle moved more than one cell in one step");
   if (e & kErrIndex) return fail(HV_ECUDA, "a corrupt particle cell index was found");
   if (e & kErrTimeout) return fail(HV_ETIMEOUT, "a bounded device wait gave up");
+  if (e & kErrCapacity)
+    return fail(HV_ENOMEM, "no free particle slot for injected ions (see hv_reserve_ions)");
   return HV_OK;
 }
 
@@ -579,9 +593,121 @@ hv_status hv_load_ions(hv_ctx *c, int32_t species, double q, double m, int64_t n
     if (bad & 2) return fail(HV_EINVAL, "relative coordinate outside [-1, 1) or non-finite");
     return fail(HV_EINVAL, "non-finite velocity or weight");
   }
+  if (g.any_open) {
+    // slots in use, counted on the device (absorption and injection change it)
+    sp.n_used = (int *)ctx_alloc(c, sizeof(int));
+    if (!sp.n_used) return fail(HV_ENOMEM, "slot counter allocation failed");
+    const int nn = (int)n;
+    e = cudaMemcpyAsync(sp.n_used, &nn, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slot counter");
+  }
   c->nspecies++;
   e = tile_ranges_even(c, species);
   if (e != cudaSuccess) return cuda_fail(e, "tile ranges");
+  return HV_OK;
+}
+
+__global__ void mark_dead_kernel(int32_t *cell, int64_t lo, int64_t hi) {
+  for (int64_t t = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < hi;
+       t += (int64_t)gridDim.x * blockDim.x)
+    cell[t] = kDeadVox;
+}
+
+hv_status hv_reserve_ions(hv_ctx *c, int32_t species, int64_t capacity) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (!c->g.any_open) return fail(HV_EINVAL, "slot reserve is for contexts with open faces");
+  if (c->started) return fail(HV_ESTATE, "reserve slots before the first step");
+  if (species < 0 || species >= c->nspecies) return fail(HV_EINVAL, "no such species");
+  Species &sp = c->sp[species];
+  if (capacity < sp.n || capacity >= ((int64_t)1 << 31) - 4)
+    return fail(HV_EINVAL, "capacity must be at least the loaded ions and below 2^31 - 4");
+  const Geom &g = c->g;
+  const int64_t cap = std::max<int64_t>(4, ((capacity + 3) / 4) * 4);
+  const size_t arr = align256(sizeof(float) * cap);
+  const int narr = g.dim2 ? 7 : 8;
+  void *base[2] = {nullptr, nullptr};
+  Soa buf[2];
+  for (int b = 0; b < 2; ++b) {
+    base[b] = dev_alloc(arr * narr, c->stream);
+    if (!base[b]) {
+      if (b) dev_free(base[0], arr * narr, c->stream);
+      return fail(HV_ENOMEM, "particle allocation failed");
+    }
+    char *q = (char *)base[b];
+    int slot = 0;
+    buf[b].cell = (int32_t *)(q + arr * slot++);
+    buf[b].ox = (float *)(q + arr * slot++);
+    buf[b].oy = g.dim2 ? nullptr : (float *)(q + arr * slot++);
+    buf[b].oz = (float *)(q + arr * slot++);
+    buf[b].vx = (float *)(q + arr * slot++);
+    buf[b].vy = (float *)(q + arr * slot++);
+    buf[b].vz = (float *)(q + arr * slot++);
+    buf[b].w = (float *)(q + arr * slot++);
+  }
+  const Soa &o = sp.buf[sp.cur];
+  const size_t b4 = 4 * (size_t)sp.n;
+  cudaError_t e = cudaSuccess;
+  if (sp.n > 0) {
+    const void *src[8] = {o.cell, o.ox, o.oy, o.oz, o.vx, o.vy, o.vz, o.w};
+    void *dst[8] = {buf[0].cell, buf[0].ox, buf[0].oy, buf[0].oz, buf[0].vx, buf[0].vy,
+                    buf[0].vz, buf[0].w};
+    for (int f = 0; f < 8 && e == cudaSuccess; ++f)
+      if (src[f]) e = cudaMemcpyAsync(dst[f], src[f], b4, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  if (e == cudaSuccess && cap > sp.n) {
+    mark_dead_kernel<<<eblocks(cap - sp.n), 256, 0, c->stream>>>(buf[0].cell, sp.n, cap);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    for (int b = 0; b < 2; ++b) dev_free(base[b], arr * narr, c->stream);
+    return cuda_fail(e, "hv_reserve_ions");
+  }
+  for (int b = 0; b < 2; ++b) dev_free(sp.base[b], sp.bytes[b], c->stream);
+  for (int b = 0; b < 2; ++b) {
+    sp.base[b] = base[b];
+    sp.bytes[b] = arr * narr;
+    sp.buf[b] = buf[b];
+  }
+  sp.cur = 0;
+  sp.cap = cap;
+  sp.n = cap;  // slots; the device counter keeps the ones in use
+  if (sp.bucket) {  // sized for the old slot count
+    dev_free(sp.bucket, sp.bucket_bytes, c->stream);
+    sp.bucket = nullptr;
+  }
+  return HV_OK;
+}
+
+hv_status hv_set_injection(hv_ctx *c, int32_t species, int32_t face, double n, const double *u,
+                           double T, double w) {
+  if (!c || !u) return fail(HV_EINVAL, "ctx or u is NULL");
+  if (c->started) return fail(HV_ESTATE, "set injection before the first step");
+  if (species < 0 || species >= c->nspecies) return fail(HV_EINVAL, "no such species");
+  if (face < 0 || face > 5 || !c->g.open[face / 2])
+    return fail(HV_EINVAL, "face must be 0..5 on an axis with open faces");
+  if (!std::isfinite(n) || n < 0 || !std::isfinite(T) || T < 0 || !std::isfinite(w) || w <= 0 ||
+      !std::isfinite(u[0]) || !std::isfinite(u[1]) || !std::isfinite(u[2]))
+    return fail(HV_EINVAL, "n, T >= 0, w > 0 and u must be finite");
+  if (c->ninject >= 6 * kMaxSpecies) return fail(HV_EINVAL, "too many injection faces");
+  InjectFace f;
+  f.species = species;
+  f.face = face;
+  f.n = n;
+  f.T = T;
+  f.w = w;
+  for (int a = 0; a < 3; ++a) f.u[a] = u[a];
+  const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+  const int ax = face / 2;
+  const int cells = n3[(ax + 1) % 3] * n3[(ax + 2) % 3];
+  if (cells + 1 > c->inj_cells) {
+    int *q = (int *)ctx_alloc(c, sizeof(int) * (size_t)(cells + 1));
+    if (!q) return fail(HV_ENOMEM, "injection scratch allocation failed");
+    c->inj_scratch = q;
+    c->inj_cells = cells + 1;
+  }
+  c->inject[c->ninject++] = f;
   return HV_OK;
 }
 
@@ -635,6 +761,11 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       if (e != cudaSuccess) return cuda_fail(e, "push");
     }
     if (c->since_sort >= 0) c->since_sort++;
+    // ions entering through open faces join after the push (Sec. 2.3)
+    for (int q = 0; q < c->ninject; ++q) {
+      cudaError_t e = launch_injection(c, c->inject[q]);
+      if (e != cudaSuccess) return cuda_fail(e, "injection");
+    }
     if (ps) {
       cudaEventRecord(ev.e[2], c->stream);
       ev.launches[1] = c->launches - l0;
@@ -683,7 +814,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
         e = launch_field_stage_pe(c, c->B, c->B, c->Bs, c->pe, c->pe, c->pes, 0.5f * h);
         if (e == cudaSuccess)
           e = launch_field_stage_pe(c, c->Bs, c->B, c->B, c->pes, c->pe, c->pe, h);
-      } else if (c->p.ohm_model != 0) {
+      } else if (c->p.ohm_model != 0 || c->g.any_open) {
         // the resistive background: tiled stages
         e = launch_field_stage_tiled(c, c->B, c->B, c->Bs, 0.5f * h);
         if (e == cudaSuccess) e = launch_field_stage_tiled(c, c->Bs, c->B, c->B, h);
@@ -797,11 +928,56 @@ hv_status hv_diag(hv_ctx *c, hv_diag_t *out) {
   return HV_OK;
 }
 
+// hv_get_ions with open faces: the slots in use are read from the device and
+// the live ions among them (dead slots skipped) returned in order (host only).
+static hv_status get_ions_open(hv_ctx *c, Species &sp, int64_t *n_out, int32_t *cell, float *off3,
+                               float *v3, float *w, int on_device) {
+  if (on_device) return fail(HV_EINVAL, "with open faces hv_get_ions returns host arrays only");
+  int nu = 0;
+  cudaError_t e = cudaMemcpyAsync(&nu, sp.n_used, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_get_ions");
+  const Soa &s = sp.buf[sp.cur];
+  std::vector<int32_t> hc(nu);
+  std::vector<float> hf[7];
+  const float *src[7] = {s.ox, s.oy, s.oz, s.vx, s.vy, s.vz, s.w};
+  if (nu > 0) e = cudaMemcpyAsync(hc.data(), s.cell, 4 * (size_t)nu, cudaMemcpyDeviceToHost, c->stream);
+  for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+    hf[f].assign(nu, 0.f);
+    if (src[f] && nu > 0)
+      e = cudaMemcpyAsync(hf[f].data(), src[f], 4 * (size_t)nu, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_get_ions");
+  int64_t live = 0;
+  for (int i = 0; i < nu; ++i) live += hc[i] != kDeadVox;
+  if (n_out) *n_out = live;
+  int64_t o = 0;
+  for (int i = 0; i < nu; ++i) {
+    if (hc[i] == kDeadVox) continue;
+    if (cell) cell[o] = voxel_to_linear(c->g, hc[i]);
+    if (off3) {
+      off3[o] = hf[0][i];
+      off3[live + o] = hf[1][i];
+      off3[2 * live + o] = hf[2][i];
+    }
+    if (v3) {
+      v3[o] = hf[3][i];
+      v3[live + o] = hf[4][i];
+      v3[2 * live + o] = hf[5][i];
+    }
+    if (w) w[o] = hf[6][i];
+    ++o;
+  }
+  return latched(c, nullptr);
+}
+
 hv_status hv_get_ions(hv_ctx *c, int32_t species, int64_t *n_out, int32_t *cell, float *off3,
                       float *v3, float *w, int on_device) {
   if (!c) return fail(HV_EINVAL, "ctx is NULL");
   if (species < 0 || species >= c->nspecies) return fail(HV_EINVAL, "no such species");
   Species &sp = c->sp[species];
+  if (c->g.any_open) return get_ions_open(c, sp, n_out, cell, off3, v3, w, on_device);
   if (n_out) *n_out = sp.n;
   const int64_t n = sp.n;
   const Soa &s = sp.buf[sp.cur];
@@ -849,6 +1025,7 @@ hv_status hv_set_filter(hv_ctx *c, const float *params, const float *scale4, dou
     return HV_OK;
   }
   if (!c->g.dim2) return fail(HV_EINVAL, "the learned filter is built for the x-z layout (ny = 1)");
+  if (c->g.any_open) return fail(HV_EINVAL, "the learned filter pads periodically (no open faces)");
   if (!scale4) return fail(HV_EINVAL, "scale4 is NULL");
   for (int i = 0; i < kFilterParams; ++i)
     if (!std::isfinite(params[i])) return fail(HV_EINVAL, "non-finite filter parameter");
@@ -1037,8 +1214,8 @@ hv_status hv_get_tile_offsets(hv_ctx *c, int32_t species, int32_t *tile_off) {
 
 hv_status hv_inject_error(hv_ctx *c, int32_t bits) {
   if (!c) return fail(HV_EINVAL, "ctx is NULL");
-  if (bits <= 0 || (bits & ~(kErrCfl | kErrNonFinite | kErrIndex | kErrTimeout)))
-    return fail(HV_EINVAL, "bits must be a non-empty combination of 1, 2, 4 and 8");
+  if (bits <= 0 || (bits & ~(kErrCfl | kErrNonFinite | kErrIndex | kErrTimeout | kErrCapacity)))
+    return fail(HV_EINVAL, "bits must be a non-empty combination of 1, 2, 4, 8 and 16");
   inject_error_kernel<<<1, 1, 0, c->stream>>>(c->err, bits);
   c->launches++;
   cudaError_t e = cudaGetLastError();

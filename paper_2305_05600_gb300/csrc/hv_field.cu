@@ -90,10 +90,10 @@ __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
       continue;
     }
     int xs[5], ys[5], zs[5];
-    const int nxs = axis_images(i, g.nx, xs);
-    const int nys = g.dim2 ? 1 : axis_images(j, g.ny, ys);
+    const int nxs = axis_sources(i, g.nx, g.open[0], xs);
+    const int nys = g.dim2 ? 1 : axis_sources(j, g.ny, g.open[1], ys);
     if (g.dim2) ys[0] = 0;
-    const int nzs = axis_images(k, g.nz, zs);
+    const int nzs = axis_sources(k, g.nz, g.open[2], zs);
     for (int a3 = 0; a3 < nzs; ++a3)
       for (int a2 = 0; a2 < nys; ++a2)
         for (int a1 = 0; a1 < nxs; ++a1) {
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256) fold_records_kernel(MomArgs a) {
     int i, j, k;
     decode(g, c, i, j, k);
     int xs[5], zs[5];
-    const int nxs = axis_images(i, g.nx, xs);
-    const int nzs = axis_images(k, g.nz, zs);
+    const int nxs = axis_sources(i, g.nx, g.open[0], xs);
+    const int nzs = axis_sources(k, g.nz, g.open[2], zs);
     float m[4] = {0.f, 0.f, 0.f, 0.f};
     for (int a3 = 0; a3 < nzs; ++a3)
       for (int a1 = 0; a1 < nxs; ++a1) {
@@ -291,16 +291,17 @@ struct StageArgs {
 };
 
 // Output tile and halos.  FINAL = 0: stage (E on halo 1, B on halo 3);
-// FINAL = 1: E on the tile itself (B on halo 2).  DIM = 2: x-z plane.
+// FINAL = 1: E on the tile itself (B on halo 2), or with OPEN on halo 1 too
+// (the ghost cells beyond open faces get their own E).  DIM = 2: x-z plane.
 // PEQ: p_e is a field (electron energy equation), read instead of the
 // equation of state; a stage also advances it and keeps u_e, p_e u_e and
-// T_e on the E region.
-template <int DIM, int FINAL, int PEQ = 0>
+// T_e on the E region.  OPEN: some axes have open faces (Sec. 2.3).
+template <int DIM, int FINAL, int PEQ = 0, int OPEN = 0>
 struct Tile {
   static constexpr int OX = DIM == 2 ? 32 : 8;
   static constexpr int OY = DIM == 2 ? 1 : 8;
   static constexpr int OZ = DIM == 2 ? 16 : 4;
-  static constexpr int HE = FINAL ? 0 : 1;  // E halo
+  static constexpr int HE = FINAL && !OPEN ? 0 : 1;  // E halo
   static constexpr int HJ = HE + 1;         // J, n halo
   static constexpr int HB = HE + 2;         // B halo
   static constexpr int HY = DIM == 2 ? 0 : 1;  // y halos scale by this
@@ -314,10 +315,16 @@ struct Tile {
   static constexpr size_t smem_floats = 3 * NB + 3 * NJ + 2 * NJ + 3 * NE + NX;
 };
 
-template <int DIM, int FINAL, int PEQ = 0>
+// With OPEN (open faces, Sec. 2.3): B1, B0 and the moments beyond an open
+// face are read from the interior cell next to it (clamped index), and in a
+// cell beyond an open face every derivative normal to that face is zero
+// (J = curl B1, the Laplacian of J, grad p_e): Ohm's law in the ghost cell
+// has no normal gradients.  The final variant also writes E and B of the
+// ghost cells into the first ghost layer of the gather array.
+template <int DIM, int FINAL, int PEQ = 0, int OPEN = 0>
 __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   pdl_begin();
-  using T = Tile<DIM, FINAL, PEQ>;
+  using T = Tile<DIM, FINAL, PEQ, OPEN>;
   using RB = typename T::template R<T::HB>;
   using RJ = typename T::template R<T::HJ>;
   using RE = typename T::template R<T::HE>;
@@ -340,13 +347,23 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   const int tz = bid / (ntx * nty);
   const int x0 = tx * T::OX, y0 = ty * T::OY, z0 = tz * T::OZ;
 
-  // global interior index of a tile-relative coordinate (periodic; tiles
-  // may overhang the grid by up to one tile minus a cell, halos by HB)
+  // global interior index of a tile-relative coordinate (periodic, or on
+  // an open axis clamped to the interior cell next to the face; tiles may
+  // overhang the grid by up to one tile minus a cell, halos by HB)
+  auto coord = [&](int gc, int n, int open, int reach) {
+    if (OPEN && open) return gc < 0 ? 0 : (gc >= n ? n - 1 : gc);
+    return wrap_near(gc, n, reach);
+  };
   auto gidx = [&](int lx, int ly, int lz) {
-    const int ii = wrap_near(x0 + lx, g.nx, T::OX + T::HB);
-    const int jj = DIM == 2 ? 0 : wrap_near(y0 + ly, g.ny, T::OY + T::HB);
-    const int kk = wrap_near(z0 + lz, g.nz, T::OZ + T::HB);
+    const int ii = coord(x0 + lx, g.nx, g.open[0], T::OX + T::HB);
+    const int jj = DIM == 2 ? 0 : coord(y0 + ly, g.ny, g.open[1], T::OY + T::HB);
+    const int kk = coord(z0 + lz, g.nz, g.open[2], T::OZ + T::HB);
     return ii + g.nx * (jj + g.ny * kk);
+  };
+  // 1 where the derivative along an axis is kept: 0 in a cell beyond an
+  // open face of that axis
+  auto keep = [&](int gc, int n, int open) -> float {
+    return (OPEN && open && (gc < 0 || gc >= n)) ? 0.f : 1.f;
   };
 
   // B on the B region
@@ -379,12 +396,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     const int ly = (r / RJ::X) % RJ::Y - T::HJ * T::HY;
     const int lz = r / (RJ::X * RJ::Y) - T::HJ;
     const int b = (lx + T::HB) + (ly + T::HB * T::HY) * sBy + (lz + T::HB) * sBz;
-    const float dBz_dy = DIM == 2 ? 0.f : (Bz[b + sBy] - Bz[b - sBy]) * k.idy2;
-    const float dBx_dy = DIM == 2 ? 0.f : (Bx[b + sBy] - Bx[b - sBy]) * k.idy2;
-    const float dBy_dz = (By[b + sBz] - By[b - sBz]) * k.idz2;
-    const float dBx_dz = (Bx[b + sBz] - Bx[b - sBz]) * k.idz2;
-    const float dBz_dx = (Bz[b + 1] - Bz[b - 1]) * k.idx2;
-    const float dBy_dx = (By[b + 1] - By[b - 1]) * k.idx2;
+    const float kx = keep(x0 + lx, g.nx, g.open[0]), kz = keep(z0 + lz, g.nz, g.open[2]);
+    const float ky = DIM == 2 ? 1.f : keep(y0 + ly, g.ny, g.open[1]);
+    const float dBz_dy = DIM == 2 ? 0.f : ky * (Bz[b + sBy] - Bz[b - sBy]) * k.idy2;
+    const float dBx_dy = DIM == 2 ? 0.f : ky * (Bx[b + sBy] - Bx[b - sBy]) * k.idy2;
+    const float dBy_dz = kz * (By[b + sBz] - By[b - sBz]) * k.idz2;
+    const float dBx_dz = kz * (Bx[b + sBz] - Bx[b - sBz]) * k.idz2;
+    const float dBz_dx = kx * (Bz[b + 1] - Bz[b - 1]) * k.idx2;
+    const float dBy_dx = kx * (By[b + 1] - By[b - 1]) * k.idx2;
     Jx[r] = dBz_dy - dBy_dz;
     Jy[r] = dBx_dz - dBz_dx;
     Jz[r] = dBy_dx - dBx_dy;
@@ -411,19 +430,21 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     }
     const float jx = Jx[jc], jy = Jy[jc], jz = Jz[jc];
     const float ux = jx - mi.y, uy = jy - mi.z, uz = jz - mi.w;
-    const float gpx = (pe[jc + 1] - pe[jc - 1]) * k.idx2;
-    const float gpy = DIM == 2 ? 0.f : (pe[jc + sJy] - pe[jc - sJy]) * k.idy2;
-    const float gpz = (pe[jc + sJz] - pe[jc - sJz]) * k.idz2;
-    float lx_ = (Jx[jc + 1] + Jx[jc - 1] - 2.f * jx) * k.ilx +
-                (Jx[jc + sJz] + Jx[jc - sJz] - 2.f * jx) * k.ilz;
-    float ly_ = (Jy[jc + 1] + Jy[jc - 1] - 2.f * jy) * k.ilx +
-                (Jy[jc + sJz] + Jy[jc - sJz] - 2.f * jy) * k.ilz;
-    float lz_ = (Jz[jc + 1] + Jz[jc - 1] - 2.f * jz) * k.ilx +
-                (Jz[jc + sJz] + Jz[jc - sJz] - 2.f * jz) * k.ilz;
+    const float qx = keep(x0 + lx, g.nx, g.open[0]), qz = keep(z0 + lz, g.nz, g.open[2]);
+    const float qy = DIM == 2 ? 1.f : keep(y0 + ly, g.ny, g.open[1]);
+    const float gpx = qx * (pe[jc + 1] - pe[jc - 1]) * k.idx2;
+    const float gpy = DIM == 2 ? 0.f : qy * (pe[jc + sJy] - pe[jc - sJy]) * k.idy2;
+    const float gpz = qz * (pe[jc + sJz] - pe[jc - sJz]) * k.idz2;
+    float lx_ = qx * (Jx[jc + 1] + Jx[jc - 1] - 2.f * jx) * k.ilx +
+                qz * (Jx[jc + sJz] + Jx[jc - sJz] - 2.f * jx) * k.ilz;
+    float ly_ = qx * (Jy[jc + 1] + Jy[jc - 1] - 2.f * jy) * k.ilx +
+                qz * (Jy[jc + sJz] + Jy[jc - sJz] - 2.f * jy) * k.ilz;
+    float lz_ = qx * (Jz[jc + 1] + Jz[jc - 1] - 2.f * jz) * k.ilx +
+                qz * (Jz[jc + sJz] + Jz[jc - sJz] - 2.f * jz) * k.ilz;
     if (DIM == 3) {
-      lx_ += (Jx[jc + sJy] + Jx[jc - sJy] - 2.f * jx) * k.ily;
-      ly_ += (Jy[jc + sJy] + Jy[jc - sJy] - 2.f * jy) * k.ily;
-      lz_ += (Jz[jc + sJy] + Jz[jc - sJy] - 2.f * jz) * k.ily;
+      lx_ += qy * (Jx[jc + sJy] + Jx[jc - sJy] - 2.f * jx) * k.ily;
+      ly_ += qy * (Jy[jc + sJy] + Jy[jc - sJy] - 2.f * jy) * k.ily;
+      lz_ += qy * (Jz[jc + sJy] + Jz[jc - sJy] - 2.f * jz) * k.ily;
     }
     float ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx_;
     float ey = ((uz * bx - ux * bz) - gpy) * inv + k.eta * jy - k.eta_h * ly_;
@@ -439,11 +460,40 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     }
     if (FINAL) {
       // interior cell of the tile: write E, B into the padded gather array
-      // at the cell and at each of its ghost images
+      // at the cell and at each of its ghost images (with OPEN also the
+      // ghost cells beyond the faces this tile touches)
       const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-      if (gx < g.nx && (DIM == 2 || gy < g.ny) && gz < g.nz) {
+      auto owns = [&](int gc, int org, int ext, int n, int open) {
+        if (gc >= org && gc < org + ext && gc < n) return true;
+        return OPEN && open && ((gc == -1 && org == 0) || (gc == n && org + ext >= n));
+      };
+      const bool mine = OPEN ? owns(gx, x0, T::OX, g.nx, g.open[0]) &&
+                                   (DIM == 2 || owns(gy, y0, T::OY, g.ny, g.open[1])) &&
+                                   owns(gz, z0, T::OZ, g.nz, g.open[2])
+                             : (gx < g.nx && (DIM == 2 || gy < g.ny) && gz < g.nz);
+      if (mine) {
         const float4 e0 = make_float4(ex, ey, ez, bx);
         const float4 e1 = make_float4(by, bz, 0.f, 0.f);
+        if (OPEN) {
+          int xs[5], ys[5], zs[5];
+          const int nxs = (g.open[0] || gx < 0 || gx >= g.nx) ? (xs[0] = gx + kGhost, 1)
+                                                               : axis_images(gx, g.nx, xs);
+          int nys = 1;
+          ys[0] = 0;
+          if (DIM == 3)
+            nys = (g.open[1] || gy < 0 || gy >= g.ny) ? (ys[0] = gy + kGhost, 1)
+                                                      : axis_images(gy, g.ny, ys);
+          const int nzs = (g.open[2] || gz < 0 || gz >= g.nz) ? (zs[0] = gz + kGhost, 1)
+                                                               : axis_images(gz, g.nz, zs);
+          for (int a3 = 0; a3 < nzs; ++a3)
+            for (int a2 = 0; a2 < nys; ++a2)
+              for (int a1 = 0; a1 < nxs; ++a1) {
+                const int p = xs[a1] + (DIM == 2 ? 0 : ys[a2] * g.sy) + zs[a3] * g.sz;
+                a.EB[2 * p] = e0;
+                a.EB[2 * p + 1] = e1;
+              }
+          continue;
+        }
         if (single_image(g, gx, gy, gz)) {
           const int p = voxel_of(g, gx, gy, gz);
           a.EB[2 * p] = e0;
@@ -1012,17 +1062,18 @@ FieldConsts field_consts(const hv_ctx *c) {
   return k;
 }
 
-template <int DIM, int FINAL, int PEQ = 0>
+template <int DIM, int FINAL, int PEQ = 0, int OPEN = 0>
 cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
-  using T = Tile<DIM, FINAL, PEQ>;
+  using T = Tile<DIM, FINAL, PEQ, OPEN>;
   const size_t smem = T::smem_floats * sizeof(float);
   static std::atomic<uint64_t> attr_set{0};
-  cudaError_t e = set_smem_once(stage_kernel<DIM, FINAL, PEQ>, smem, attr_set);
+  cudaError_t e = set_smem_once(stage_kernel<DIM, FINAL, PEQ, OPEN>, smem, attr_set);
   if (e != cudaSuccess) return e;
   const int ntx = (c->g.nx + T::OX - 1) / T::OX;
   const int nty = DIM == 2 ? 1 : (c->g.ny + T::OY - 1) / T::OY;
   const int ntz = (c->g.nz + T::OZ - 1) / T::OZ;
-  return launch_pdl(stage_kernel<DIM, FINAL, PEQ>, ntx * nty * ntz, 256, smem, c->stream, a);
+  return launch_pdl(stage_kernel<DIM, FINAL, PEQ, OPEN>, ntx * nty * ntz, 256, smem, c->stream,
+                    a);
 }
 
 // ----------------------------------------------------------------------------
@@ -1045,12 +1096,17 @@ __global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, f
     }
     wb += 0.5 * ((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) * vc;
     ch += (double)mom[c].x * vc;
-    const int xp = wrapn(i + 1, g.nx) + g.nx * (j + g.ny * kk);
-    const int xm = wrapn(i - 1, g.nx) + g.nx * (j + g.ny * kk);
-    const int yp = i + g.nx * (wrapn(j + 1, g.ny) + g.ny * kk);
-    const int ym = i + g.nx * (wrapn(j - 1, g.ny) + g.ny * kk);
-    const int zp = i + g.nx * (j + g.ny * wrapn(kk + 1, g.nz));
-    const int zm = i + g.nx * (j + g.ny * wrapn(kk - 1, g.nz));
+    // neighbours: periodic images, or on an open axis the cell itself beyond
+    // the face (the ghost copies its interior neighbour)
+    auto nb = [](int c, int n, int open) {
+      return open ? (c < 0 ? 0 : (c >= n ? n - 1 : c)) : wrapn(c, n);
+    };
+    const int xp = nb(i + 1, g.nx, g.open[0]) + g.nx * (j + g.ny * kk);
+    const int xm = nb(i - 1, g.nx, g.open[0]) + g.nx * (j + g.ny * kk);
+    const int yp = i + g.nx * (nb(j + 1, g.ny, g.open[1]) + g.ny * kk);
+    const int ym = i + g.nx * (nb(j - 1, g.ny, g.open[1]) + g.ny * kk);
+    const int zp = i + g.nx * (j + g.ny * nb(kk + 1, g.nz, g.open[2]));
+    const int zm = i + g.nx * (j + g.ny * nb(kk - 1, g.nz, g.open[2]));
     const double dv = ((double)B[xp].x - B[xm].x) * k.idx2 + ((double)B[yp].y - B[ym].y) * k.idy2 +
                       ((double)B[zp].z - B[zm].z) * k.idz2;
     md = fmax(md, fabs(dv));
@@ -1212,7 +1268,7 @@ cudaError_t launch_field_stage(hv_ctx *c, const float4 *Bin, const float4 *Bbase
   return launch_pdl(stage3d_kernel, blocks, st3d::kThreads, smem, c->stream, a);
 }
 
-bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0; }
+bool fused_substeps(const hv_ctx *c) { return c->g.dim2 != 0 && !c->g.any_open; }
 
 cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h) {
   SubArgs a;
@@ -1331,6 +1387,8 @@ cudaError_t launch_field_stage_tiled(hv_ctx *c, const float4 *Bin, const float4 
   a.pcoef = 0.f;
   a.B0 = c->B0ext;
   c->launches++;
+  if (c->g.any_open)
+    return c->g.dim2 ? launch_stage_t<2, 0, 0, 1>(c, a) : launch_stage_t<3, 0, 0, 1>(c, a);
   return c->g.dim2 ? launch_stage_t<2, 0>(c, a) : launch_stage_t<3, 0>(c, a);
 }
 
@@ -1364,6 +1422,8 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
   cudaError_t e;
   if (c->p.pe_eq)
     e = c->g.dim2 ? launch_stage_t<2, 1, 1>(c, a) : launch_stage_t<3, 1, 1>(c, a);
+  else if (c->g.any_open)
+    e = c->g.dim2 ? launch_stage_t<2, 1, 0, 1>(c, a) : launch_stage_t<3, 1, 0, 1>(c, a);
   else
     e = c->g.dim2 ? launch_stage_t<2, 1>(c, a) : launch_stage_t<3, 1>(c, a);
   if (e != cudaSuccess) return e;

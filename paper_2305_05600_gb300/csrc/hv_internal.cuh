@@ -115,7 +115,15 @@ struct Geom {
   int ntx, nty, ntz;    // tiles per axis
   int ntiles;
   int tlog;             // log2(cells per tile)
+  int open[3];          // 1: the axis has open faces (Sec. 2.3), 0: periodic
+  int any_open;
 };
+
+// Voxel index of an ion that left through an open face: it stays in its slot,
+// is skipped by the push and is sorted behind the live ions.
+constexpr int kDeadVox = -1;
+// Error bit: injection found no free particle slot (hv_reserve_ions).
+constexpr int kErrCapacity = 16;
 
 // Tile extents of the supercell order: 16x16 cells in the x-z layout,
 // 8x8x8 cells in 3D (cells per tile a power of two).
@@ -179,6 +187,34 @@ __host__ __device__ __forceinline__ int axis_images(int i, int n, int *out) {
   return c;
 }
 
+// Padded voxels whose deposits belong to interior coordinate i: the
+// periodic images, or on an open axis the cell itself plus, next to a face,
+// the ghost layers beyond it (deposits beyond an open face fold onto the
+// cell next to it).
+__host__ __device__ __forceinline__ int axis_sources(int i, int n, int open, int *out) {
+  if (!open) return axis_images(i, n, out);
+  int c = 0;
+  out[c++] = i + kGhost;
+  if (i == 0) {
+    out[c++] = 0;
+    out[c++] = 1;
+  }
+  if (i == n - 1) {
+    out[c++] = n + kGhost;
+    out[c++] = n + kGhost + 1;
+  }
+  return c;
+}
+
+// Padded voxels that hold interior coordinate i in the gather array: the
+// periodic images, or on an open axis the cell itself only (the ghost layer
+// holds the ghost cell's own E).
+__host__ __device__ __forceinline__ int axis_holders(int i, int n, int open, int *out) {
+  if (!open) return axis_images(i, n, out);
+  out[0] = i + kGhost;
+  return 1;
+}
+
 // Particle SoA for one species, one buffer set.  Arrays are 256-byte aligned
 // and have capacity rounded up to a multiple of 4 elements.
 struct Soa {
@@ -198,6 +234,9 @@ struct Species {
   size_t bucket_bytes;  // and every ion's rank in its key
   int32_t *wcnt;        // windowed sort: per tile and window slot, the count
   size_t wcnt_bytes;    // and then the prefix over earlier tiles
+  int *n_used;          // open faces: slots in use on the device (live ions
+                        // and dead slots not yet sorted out, then injected
+                        // ions); n is then the slot capacity
   Soa buf[2];
   int cur;              // index of the live buffer set
   void *base[2];        // allocation bases
@@ -213,6 +252,13 @@ struct PushConsts {
 };
 
 struct SortScratch;
+
+// A drifting Maxwellian injected through an open face (face 0 -x, 1 +x, 2 -y,
+// 3 +y, 4 -z, 5 +z): density n, flow u, temperature T, ion weight w.
+struct InjectFace {
+  int species, face;
+  double n, u[3], T, w;
+};
 
 // Learned moment filter: packed bf16 weights (W1 [16][48], W2 [16][144],
 // W3 [8][144], B matrices stored [n][K]), biases b1[16] b2[16] b3[8], channel
@@ -237,6 +283,10 @@ struct hv_ctx {
   int presorted;        // the current step's sort was issued on `side`
   int since_sort;       // pushes since the last sort (-1: the ions are in
                         // load order, not sorted yet)
+  hv::InjectFace inject[6 * hv::kMaxSpecies];  // injection through open faces
+  int ninject;
+  int *inj_scratch;     // per face cell counts and offsets of an injection
+  int inj_cells;
   int device;
   double vc;
   // grids (device)
@@ -294,6 +344,9 @@ hv_status cuda_fail(cudaError_t e, const char *what);
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 
+// injection through open faces (Sec. 2.3), after the push of a step
+cudaError_t launch_injection(hv_ctx *c, const InjectFace &f);
+
 // kernels launchers (return cudaGetLastError of the launch)
 cudaError_t launch_push(hv_ctx *c, int species, int mode);
 cudaError_t launch_moments(hv_ctx *c, int init);
@@ -320,7 +373,7 @@ cudaError_t launch_adam(hv_ctx *c, float *P, float *grad, float *m1, float *m2, 
                         const FilterParams &fp, __nv_bfloat16 *wt);
 cudaError_t launch_interleave4(hv_ctx *c, int nb, const float *in, float4 *out);
 // whole explicit-midpoint substeps fused in one kernel (x-z layout)
-bool fused_substeps(const hv_ctx *c);
+bool fused_substeps(const hv_ctx *c);  // (not with open faces)
 cudaError_t launch_substep(hv_ctx *c, const float4 *Bin, float4 *Bout, float h);
 cudaError_t launch_diag(hv_ctx *c);
 int grid_reduce_blocks(int device);

@@ -51,6 +51,7 @@ constexpr int kGroup = HV_PUSH_GROUP;  // ions a lane moves with one vector acce
 struct PushArgs {
   Soa s;
   int64_t n;
+  const int *n_dev;     // slots in use, read on the device (open faces), or null
   const int *tile_off;  // [ntiles + 1]
   const float4 *EB;
   float4 *acc;       // per-target accumulator
@@ -426,6 +427,7 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
   constexpr int NT = Shape<DIM, SHAPE>::NT;
   const Geom &g = a.g;
   const int vox0 = vox;
+  if (vox0 == kDeadVox) return INT_MIN;  // left through an open face earlier
   if (vox0 < g.vlo || vox0 >= g.vhi) {
     atomicOr(a.err, kErrIndex);
     return INT_MIN;
@@ -554,13 +556,17 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
       shy = rebase(hy);
       my = rebase(nyo);
     }
-    // new cell, wrapped into the interior
+    // new cell, wrapped into the interior (periodic), or the ion leaves
+    // through an open face (Sec. 2.3) and its slot is marked dead
     const int i1 = ip - kGhost + mx, k1 = kp - kGhost + mz;
     const int j1 = DIM == 2 ? 0 : jp - kGhost + my;
     const int iw = i1 < 0 ? i1 + g.nx : (i1 >= g.nx ? i1 - g.nx : i1);
     const int kw = k1 < 0 ? k1 + g.nz : (k1 >= g.nz ? k1 - g.nz : k1);
     const int jw = DIM == 2 ? 0 : (j1 < 0 ? j1 + g.ny : (j1 >= g.ny ? j1 - g.ny : j1));
     vox = voxel_of(g, iw, jw, kw);
+    if (g.any_open && ((g.open[0] && iw != i1) || (g.open[2] && kw != k1) ||
+                       (DIM == 3 && g.open[1] && jw != j1)))
+      vox = kDeadVox;
     ox = nxo;
     if (DIM == 3) oy = nyo;
     oz = nzo;
@@ -680,7 +686,8 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   const int part = blockIdx.x % kPushSplit;
   const int ti = tile % g.ntx, tj = (tile / g.ntx) % g.nty, tk = tile / (g.ntx * g.nty);
   const int i0 = ti * W::TX, j0 = tj * W::TY, k0 = tk * W::TZ;
-  const int64_t nq = (a.n + 3) >> 2;
+  const int64_t n_ions = a.n_dev ? (int64_t)*a.n_dev : a.n;
+  const int64_t nq = (n_ions + 3) >> 2;
   const int64_t qa = tile == 0 ? 0 : (int64_t)a.tile_off[tile] >> 2;
   const int64_t qe = tile == g.ntiles - 1 ? nq : (int64_t)a.tile_off[tile + 1] >> 2;
   const int64_t nst = qe > qa ? (qe - qa + TQ - 1) / TQ : 0;  // staging tiles of the tile
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
       ldv<kGroup>(&T[SL::VY][e0], vy);
       ldv<kGroup>(&T[SL::VZ][e0], vz);
       ldv<kGroup>(&T[SL::W][e0], ww);
-      const int64_t nvalid = a.n - (q0 * 4 + e0);  // ions of the group that exist
+      const int64_t nvalid = n_ions - (q0 * 4 + e0);  // ions of the group that exist
 #pragma unroll
       for (int p = 0; p < kGroup; ++p) {
         if (p >= nvalid) continue;
@@ -858,6 +865,7 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   PushArgs a;
   a.s = sp.buf[sp.cur];
   a.n = sp.n;
+  a.n_dev = c->g.any_open ? sp.n_used : nullptr;
   a.tile_off = sp.tile_off;
   a.EB = gather_array(c);
   a.acc = c->acc;

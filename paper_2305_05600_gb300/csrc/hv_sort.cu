@@ -802,10 +802,21 @@ __global__ void __launch_bounds__(256) wsort_scatter_flat_kernel(Geom g, Soa in,
 }
 
 // General path: keys, gather by permutation, tile ranges from sorted keys.
+// (a dead slot, open faces, takes the key after the last one: behind every
+// live ion)
 __global__ void ion_keys_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *keys) {
+  const int dead_key = g.ntiles << g.tlog;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    keys[i] = ion_key(g, vox[i]);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int v = vox[i];
+    keys[i] = v == kDeadVox ? dead_key : ion_key(g, v);
+  }
+}
+
+// slots in use after a sort with open faces: the live ions (the dead sorted
+// behind them)
+__global__ void live_count_kernel(const int *tile_off, int ntiles, int *n_used) {
+  *n_used = tile_off[ntiles];
 }
 
 __global__ void gather_kernel(Soa in, Soa out, const int32_t *perm, int64_t n) {
@@ -940,13 +951,18 @@ hv_status sort_general(hv_ctx *c, Species &sp, cudaStream_t st) {
   ion_keys_kernel<<<eb, 256, 0, st>>>(g, src.cell, sp.n, s->v[1]);
   int32_t *perm = nullptr, *skeys = nullptr;
   int64_t launches = 1;
-  cudaError_t e = radix_perm(s->v[1], sp.n, nkeys, s, st, &perm, &launches, &skeys);
+  cudaError_t e = radix_perm(s->v[1], sp.n, nkeys + (g.any_open ? 1 : 0), s, st, &perm,
+                             &launches, &skeys);
   if (e == cudaSuccess) {
     gather_kernel<<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(src, sp.buf[sp.cur ^ 1], perm,
                                                                   sp.n);
     tile_bounds_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(skeys, sp.n, g.tlog, g.ntiles,
                                                               sp.tile_off_next);
     launches += 2;
+    if (g.any_open) {
+      live_count_kernel<<<1, 1, 0, st>>>(sp.tile_off_next, g.ntiles, sp.n_used);
+      launches++;
+    }
     e = cudaGetLastError();
   }
   c->launches += launches;
@@ -961,7 +977,9 @@ int sort_window(const hv_ctx *c) { return c->g.dim2 ? SortWin<2>::H : SortWin<3>
 hv_status sort_species(hv_ctx *c, int sidx, cudaStream_t stream) {
   Species &sp = c->sp[sidx];
   if (sp.n == 0) return HV_OK;
-  const bool windowed = c->since_sort >= 0 && c->since_sort <= sort_window(c);
+  // (open faces: dead slots must be sorted out, which the general path does)
+  const bool windowed =
+      !c->g.any_open && c->since_sort >= 0 && c->since_sort <= sort_window(c);
   hv_status st;
   if (windowed)
     st = c->g.dim2 ? sort_windowed<2>(c, sp, stream) : sort_windowed<3>(c, sp, stream);

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
                 ("sort_every", ctypes.c_int32), ("field_smooth_passes", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("pe_eq", ctypes.c_int32),
                 ("ohm_model", ctypes.c_int32), ("kappa", ctypes.c_double),
-                ("relativistic", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("relativistic", ctypes.c_int32), ("open_faces", ctypes.c_int32),
                 ("c_light", ctypes.c_double)]
 
 
@@ -86,7 +86,8 @@ EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_mo
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
            "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
            "hv_filter_get_params", "hv_electron_pressure", "hv_get_tile_offsets",
-           "hv_inject_error", "hv_error_status", "hv_set_external_field", "hv_last_error"]
+           "hv_inject_error", "hv_error_status", "hv_set_external_field", "hv_reserve_ions", "hv_set_injection",
+           "hv_last_error"]
 
 
 def library_path() -> str:
@@ -117,6 +118,9 @@ def lib():
         L.hv_inject_error.argtypes = [P, I32]
         L.hv_error_status.argtypes = [I32]
         L.hv_set_external_field.argtypes = [P, P]
+        L.hv_reserve_ions.argtypes = [P, I32, I64]
+        L.hv_set_injection.argtypes = [P, I32, I32, ctypes.c_double, P, ctypes.c_double,
+                                       ctypes.c_double]
         L.hv_set_filter.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
         L.hv_filter_moments.argtypes = [P, P, P, ctypes.c_int]
         L.hv_filter_train_init.argtypes = [P, P, P]
@@ -182,8 +186,8 @@ def params_from(d: dict) -> Params:
                   int(d.get("smooth_passes", 0)), int(d.get("sort_every", 0)),
                   int(d.get("field_smooth_passes", 0)),
                   int(d.get("seed", 0)), int(d.get("pe_eq", 0)), int(d.get("ohm_model", 0)),
-                  float(d.get("kappa", 0.0)), int(d.get("relativistic", 0)), 0,
-                  float(d.get("c_light", 0.0)))
+                  float(d.get("kappa", 0.0)), int(d.get("relativistic", 0)),
+                  int(d.get("open_faces", 0)), float(d.get("c_light", 0.0)))
 
 
 def _ptr(a):
@@ -251,6 +255,18 @@ def hv_set_external_field(ctx: Ctx, B0ext):
     if b.size != 3 * p.nx * p.ny * p.nz:
         raise ValueError("the external field must have 3*nx*ny*nz values")
     _check(lib().hv_set_external_field(ctx.handle, b.ctypes.data))
+
+
+def hv_reserve_ions(ctx: Ctx, species: int, capacity: int):
+    """Particle slots for ions injected through open faces."""
+    _check(lib().hv_reserve_ions(ctx.handle, int(species), int(capacity)))
+
+
+def hv_set_injection(ctx: Ctx, species: int, face: int, n: float, u, T: float, w: float):
+    """Drifting Maxwellian injected through an open face every step."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(3))
+    _check(lib().hv_set_injection(ctx.handle, int(species), int(face), float(n),
+                                  uu.ctypes.data, float(T), float(w)))
 
 
 def hv_load_ions(ctx: Ctx, species: int, q: float, m: float, cell, off3, v3, w):

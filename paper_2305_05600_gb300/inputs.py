@@ -501,3 +501,28 @@ def harris_device(nx=512, ny=256, nz=256, ppc=32, dx=0.5, seed=3000, steps=1000,
     return Workload("harris3d", p, B.astype(np.float32), [sp], steps,
                     notes=f"{nx}x{ny}x{nz} cells, {ppc} ppc, dx={dx}, guide={guide}, seed={seed}, "
                           f"generated on the GPU")
+
+
+def drifting_slab(nx=32, ny=1, nz=16, ppc=32, dx=0.5, U=0.4, Ti=0.04, Te=0.02, Bz=0.3,
+                  seed=90, dt=0.02, nsub=4, shape="qs", open_faces=1, sort_every=0,
+                  w_scale=1.0) -> Workload:
+    """A uniform plasma flowing at U along x through a box (open faces on the
+    axes in ``open_faces``, bits x = 1, y = 2, z = 4) in the field
+    B = (1, 0, Bz), with ion temperature Ti: the workload of the open-face
+    tests.  Weights are n V_c / ppc times w_scale."""
+    dy = dx if ny > 1 else 1.0
+    p = base_params(nx, ny, nz, dx, dy, dx, dt, nsub, Te=Te, shape=shape, sort_every=sort_every,
+                    eta=1e-3, eta_h=1e-4)
+    p["open_faces"] = open_faces
+    rng = _rng(seed)
+    B = np.zeros((3, nz, ny, nx))
+    B[0] = 1.0
+    B[2] = Bz
+    ncell = nx * ny * nz
+    cell, off = load_cells(p, np.full(ncell, ppc), rng, (nx, ny, nz))
+    n = cell.shape[0]
+    v = np.sqrt(Ti) * _box_muller(rng, (3, n))
+    v[0] += U
+    w = np.full(n, dx * dy * dx / ppc * w_scale)
+    return Workload("drifting_slab", p, B.astype(np.float32), [_finish(cell, off, v, w)], 1,
+                    notes=f"{nx}x{ny}x{nz} cells, {ppc} ppc, U={U}, open_faces={open_faces}")

@@ -116,3 +116,21 @@ def test_noalloc_binding_rejects_host_tensors():
     perm = torch.zeros(8, dtype=torch.int32)
     with pytest.raises(TypeError):
         hv.hv_sort_keys_noalloc(keys, 4, perm)
+
+
+@pytest.mark.parametrize("bad", [dict(open_faces=8), dict(open_faces=2),
+                                 dict(open_faces=1, pe_eq=1), dict(open_faces=1, smooth_passes=1),
+                                 dict(open_faces=4, ohm_model=1),
+                                 dict(open_faces=1, relativistic=1, c_light=10.0)])
+def test_open_faces_rejected_outside_their_scope(bad):
+    """Open faces (Sec. 2.3): bits 1, 2, 4 only, an open axis needs more than
+    one cell (the 2D layout's y axis has one), hybrid Ohm's law with the
+    equation of state, no smoothing, no relativistic push."""
+    rc, h = _init_status(_params(**bad))
+    assert rc == hv.HV_EINVAL and not h
+
+
+def test_capacity_error_bit_maps_to_enomem():
+    assert hv.hv_error_status(16) == hv.HV_ENOMEM
+    assert "slot" in hv.hv_last_error()
+    assert hv.hv_error_status(16 | 8) == hv.HV_ETIMEOUT
