@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="harris2d",
                     choices=["harris2d", "harris2d_small", "alfven2d", "beam3d_small", "beam3d",
-                             "beam3d_2ppc", "harris3d", "harris3d_quarter", "ebeam2d"])
+                             "beam3d_2ppc", "harris3d", "harris3d_quarter", "ebeam2d",
+                             "slab2d_open"])
     ap.add_argument("--shape", default="qs", choices=["qs", "cic", "ngp"])
     ap.add_argument("--sort-every", type=int, default=None,
                     help="override the workload's sort interval")
@@ -81,6 +82,10 @@ def make_workload(name, shape, seed_offset=0):
         return I.harris_device(nx=256, ny=128, nz=128, shape=shape, seed=3000 + seed_offset)
     if name == "ebeam2d":  # relativistic electron beam, resistive background, 640x320, 13.1M
         return I.ebeam2d(shape=shape, seed=8000 + seed_offset)
+    if name == "slab2d_open":  # plasma flowing through faces open in x, injection, 52.4M ions
+        return I.drifting_slab(nx=1024, nz=512, ppc=100, dx=0.25, U=0.4, Ti=0.04, Te=0.02,
+                               dt=0.02, nsub=10, shape=shape, open_faces=1, sort_every=4,
+                               seed=9000 + seed_offset)
     raise ValueError(name)
 
 
@@ -474,6 +479,10 @@ def run_e2e(args, wl, world, dev, stream):
     t0 = time.perf_counter()
     for i, (q, m, c, o, v, w) in enumerate(hsp):
         hv.hv_load_ions(ctx, i, q, m, c, o, v, w)
+        if wl.reserve > 0.0:
+            hv.hv_reserve_ions(ctx, i, int(wl.reserve * c.shape[0]) + 1024)
+    for s_idx, face, n_b, u_b, T_b, w_b in wl.inject:
+        hv.hv_set_injection(ctx, s_idx, face, n_b, u_b, T_b, w_b)
     for _ in range(steps):
         hv.hv_step(ctx, 1)
         hv.hv_diag(ctx)

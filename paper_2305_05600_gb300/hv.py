@@ -492,4 +492,8 @@ def load_workload(wl, stream=None, **override) -> Ctx:
     ctx = hv_init_grid(p, wl.B0, stream)
     for s_idx, s in enumerate(wl.species):
         hv_load_ions(ctx, s_idx, s.q, s.m, s.cell, s.off, s.v, s.w)
+        if getattr(wl, "reserve", 0.0) > 0.0:
+            hv_reserve_ions(ctx, s_idx, int(wl.reserve * s.n) + 1024)
+    for s_idx, face, n, u, T, w in getattr(wl, "inject", []):
+        hv_set_injection(ctx, s_idx, face, n, u, T, w)
     return ctx

@@ -55,6 +55,10 @@ class Workload:
     species: list = field(default_factory=list)
     steps: int = 1
     notes: str = ""
+    # open faces: (species, face, n, u, T, w) injected every step, and the
+    # particle slots to reserve per species as a multiple of its ions
+    inject: list = field(default_factory=list)
+    reserve: float = 0.0
 
     @property
     def n_particles(self) -> int:
@@ -524,5 +528,13 @@ def drifting_slab(nx=32, ny=1, nz=16, ppc=32, dx=0.5, U=0.4, Ti=0.04, Te=0.02, B
     v = np.sqrt(Ti) * _box_muller(rng, (3, n))
     v[0] += U
     w = np.full(n, dx * dy * dx / ppc * w_scale)
-    return Workload("drifting_slab", p, B.astype(np.float32), [_finish(cell, off, v, w)], 1,
-                    notes=f"{nx}x{ny}x{nz} cells, {ppc} ppc, U={U}, open_faces={open_faces}")
+    wl = Workload("drifting_slab", p, B.astype(np.float32), [_finish(cell, off, v, w)], 1,
+                  notes=f"{nx}x{ny}x{nz} cells, {ppc} ppc, U={U}, open_faces={open_faces}")
+    # the same drifting Maxwellian enters through every open face
+    w_inj = float(np.float32(dx * dy * dx / ppc * w_scale))
+    for a in range(3):
+        if (open_faces >> a) & 1:
+            u = [U, 0.0, 0.0]
+            wl.inject += [(0, 2 * a, 1.0, u, Ti, w_inj), (0, 2 * a + 1, 1.0, u, Ti, w_inj)]
+    wl.reserve = 1.25 if open_faces else 0.0
+    return wl
