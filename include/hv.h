@@ -133,7 +133,8 @@ typedef struct {
  * stream; a sort issued ahead of its step on the library's side stream is
  * timed with events on that stream, so ms_sort is the sorts' own duration
  * even where they overlap the field phase (ms_field then includes the
- * overlap). */
+ * overlap).  Injection through open faces counts with the moment post
+ * (ms_moments, n_moments), so that ms_push / n_push is the push kernel's. */
 typedef struct {
   double ms_sort, ms_push, ms_moments, ms_field, ms_ohm, ms_diag;
   int64_t n_sort, n_push, n_moments, n_field, n_ohm, n_diag; /* launches */

@@ -761,15 +761,16 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       if (e != cudaSuccess) return cuda_fail(e, "push");
     }
     if (c->since_sort >= 0) c->since_sort++;
-    // ions entering through open faces join after the push (Sec. 2.3)
-    for (int q = 0; q < c->ninject; ++q) {
-      cudaError_t e = launch_injection(c, c->inject[q]);
-      if (e != cudaSuccess) return cuda_fail(e, "injection");
-    }
     if (ps) {
       cudaEventRecord(ev.e[2], c->stream);
       ev.launches[1] = c->launches - l0;
       l0 = c->launches;
+    }
+    // ions entering through open faces join after the push (Sec. 2.3); the
+    // profile counts them with the moment post
+    for (int q = 0; q < c->ninject; ++q) {
+      cudaError_t e = launch_injection(c, c->inject[q]);
+      if (e != cudaSuccess) return cuda_fail(e, "injection");
     }
     // The next step's sort needs only the pushed ions, not the fields: when
     // it is due and runs in this call, issue it now on the side stream so
