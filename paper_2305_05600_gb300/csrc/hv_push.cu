@@ -505,8 +505,9 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
       ty *= ig;
       tz *= ig;
     }
-    // 2 * rn(1/x) equals rn(2/x): scaling by 2 is exact
-    const float f = 2.f * __frcp_rn(1.f + (tx * tx + ty * ty + tz * tz));
+    // 2 / (1 + |t|^2) by the fast approximate division: the divisor is at
+    // least 1, where its error stays within 2 ulp
+    const float f = __fdividef(2.f, 1.f + (tx * tx + ty * ty + tz * tz));
     const float sx = f * tx, sy = f * ty, sz = f * tz;
     const float vpx = vmx + (vmy * tz - vmz * ty);
     const float vpy = vmy + (vmz * tx - vmx * tz);
@@ -628,6 +629,7 @@ struct Run {
     bool cut = lane == 31 || knext != key;  // a segment ends at this lane
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (__all_sync(kFull, cut)) break;  // every segment is closed: nothing left to combine
       const bool cut_o = __shfl_down_sync(kFull, cut, o);
       const bool take = !cut && lane + o < 32;
 #pragma unroll
