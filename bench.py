@@ -5,7 +5,7 @@ Harris-sheet workload (1024x512 cells, dx = 0.25 d_i, 100 ions per cell,
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one pass of the whole hot path (sort every 4 steps, gather +
+One step = one pass of the whole hot path (sort every 8 steps, gather +
 Boris push + half-step deposit + move, moment post, 10 field subcycles of
 two Ohm/Faraday stages, final Ohm).  Under torchrun each rank runs an
 independent replica (the path is not sharded); rank 0 prints one JSON line.
@@ -61,13 +61,14 @@ def parse():
 
 def make_workload(name, shape, seed_offset=0):
     from paper_2305_05600_gb300 import inputs as I
-    # The counting sort costs about 1.1 ms per call at 1024x512 and the push
-    # loses about 0.045 ms per step of drift since the last sort; sorting
-    # every 4 steps minimises their sum (measured on GB300 for 2, 4, 8, 20).
+    # The windowed counting sort costs about 1.5 ms per call at 1024x512; the
+    # push is fastest at mid-interval, where the ions have reached the cells
+    # they were sorted by (predicted half an interval ahead).  Sorting every
+    # 8 steps minimises the sum (measured on GB300 for 4, 6, 8).
     if name == "harris2d":
-        return I.harris(shape=shape, seed=1000 + seed_offset, sort_every=4)
+        return I.harris(shape=shape, seed=1000 + seed_offset, sort_every=8)
     if name == "harris2d_small":  # ncu-sized case: 13.1M ions, > L2
-        return I.harris(nx=512, nz=256, shape=shape, seed=1000 + seed_offset, sort_every=4)
+        return I.harris(nx=512, nz=256, shape=shape, seed=1000 + seed_offset, sort_every=8)
     if name == "alfven2d":
         return I.alfven2d(shape=shape, seed=seed_offset)
     if name == "beam3d_small":

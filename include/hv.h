@@ -5,7 +5,7 @@
  *
  * One step n -> n+1 (Sec. 2.2 of the paper):
  *   [every sort_every steps: stable counting sort of the ions by supercell
- *    key (tile, then cell in the tile)]
+ *    key (tile, then cell in the tile) of their predicted cells]
  *   gather E^n, B^n at x^n with the particle shape (NGP Eq. 13, QS Eqs. 17-19,
  *   or CIC on cell centres) -> non-relativistic Boris push (Eq. 9) ->
  *   deposit n, J_i at the half-step position (App. B) -> move (Eq. 10)
@@ -74,7 +74,15 @@ typedef struct {
   double n_floor;       /* density floor n_f in Ohm's law (Sec. 2.1) */
   int32_t shape;        /* hv_shape */
   int32_t smooth_passes;/* binomial passes applied to deposited moments */
-  int32_t sort_every;   /* sort ions by cell every this many steps; 0 never */
+  int32_t sort_every;   /* sort ions by cell every this many steps; 0 never.
+                           The cell an ion is sorted by is its cell moved by
+                           at most one cell along each axis toward where it
+                           is predicted to be half a sort interval later:
+                           along an axis of more than one cell, by +1 when
+                           off + v * (sort_every * dt / Delta) >= 1 and by
+                           -1 when it is < -1 (FP32, product and sum rounded
+                           separately; the stored v, u with relativistic
+                           particles), periodically.  Not with open faces. */
   int32_t field_smooth_passes; /* binomial passes applied to copies of E^n and
                            B^n that the push gathers (the self-consistent
                            field smoothing of Sec. 2.2); the field state is
@@ -312,15 +320,17 @@ hv_status hv_filter_get_params(hv_ctx *ctx, float *params_out);
 
 /* Fill *out with the context's layout: the library keeps ions sorted
  * tile-major (supercell tile index, then the linear cell inside the tile,
- * both x fastest) whenever it sorts them, with tile extents as reported. */
+ * both x fastest, of each ion's predicted cell, see sort_every) whenever it
+ * sorts them, with tile extents as reported. */
 hv_status hv_query(const hv_ctx *ctx, hv_info_t *out);
 
 /* The ion range of every supercell tile of species `species` in the
  * library's current particle order: tile_off [ntiles + 1] (host memory)
  * receives the first ion of each tile and, last, the ion count.  After a
  * sort these are the offsets of a stable counting sort of the ions'
- * supercell keys (the key of a cell is its tile index times the cells per
- * tile plus its cell inside the tile, x fastest; hv_query gives the tile
+ * supercell keys (the key of an ion is that of its predicted cell, see
+ * sort_every; the key of a cell is its tile index times the cells per tile
+ * plus its cell inside the tile, x fastest; hv_query gives the tile
  * extents); before the first sort they split the ions evenly.  The sort is
  * an ordering device of the GPU layout (the paper prescribes none; it
  * changes results only through FP32 summation order).  Synchronises and

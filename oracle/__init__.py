@@ -392,16 +392,39 @@ def sort_stable(keys, nkeys):
     return perm, counts, offsets
 
 
-def supercell_keys(cell, nx, ny, nz, tile):
+def sort_pred_coeffs(params):
+    """The library's key-cell prediction coefficients per axis (FP32):
+    sort_every * dt / Delta, 0 on single-cell axes, with open faces and
+    without sorting (``include/hv.h``, sort_every)."""
+    p = params
+    on = p.get("sort_every", 0) > 0 and not p.get("open_faces", 0)
+    return tuple(np.float32(p["sort_every"] * p["dt"] / p[d]) if on and p[n] > 1
+                 else np.float32(0.0)
+                 for n, d in (("nx", "dx"), ("ny", "dy"), ("nz", "dz")))
+
+
+def supercell_keys(cell, nx, ny, nz, tile, off=None, v=None, pc=None):
     """Keys of the library's documented ion order (``include/hv.h``,
     hv_query / hv_get_tile_offsets), restated here so that the oracle side
     never calls the product: for linear cell c = i + nx (j + ny k) and tile
     extents (tx, ty, tz), key = tile index * (tx ty tz) + the cell's linear
-    index inside its tile, both x fastest.  The paper prescribes no ion
-    order; sorting only permutes the oracle's FP64 summation order."""
+    index inside its tile, both x fastest.  With off, v [3][n] (FP32 state)
+    and pc (sort_pred_coeffs) the key is that of the predicted cell: the
+    cell moved by one along each axis where off + v * pc (FP32, product and
+    sum rounded separately) is >= 1 or < -1, periodically.  The paper
+    prescribes no ion order; sorting only permutes the oracle's FP64
+    summation order."""
     c = np.asarray(cell, dtype=np.int64)
     tx, ty, tz = (int(t) for t in tile)
     i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    if off is not None:
+        o = np.asarray(off, dtype=np.float32)
+        w = np.asarray(v, dtype=np.float32)
+        sh = []
+        for a in range(3):
+            q = o[a] + w[a] * np.float32(pc[a])
+            sh.append((q >= np.float32(1.0)).astype(np.int64) - (q < np.float32(-1.0)))
+        i, j, k = (i + sh[0]) % nx, (j + sh[1]) % ny, (k + sh[2]) % nz
     ntx, nty = -(-nx // tx), -(-ny // ty)
     t = (i // tx) + ntx * ((j // ty) + nty * (k // tz))
     return t * (tx * ty * tz) + (i % tx) + tx * ((j % ty) + ty * (k % tz))

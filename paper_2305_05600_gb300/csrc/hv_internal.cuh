@@ -117,6 +117,11 @@ struct Geom {
   int tlog;             // log2(cells per tile)
   int open[3];          // 1: the axis has open faces (Sec. 2.3), 0: periodic
   int any_open;
+  // sort keys predict the ion's cell half a sort interval ahead: the
+  // displacement of sort_every / 2 steps in offset units per unit velocity,
+  // sort_every * dt / Delta per axis (0 on single-cell axes, with open
+  // faces and without sorting: the ion's own cell)
+  float pcx, pcy, pcz;
 };
 
 // Voxel index of an ion that left through an open face: it stays in its slot,
@@ -144,15 +149,31 @@ __host__ __device__ __forceinline__ int voxel_of(const Geom &g, int i, int j, in
   return (i + kGhost) + (g.dim2 ? 0 : (j + kGhost) * g.sy) + (k + kGhost) * g.sz;
 }
 
-// Supercell sort key of an ion from its voxel index (tile extents are
-// powers of two).  A voxel that is not an interior cell gets the last key,
-// so a corrupt index stays inside the count arrays (the push reports it).
-__device__ __forceinline__ int ion_key(const Geom &g, int vox) {
+// Cell shift of the sort key along one axis: +1 or -1 when the offset plus
+// the velocity times pc (the predicted displacement) leaves [-1, 1), else 0
+// (at most one cell).  The product and the sum are rounded separately (no
+// fused multiply-add), so the key is a reproducible FP32 function of the
+// stored state.
+__device__ __forceinline__ int pred_shift(float off, float v, float pc) {
+  const float q = __fadd_rn(off, __fmul_rn(v, pc));
+  return (q >= 1.f) - (q < -1.f);
+}
+
+// c + s (|s| <= 1) periodically on an axis of n cells
+__host__ __device__ __forceinline__ int wrap1(int c, int n) {
+  return c < 0 ? c + n : (c >= n ? c - n : c);
+}
+
+// Supercell sort key of an ion from its voxel index and its predicted cell
+// shift (tile extents are powers of two).  A voxel that is not an interior
+// cell gets the last key, so a corrupt index stays inside the count arrays
+// (the push reports it).
+__device__ __forceinline__ int ion_key(const Geom &g, int vox, int sx, int sy, int sz) {
   const int last = (g.ntiles << g.tlog) - 1;
   if (vox < g.vlo || vox >= g.vhi) return last;
   const uint32_t v = (uint32_t)vox;
   const uint32_t q = fdiv(v, g.div_px);
-  const int i = (int)(v - q * (uint32_t)g.px) - kGhost;
+  int i = (int)(v - q * (uint32_t)g.px) - kGhost;
   int j = 0, k;
   if (g.dim2) {
     k = (int)q - kGhost;
@@ -164,6 +185,9 @@ __device__ __forceinline__ int ion_key(const Geom &g, int vox) {
   if ((unsigned)i >= (unsigned)g.nx || (unsigned)j >= (unsigned)g.ny ||
       (unsigned)k >= (unsigned)g.nz)
     return last;
+  i = wrap1(i + sx, g.nx);
+  j = wrap1(j + sy, g.ny);
+  k = wrap1(k + sz, g.nz);
   const int lx = __ffs(g.tx) - 1, ly = __ffs(g.ty) - 1, lz = __ffs(g.tz) - 1;
   const int tile = (i >> lx) + g.ntx * ((j >> ly) + g.nty * (k >> lz));
   const int local = (i & (g.tx - 1)) + ((j & (g.ty - 1)) << lx) + ((k & (g.tz - 1)) << (lx + ly));

@@ -306,8 +306,13 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 
 // ----------------------------------------------------------------------------
 // The step's sort: a stable counting sort of the ions by supercell key (tile,
-// then cell in the tile); ions with equal keys keep the order they had.  Two
-// paths give the same permutation:
+// then cell in the tile); ions with equal keys keep the order they had.  An
+// ion's key cell is its cell moved by at most one cell along an axis on
+// which its offset plus its velocity times sort_every * dt / Delta leaves
+// [-1, 1): the cell it is predicted to reach half a sort interval later
+// (pred_shift; none with open faces).  Ions leave their sorted cells in both
+// directions between two sorts instead of in one, which halves the deposit
+// runs the push has to break.  Two paths give the same permutation:
 //
 // General path (the first sort after loading, long sort intervals): the keys
 // go through the stable radix passes above, the ions are gathered by the
@@ -315,10 +320,12 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 // the sorted keys.
 //
 // Windowed path: between two sorts an ion moves at most one cell per axis
-// per step (a larger move is a CFL error and the ion is held), so when at
-// most H steps have passed, every ion of tile t's last range
-// [tile_off[t], tile_off[t+1]) lies in t's window: the tile grown by H cells
-// on each side, periodically.  A cell's position in that window is its slot.
+// per step (a larger move is a CFL error and the ion is held), and a key
+// cell is at most one cell from the ion's cell at either sort, so when at
+// most H - 2 steps have passed (H with no prediction), every ion of tile t's
+// last range [tile_off[t], tile_off[t+1]) has its key cell in t's window:
+// the tile grown by H cells on each side, periodically.  A cell's position
+// in that window is its slot.
 //   rank:    one block per tile walks the tile's range in order, each warp
 //            a contiguous part with warp-private slot counters; a first walk
 //            counts, an exclusive scan over the warps turns the counts into
@@ -328,20 +335,19 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 //            each (tile, slot) count becomes the number of ions of that key
 //            in earlier tiles' ranges, and their sum is the key's count;
 //   scan:    counts -> offsets (in place), tile ranges from the offsets;
-//   scatter: one block per tile moves every ion to
-//            offset[key] + prefix[tile][slot] + rank.
+//   base:    per (tile, slot) the key's offset plus that prefix;
+//   scatter: one ion per thread moves to base[tile][slot] + rank.
 // ----------------------------------------------------------------------------
 template <int DIM>
 struct SortWin {
   static constexpr int TX = DIM == 2 ? kTile2X : kTile3;
   static constexpr int TY = DIM == 2 ? 1 : kTile3;
   static constexpr int TZ = DIM == 2 ? kTile2Z : kTile3;
-  static constexpr int H = DIM == 2 ? 8 : 4;  // window halo in cells
+  static constexpr int H = DIM == 2 ? 10 : 4;  // window halo in cells
   static constexpr int WX = TX + 2 * H, WY = DIM == 2 ? 1 : TY + 2 * H, WZ = TZ + 2 * H;
   static constexpr int NS = WX * WY * WZ;     // slots per window
   static constexpr int WARPS = DIM == 2 ? 8 : 4;
   static constexpr size_t rank_smem = sizeof(int32_t) * WARPS * NS;
-  static constexpr size_t scatter_smem = sizeof(int32_t) * NS;
   static_assert(NS <= 65536, "slots are cached as 16-bit values");
 };
 
@@ -395,14 +401,17 @@ __device__ __forceinline__ int win_slot(const Geom &g, int x0, int y0, int z0, i
   return sx + SW::WX * (sy + SW::WY * sz);
 }
 
-// Slot of an ion in tile t's window; an ion that is not in the window (only
-// a corrupt cell index can do that) takes slot 0 and raises the index error.
+// Slot of an ion's key cell (its cell moved by the predicted shift) in tile
+// t's window; an ion that is not in the window (only a corrupt cell index
+// can do that) takes slot 0 and raises the index error.
 template <int DIM>
-__device__ __forceinline__ int ion_slot(const Geom &g, int x0, int y0, int z0, int vox,
-                                        bool &bad) {
+__device__ __forceinline__ int ion_slot(const Geom &g, int x0, int y0, int z0, int vox, int sx,
+                                        int sy, int sz, bool &bad) {
   int i, j, k;
   int s = -1;
-  if (vox_cell(g, vox, i, j, k)) s = win_slot<DIM>(g, x0, y0, z0, i, j, k);
+  if (vox_cell(g, vox, i, j, k))
+    s = win_slot<DIM>(g, x0, y0, z0, wrap1(i + sx, g.nx), wrap1(j + sy, g.ny),
+                      wrap1(k + sz, g.nz));
   if (s < 0) {
     bad = true;
     s = 0;
@@ -412,8 +421,8 @@ __device__ __forceinline__ int ion_slot(const Geom &g, int x0, int y0, int z0, i
 
 template <int DIM>
 __global__ void __launch_bounds__(SortWin<DIM>::WARPS * 32)
-    wsort_rank_kernel(Geom g, const int32_t *vox, const int *tile_off, int32_t *wcnt,
-                      int32_t *rank, uint16_t *slot_cache, int *err) {
+    wsort_rank_kernel(Geom g, Soa ions, const int *tile_off, int32_t *wcnt, int32_t *rank,
+                      uint16_t *slot_cache, int *err) {
   using SW = SortWin<DIM>;
   extern __shared__ int32_t cw[];  // [WARPS][NS] warp-private slot counters
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -433,16 +442,23 @@ __global__ void __launch_bounds__(SortWin<DIM>::WARPS * 32)
       int sl[kSortUnroll];
       if (walk == 0) {
         // the first walk computes the slots and keeps them for the second
-        int v[kSortUnroll];
+        int v[kSortUnroll], sx[kSortUnroll], sy[kSortUnroll], sz[kSortUnroll];
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) {
           const int idx = base + 32 * u + lane;
-          v[u] = idx < wb ? vox[idx] : 0;
+          v[u] = 0;
+          sx[u] = sy[u] = sz[u] = 0;
+          if (idx < wb) {
+            v[u] = ions.cell[idx];
+            sx[u] = pred_shift(ions.ox[idx], ions.vx[idx], g.pcx);
+            if (DIM == 3) sy[u] = pred_shift(ions.oy[idx], ions.vy[idx], g.pcy);
+            sz[u] = pred_shift(ions.oz[idx], ions.vz[idx], g.pcz);
+          }
         }
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) {
           const int idx = base + 32 * u + lane;
-          sl[u] = idx < wb ? ion_slot<DIM>(g, x0, y0, z0, v[u], bad) : 0;
+          sl[u] = idx < wb ? ion_slot<DIM>(g, x0, y0, z0, v[u], sx[u], sy[u], sz[u], bad) : 0;
           if (idx < wb) slot_cache[idx] = (uint16_t)sl[u];
         }
       } else {
@@ -546,196 +562,6 @@ __global__ void __launch_bounds__(256) wsort_prefix_kernel(Geom g, int32_t *wcnt
   }
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(256) wsort_scatter_kernel(Geom g, Soa in, Soa out,
-                                                            const int *tile_off,
-                                                            const int32_t *wpre,
-                                                            const int32_t *off,
-                                                            const int32_t *rank) {
-  using SW = SortWin<DIM>;
-  extern __shared__ int32_t dbase[];  // [NS] first destination of each slot
-  const int t = blockIdx.x;
-  int x0, y0, z0;
-  tile_origin<DIM>(g, t, x0, y0, z0);
-  for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) {
-    const int sx = s % SW::WX, sy = (s / SW::WX) % SW::WY, sz = s / (SW::WX * SW::WY);
-    const int i = wrap0(x0 - SW::H + sx, g.nx);
-    const int j = DIM == 2 ? 0 : wrap0(y0 - SW::H + sy, g.ny);
-    const int k = wrap0(z0 - SW::H + sz, g.nz);
-    dbase[s] = off[supercell_key(g, i, j, k)] + wpre[(size_t)t * SW::NS + s];
-  }
-  __syncthreads();
-  const int a = tile_off[t], b = tile_off[t + 1];
-  const bool has_y = in.oy != nullptr;
-  bool bad = false;
-  for (int i0 = a + threadIdx.x; i0 < b; i0 += blockDim.x * kSortUnroll) {
-    int c[kSortUnroll], r[kSortUnroll];
-    float x[kSortUnroll], y[kSortUnroll], z[kSortUnroll], vx[kSortUnroll], vy[kSortUnroll],
-        vz[kSortUnroll], w[kSortUnroll];
-#pragma unroll
-    for (int u = 0; u < kSortUnroll; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i >= b) continue;
-      c[u] = in.cell[i];
-      r[u] = rank[i];
-      x[u] = in.ox[i];
-      y[u] = has_y ? in.oy[i] : 0.f;
-      z[u] = in.oz[i];
-      vx[u] = in.vx[i];
-      vy[u] = in.vy[i];
-      vz[u] = in.vz[i];
-      w[u] = in.w[i];
-    }
-#pragma unroll
-    for (int u = 0; u < kSortUnroll; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i >= b) continue;
-      const int d = dbase[ion_slot<DIM>(g, x0, y0, z0, c[u], bad)] + r[u];
-      out.cell[d] = c[u];
-      out.ox[d] = x[u];
-      if (has_y) out.oy[d] = y[u];
-      out.oz[d] = z[u];
-      out.vx[d] = vx[u];
-      out.vy[d] = vy[u];
-      out.vz[d] = vz[u];
-      out.w[d] = w[u];
-    }
-  }
-}
-
-// The same scatter with the stores grouped: a block takes its tile's ions in
-// chunks of kScatChunk, places each chunk in shared memory grouped by window
-// slot (the chunk's ions of one slot have consecutive destinations), and
-// writes the staged ions out in that order, so a warp's store covers one or
-// two contiguous runs instead of the five or so that 32 consecutive ions of
-// a drifted tile scatter to.
-// Scatter variant of the windowed path: 0 per-tile blocks, 1 per-tile
-// blocks with staged stores, 2 one ion per thread over the whole array.
-#ifndef HV_WSCATTER_MODE
-#define HV_WSCATTER_MODE 2
-#endif
-constexpr int kScatChunk = 1024;
-
-template <int DIM>
-struct ScatSmem {
-  static constexpr int NS = SortWin<DIM>::NS;
-  // dbase[NS], bins[NS], dest[chunk], fields[8][chunk]
-  static constexpr size_t bytes = sizeof(int32_t) * (2 * NS + 9 * kScatChunk);
-};
-
-template <int DIM>
-__global__ void __launch_bounds__(256) wsort_scatter_staged_kernel(Geom g, Soa in, Soa out,
-                                                                   const int *tile_off,
-                                                                   const int32_t *wpre,
-                                                                   const int32_t *off,
-                                                                   const int32_t *rank) {
-  using SW = SortWin<DIM>;
-  constexpr int PT = kScatChunk / 256;  // ions per thread per chunk
-  constexpr int BPT = (SW::NS + 255) / 256;  // bins per thread in the scan
-  __shared__ int s_warp[kWarps + 1];
-  extern __shared__ int32_t ssm[];
-  int32_t *dbase = ssm;                 // first destination of each slot
-  int32_t *bins = dbase + SW::NS;       // chunk counts per slot, then offsets
-  int32_t *sdst = bins + SW::NS;        // destinations in staged order
-  int32_t *sval = sdst + kScatChunk;    // [8][chunk] fields in staged order
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int t = blockIdx.x;
-  int x0, y0, z0;
-  tile_origin<DIM>(g, t, x0, y0, z0);
-  for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) {
-    const int sx = s % SW::WX, sy = (s / SW::WX) % SW::WY, sz = s / (SW::WX * SW::WY);
-    const int i = wrap0(x0 - SW::H + sx, g.nx);
-    const int j = DIM == 2 ? 0 : wrap0(y0 - SW::H + sy, g.ny);
-    const int k = wrap0(z0 - SW::H + sz, g.nz);
-    dbase[s] = off[supercell_key(g, i, j, k)] + wpre[(size_t)t * SW::NS + s];
-  }
-  const int a = tile_off[t], b = tile_off[t + 1];
-  const bool has_y = in.oy != nullptr;
-  bool bad = false;
-  for (int c0 = a; c0 < b; c0 += kScatChunk) {
-    for (int s = threadIdx.x; s < SW::NS; s += blockDim.x) bins[s] = 0;
-    __syncthreads();
-    int sl[PT], d[PT], pos[PT];
-    uint32_t f[PT][8];
-#pragma unroll
-    for (int u = 0; u < PT; ++u) {
-      const int i = c0 + threadIdx.x + 256 * u;
-      sl[u] = 0;
-      if (i >= b) continue;
-      const int c = in.cell[i];
-      d[u] = rank[i];
-      f[u][0] = (uint32_t)c;
-      f[u][1] = __float_as_uint(in.ox[i]);
-      f[u][2] = has_y ? __float_as_uint(in.oy[i]) : 0u;
-      f[u][3] = __float_as_uint(in.oz[i]);
-      f[u][4] = __float_as_uint(in.vx[i]);
-      f[u][5] = __float_as_uint(in.vy[i]);
-      f[u][6] = __float_as_uint(in.vz[i]);
-      f[u][7] = __float_as_uint(in.w[i]);
-      sl[u] = ion_slot<DIM>(g, x0, y0, z0, c, bad);
-      d[u] += dbase[sl[u]];
-    }
-    // position of each ion within its slot's group of the chunk
-#pragma unroll
-    for (int u = 0; u < PT; ++u) {
-      const int i = c0 + threadIdx.x + 256 * u;
-      const unsigned act = __ballot_sync(kFull, i < b);
-      if (i < b) {
-        const unsigned peers = __match_any_sync(act, sl[u]);
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&bins[sl[u]], __popc(peers));
-        base = __shfl_sync(act, base, leader);
-        pos[u] = base + __popc(peers & lt);
-      }
-    }
-    __syncthreads();
-    // exclusive scan of the slot counts: BPT consecutive bins per thread
-    {
-      int v[BPT], tot = 0;
-#pragma unroll
-      for (int q = 0; q < BPT; ++q) {
-        const int s = threadIdx.x * BPT + q;
-        v[q] = s < SW::NS ? bins[s] : 0;
-        tot += v[q];
-      }
-      int total;
-      int ex = block_exclusive_scan(tot, s_warp, total);
-#pragma unroll
-      for (int q = 0; q < BPT; ++q) {
-        const int s = threadIdx.x * BPT + q;
-        if (s < SW::NS) bins[s] = ex;
-        ex += v[q];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PT; ++u) {
-      const int i = c0 + threadIdx.x + 256 * u;
-      if (i >= b) continue;
-      const int j = bins[sl[u]] + pos[u];
-      sdst[j] = d[u];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sval[q * kScatChunk + j] = (int32_t)f[u][q];
-    }
-    __syncthreads();
-    const int m = min(kScatChunk, b - c0);
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      const int dd = sdst[j];
-      out.cell[dd] = sval[j];
-      out.ox[dd] = __int_as_float(sval[kScatChunk + j]);
-      if (has_y) out.oy[dd] = __int_as_float(sval[2 * kScatChunk + j]);
-      out.oz[dd] = __int_as_float(sval[3 * kScatChunk + j]);
-      out.vx[dd] = __int_as_float(sval[4 * kScatChunk + j]);
-      out.vy[dd] = __int_as_float(sval[5 * kScatChunk + j]);
-      out.vz[dd] = __int_as_float(sval[6 * kScatChunk + j]);
-      out.w[dd] = __int_as_float(sval[7 * kScatChunk + j]);
-    }
-    __syncthreads();
-  }
-}
-
 // First destination of every (tile, slot): the key's offset plus the count
 // of its ions in earlier tiles' ranges (in place over the prefixes).
 template <int DIM>
@@ -790,7 +616,10 @@ __global__ void __launch_bounds__(256) wsort_scatter_flat_kernel(Geom g, Soa in,
   const float x = in.ox[i], y = has_y ? in.oy[i] : 0.f, z = in.oz[i];
   const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
   bool bad = false;
-  const int d = __ldg(wbase + (size_t)t * SW::NS + ion_slot<DIM>(g, x0, y0, z0, c, bad)) + r;
+  const int sx = pred_shift(x, vx, g.pcx), sy = DIM == 3 ? pred_shift(y, vy, g.pcy) : 0,
+            sz = pred_shift(z, vz, g.pcz);
+  const int d =
+      __ldg(wbase + (size_t)t * SW::NS + ion_slot<DIM>(g, x0, y0, z0, c, sx, sy, sz, bad)) + r;
   out.cell[d] = c;
   out.ox[d] = x;
   if (has_y) out.oy[d] = y;
@@ -804,12 +633,16 @@ __global__ void __launch_bounds__(256) wsort_scatter_flat_kernel(Geom g, Soa in,
 // General path: keys, gather by permutation, tile ranges from sorted keys.
 // (a dead slot, open faces, takes the key after the last one: behind every
 // live ion)
-__global__ void ion_keys_kernel(Geom g, const int32_t *vox, int64_t n, int32_t *keys) {
+__global__ void ion_keys_kernel(Geom g, Soa ions, int64_t n, int32_t *keys) {
   const int dead_key = g.ntiles << g.tlog;
+  const bool has_y = ions.oy != nullptr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int v = vox[i];
-    keys[i] = v == kDeadVox ? dead_key : ion_key(g, v);
+    const int v = ions.cell[i];
+    const int sx = pred_shift(ions.ox[i], ions.vx[i], g.pcx);
+    const int sy = has_y ? pred_shift(ions.oy[i], ions.vy[i], g.pcy) : 0;
+    const int sz = pred_shift(ions.oz[i], ions.vz[i], g.pcz);
+    keys[i] = v == kDeadVox ? dead_key : ion_key(g, v, sx, sy, sz);
   }
 }
 
@@ -901,39 +734,26 @@ hv_status sort_windowed(hv_ctx *c, Species &sp, cudaStream_t st) {
   uint16_t *slots;
   hv_status hs = window_reserve<DIM>(c, sp, &cnt, &bsum, &rank, &slots);
   if (hs != HV_OK) return hs;
-  static std::atomic<uint64_t> attr_rank{0}, attr_scatter{0};
+  static std::atomic<uint64_t> attr_rank{0};
   cudaError_t e = set_smem_once(wsort_rank_kernel<DIM>, SW::rank_smem, attr_rank);
-  if (e == cudaSuccess && HV_WSCATTER_MODE == 1)
-    e = set_smem_once(wsort_scatter_staged_kernel<DIM>, ScatSmem<DIM>::bytes, attr_scatter);
-  if (e == cudaSuccess && HV_WSCATTER_MODE == 0)
-    e = set_smem_once(wsort_scatter_kernel<DIM>, SW::scatter_smem, attr_scatter);
   if (e != cudaSuccess) return cuda_fail(e, "sort kernel attributes");
   const int64_t nkeys = (int64_t)g.ntiles << g.tlog;
   const int64_t nb = bsum_len(nkeys);
   const Soa &src = sp.buf[sp.cur];
   wsort_rank_kernel<DIM><<<g.ntiles, SW::WARPS * 32, SW::rank_smem, st>>>(
-      g, src.cell, sp.tile_off, sp.wcnt, rank, slots, c->err);
+      g, src, sp.tile_off, sp.wcnt, rank, slots, c->err);
   wsort_prefix_kernel<DIM><<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(g, sp.wcnt, cnt);
   chunk_sum_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
   scan_bsum_kernel<<<1, kThreads, 0, st>>>(bsum, nb);
   chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(cnt, nkeys, bsum);
   tile_starts_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(cnt, g.tlog, g.ntiles, sp.n,
                                                              sp.tile_off_next);
-  if (HV_WSCATTER_MODE == 2) {
-    const int64_t tot = (int64_t)g.ntiles * SW::NS;
-    wsort_base_kernel<DIM><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8 * 2048), 256, 0, st>>>(
-        g, sp.wcnt, cnt);
-    wsort_scatter_flat_kernel<DIM><<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(
-        g, src, sp.buf[sp.cur ^ 1], sp.n, sp.tile_off, sp.wcnt, rank);
-    c->launches++;
-  } else if (HV_WSCATTER_MODE == 1) {
-    wsort_scatter_staged_kernel<DIM><<<g.ntiles, 256, ScatSmem<DIM>::bytes, st>>>(
-        g, src, sp.buf[sp.cur ^ 1], sp.tile_off, sp.wcnt, cnt, rank);
-  } else {
-    wsort_scatter_kernel<DIM><<<g.ntiles, 256, SW::scatter_smem, st>>>(
-        g, src, sp.buf[sp.cur ^ 1], sp.tile_off, sp.wcnt, cnt, rank);
-  }
-  c->launches += 7;
+  const int64_t tot = (int64_t)g.ntiles * SW::NS;
+  wsort_base_kernel<DIM><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8 * 2048), 256, 0, st>>>(
+      g, sp.wcnt, cnt);
+  wsort_scatter_flat_kernel<DIM><<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(
+      g, src, sp.buf[sp.cur ^ 1], sp.n, sp.tile_off, sp.wcnt, rank);
+  c->launches += 8;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "windowed sort");
   return HV_OK;
@@ -948,7 +768,7 @@ hv_status sort_general(hv_ctx *c, Species &sp, cudaStream_t st) {
   const int eb = (int)std::min<int64_t>((sp.n + 255) / 256, 8 * 2048);
   // the keys live in v[1]: the first radix pass reads them and writes
   // k[0], v[0]; later passes overwrite them only after that
-  ion_keys_kernel<<<eb, 256, 0, st>>>(g, src.cell, sp.n, s->v[1]);
+  ion_keys_kernel<<<eb, 256, 0, st>>>(g, src, sp.n, s->v[1]);
   int32_t *perm = nullptr, *skeys = nullptr;
   int64_t launches = 1;
   cudaError_t e = radix_perm(s->v[1], sp.n, nkeys + (g.any_open ? 1 : 0), s, st, &perm,
@@ -977,9 +797,12 @@ int sort_window(const hv_ctx *c) { return c->g.dim2 ? SortWin<2>::H : SortWin<3>
 hv_status sort_species(hv_ctx *c, int sidx, cudaStream_t stream) {
   Species &sp = c->sp[sidx];
   if (sp.n == 0) return HV_OK;
-  // (open faces: dead slots must be sorted out, which the general path does)
-  const bool windowed =
-      !c->g.any_open && c->since_sort >= 0 && c->since_sort <= sort_window(c);
+  // (open faces: dead slots must be sorted out, which the general path does;
+  // a predicted key cell is at most one cell from the ion's cell, at this
+  // sort and at the last one)
+  const bool pred = c->g.pcx != 0.f || c->g.pcy != 0.f || c->g.pcz != 0.f;
+  const bool windowed = !c->g.any_open && c->since_sort >= 0 &&
+                        c->since_sort + (pred ? 2 : 0) <= sort_window(c);
   hv_status st;
   if (windowed)
     st = c->g.dim2 ? sort_windowed<2>(c, sp, stream) : sort_windowed<3>(c, sp, stream);

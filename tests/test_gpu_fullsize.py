@@ -2,7 +2,7 @@
 the 3D configurations at oracle-sized subdomains.
 
 Workload: the 2D Harris sheet of the benchmark, 1024x512 cells, 100 ions per
-cell (52,428,800 ions), QS shape, 10 field subcycles, sort every 4 steps.
+cell (52,428,800 ions), QS shape, 10 field subcycles, sort every 8 steps.
 One GPU step is compared with one step of the FP64 oracle on the same
 input:
   * the whole grids: deposited n, J, B (relative L2 <= 1e-6) and E
@@ -203,7 +203,7 @@ def one_step_check(hvmod, wl, nsample=NSAMPLE, seed=2024):
 
 def test_full_size_harris2d_one_step(hvmod):
     """The benchmark workload itself: 1024x512 cells, 52,428,800 ions."""
-    wl = I.harris(shape="qs", seed=1000, sort_every=4)
+    wl = I.harris(shape="qs", seed=1000, sort_every=8)
     assert (wl.params["nx"], wl.params["nz"], wl.n_particles) == (1024, 512, 52_428_800)
     one_step_check(hvmod, wl)
 

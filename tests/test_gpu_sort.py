@@ -2,7 +2,10 @@
 
 The library sorts every species by supercell key (tile index, then the cell
 inside the tile) every sort_every steps, keeping the order of ions with
-equal keys.  Ions are identified by distinct weights, which the library
+equal keys.  The key cell of an ion is its cell moved by at most one cell
+along each axis toward where it is predicted to be half a sort interval
+later (off + v * sort_every * dt / Delta outside [-1, 1), FP32;
+oracle.supercell_keys restates it).  Ions are identified by distinct weights, which the library
 copies bit for bit, so the order hv_get_ions reports after a step is the
 sort's permutation applied to the order before it (the push moves ions
 in place).  Each sort is checked against oracle.sort_stable on the keys of
@@ -12,7 +15,7 @@ the pre-sort cells:
   * the tile ranges (hv_get_tile_offsets): the oracle's key offsets at the
     first key of every tile (exact).
 The first sort after loading takes the general path (radix passes); later
-sorts at most 8 (2D) or 4 (3D) steps after the previous one take the
+sorts at most 8 (2D) or 2 (3D) steps after the previous one take the
 windowed path, longer intervals the general path again.  The cases cover
 ragged tiles, windows wider than the grid (two tiles per axis), a single
 tile, two species and both paths in 2D and 3D."""
@@ -60,9 +63,12 @@ CASES = {
     # 2D, longer than the window: every sort takes the general path
     "2d_general_every10": lambda: I.harris(nx=40, nz=24, ppc=24, dx=0.25, seed=44,
                                            sort_every=10),
-    # 3D, ragged tiles, windowed sorts every 4 steps (fast beam ions)
+    # 3D, ragged tiles, windowed sorts every 2 steps (fast beam ions)
+    "3d_ragged_every2": lambda: I.beam3d(nx=12, ny=10, nz=9, n_core=6, n_beam=3, dx=0.5,
+                                         seed=45, sort_every=2),
+    # 3D, sort every 4 steps: the general path (the window holds 2 steps)
     "3d_ragged_every4": lambda: I.beam3d(nx=12, ny=10, nz=9, n_core=6, n_beam=3, dx=0.5,
-                                         seed=45, sort_every=4),
+                                         seed=51, sort_every=4),
     # 3D, sort every 20 steps: the general path
     "3d_general_every20": lambda: I.beam3d(nx=20, ny=17, nz=9, n_core=3, n_beam=1, dx=0.5,
                                            seed=46, sort_every=20),
@@ -92,7 +98,9 @@ def test_step_sort_bit_exact(hvmod, case):
         if step % S == 0:
             nsorts += 1
             for s in range(len(wl.species)):
-                keys = O.supercell_keys(before[s]["cell"], p["nx"], p["ny"], p["nz"], tile)
+                keys = O.supercell_keys(before[s]["cell"], p["nx"], p["ny"], p["nz"], tile,
+                                        off=before[s]["off"], v=before[s]["v"],
+                                        pc=O.sort_pred_coeffs(p))
                 perm, counts, offsets = O.sort_stable(keys, nkeys)
                 assert np.array_equal(after[s]["w"], before[s]["w"][perm]), (case, step, s)
                 tile_off = hvmod.hv_get_tile_offsets(ctx, s)
