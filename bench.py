@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--per-step", type=int, default=0,
+                    help="instead of the benchmark: profile this many single steps after "
+                         "the warm-up and print the push time against the steps since "
+                         "the last sort")
     return ap.parse_args()
 
 
@@ -365,6 +369,9 @@ def run_ours(args, world, rank, local):
     for _ in range(args.warmup):
         hv.hv_step(ctx, 1)
     torch.cuda.synchronize(dev)
+    if args.per_step > 0:
+        per_step_profile(ctx, wl, args)
+        return
     hv.hv_profile(ctx, True)
     clocks = Clocks(local, not args.no_clocks and rank == 0)
     barrier(world)
@@ -522,6 +529,26 @@ def cpu_baseline(wl):
                                     f"in thread order)",
             "single_thread": {"value": out["single"]["value"], "unit": UNIT, "cores": 1,
                               "sample": out["single"]["sample"]}}
+
+
+def per_step_profile(ctx, wl, args):
+    """Push time of single steps against the steps since the last sort
+    (device time of the push phase, events on its stream), averaged over
+    the profiled steps with the same count; one JSON line."""
+    S = wl.params["sort_every"]
+    step0 = hv.hv_query(ctx)["step"]
+    times = {}
+    for _ in range(args.per_step):
+        since = (hv.hv_query(ctx)["step"] % S) if S > 0 else -1
+        hv.hv_profile(ctx, True)
+        hv.hv_step(ctx, 1)
+        p = hv.hv_profile_read(ctx)
+        times.setdefault(since, []).append(p["ms_push"] / max(1, p["n_push"]))
+    hv.hv_profile(ctx, False)
+    print(json.dumps({"workload": args.workload, "sort_every": S, "first_step": step0,
+                      "steps": args.per_step,
+                      "push_ms_by_steps_since_sort": {str(k): round(sum(v) / len(v), 4)
+                                                      for k, v in sorted(times.items())}}))
 
 
 def main():
