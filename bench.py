@@ -535,6 +535,7 @@ def per_step_profile(ctx, wl, args):
     """Push time of single steps against the steps since the last sort
     (device time of the push phase, events on its stream), averaged over
     the profiled steps with the same count; one JSON line."""
+    from paper_2305_05600_gb300 import hv
     S = wl.params["sort_every"]
     step0 = hv.hv_query(ctx)["step"]
     times = {}

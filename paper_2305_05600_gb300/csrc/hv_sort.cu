@@ -351,7 +351,11 @@ struct SortWin {
   static_assert(NS <= 65536, "slots are cached as 16-bit values");
 };
 
-constexpr int kSortUnroll = 4;
+// ions per lane whose loads the rank kernel's walks issue together
+#ifndef HV_SORT_UNROLL
+#define HV_SORT_UNROLL 4
+#endif
+constexpr int kSortUnroll = HV_SORT_UNROLL;
 
 // v mod n in [0, n) (v is almost always already in range)
 __device__ __forceinline__ int wrap0(int v, int n) {
