@@ -17,7 +17,6 @@
 //             scatter to table offset + rank.
 // A final gather applies the permutation to the particle arrays.
 #include <algorithm>
-#include <mutex>
 
 #include "hv_internal.cuh"
 
@@ -898,31 +897,19 @@ constexpr int64_t kNoAllocTable = 256 * ((kNoAllocMaxKeys + kTile - 1) / kTile);
 constexpr int64_t kNoAllocBsum = (kNoAllocTable + kScanChunk - 1) / kScanChunk;
 // words: keys x2, values x2, digit table, chunk sums, error flag (+ padding)
 constexpr int64_t kNoAllocWords = 4 * kNoAllocMaxKeys + kNoAllocTable + kNoAllocBsum + 64;
-constexpr int kNoAllocMaxDevices = 64;
 
 // About 16.3 MB of device memory per GPU.
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
 
-std::mutex g_noalloc_mu;
-int32_t *g_noalloc_base[kNoAllocMaxDevices];
-
-// Device address of the static scratch on the current device, looked up once
-// per device (the first call on a device does this).
+// Device address of the static scratch in the current context, looked up on
+// every call: a cached address would outlive a cudaDeviceReset, which
+// rebuilds the primary context and its module globals.
 hv_status noalloc_base(int32_t **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "hv_sort_keys_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kNoAllocMaxDevices)
-    return fail(HV_EINVAL, "hv_sort_keys_noalloc: device ordinal above 63");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_base[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      return cuda_fail(e, "hv_sort_keys_noalloc: cudaGetSymbolAddress of the static scratch");
-    g_noalloc_base[dev] = static_cast<int32_t *>(p);
-  }
-  *out = g_noalloc_base[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    return cuda_fail(e, "hv_sort_keys_noalloc: cudaGetSymbolAddress of the static scratch");
+  *out = static_cast<int32_t *>(p);
   return HV_OK;
 }
 
