@@ -435,6 +435,8 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   c->pushpart = (double *)ctx_alloc(c, sizeof(double) * kMaxSpecies * c->push_blocks * 4);
   c->gridpart = (double *)ctx_alloc(c, sizeof(double) * c->grid_blocks * 4);
   c->diag_dev = (double *)ctx_alloc(c, sizeof(double) * 8);
+  c->diag_blk = (double *)ctx_alloc(c, sizeof(double) * 8 * kDiagBlocks);
+  c->diag_count = (unsigned *)ctx_alloc(c, sizeof(unsigned));
   c->err = (int *)ctx_alloc(c, sizeof(int));
   const bool rec = p->shape == HV_SHAPE_QS && c->g.dim2;
   for (int b = 0; b < 2; ++b)
@@ -449,7 +451,7 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
     for (int b = 0; b < 4; ++b) c->fsm[b] = (float4 *)ctx_alloc(c, sizeof(float4) * nc);
   }
   if (!c->EB || !c->acc || !c->B || !c->Bs || !c->mhalf || !c->mext || !c->mprev || !c->mtmp ||
-      !c->pushpart || !c->gridpart || !c->diag_dev || !c->err ||
+      !c->pushpart || !c->gridpart || !c->diag_dev || !c->diag_blk || !c->diag_count || !c->err ||
       (rec && (!c->accm[0] || !c->accm[1])) ||
       (fsm && (!c->EBs || !c->fsm[0] || !c->fsm[1] || !c->fsm[2] || !c->fsm[3])) ||
       (p->pe_eq && (!c->pe || !c->pes))) {
@@ -463,6 +465,7 @@ hv_status hv_init_grid(const hv_params *p, const float *B0_host, void *cuda_stre
   cudaMemsetAsync(c->mext, 0, sizeof(float4) * nc, c->stream);
   cudaMemsetAsync(c->pushpart, 0, sizeof(double) * kMaxSpecies * c->push_blocks * 4, c->stream);
   cudaMemsetAsync(c->diag_dev, 0, sizeof(double) * 8, c->stream);
+  cudaMemsetAsync(c->diag_count, 0, sizeof(unsigned), c->stream);
   cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
   for (int b = 0; b < 2; ++b)
     if (c->accm[b]) cudaMemsetAsync(c->accm[b], 0, sizeof(float) * kMono * npad, c->stream);

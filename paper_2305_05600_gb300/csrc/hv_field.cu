@@ -1082,10 +1082,16 @@ cudaError_t launch_stage_t(const hv_ctx *c, const StageArgs &a) {
 
 // W_B of the total field (B0 + B1 with an external field), max |div| of the
 // advanced field B (B1 with an external field), charge of the moments.
-__global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, float vc,
-                                                        const float4 *B, const float4 *B0,
-                                                        const float4 *mom, double *part) {
-  double wb = 0.0, ch = 0.0, md = 0.0;
+// Per cell in FP32, summed per thread and block in FP64 (the conservation
+// sums): 1/2 |B|^2 of the total field, the charge density, and the largest
+// |div B| of the advanced field B (B1 with an external field; max is exact
+// in any precision, the divergence itself is FP32).  Block partials, not
+// yet multiplied by the cell volume: {W_B, charge, max |div B|, 0}.
+__global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, const float4 *B,
+                                                        const float4 *B0, const float4 *mom,
+                                                        double *part) {
+  double wb = 0.0, ch = 0.0;
+  float md = 0.f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
     int i, j, kk;
     decode(g, c, i, j, kk);
@@ -1094,8 +1100,8 @@ __global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, f
       const float4 e = B0[c];
       b = make_float4(b.x + e.x, b.y + e.y, b.z + e.z, 0.f);
     }
-    wb += 0.5 * ((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) * vc;
-    ch += (double)mom[c].x * vc;
+    wb += (double)(0.5f * (b.x * b.x + b.y * b.y + b.z * b.z));
+    ch += (double)mom[c].x;
     // neighbours: periodic images, or on an open axis the cell itself beyond
     // the face (the ghost copies its interior neighbour)
     auto nb = [](int c, int n, int open) {
@@ -1107,55 +1113,98 @@ __global__ void __launch_bounds__(256) grid_diag_kernel(Geom g, FieldConsts k, f
     const int ym = i + g.nx * (nb(j - 1, g.ny, g.open[1]) + g.ny * kk);
     const int zp = i + g.nx * (j + g.ny * nb(kk + 1, g.nz, g.open[2]));
     const int zm = i + g.nx * (j + g.ny * nb(kk - 1, g.nz, g.open[2]));
-    const double dv = ((double)B[xp].x - B[xm].x) * k.idx2 + ((double)B[yp].y - B[ym].y) * k.idy2 +
-                      ((double)B[zp].z - B[zm].z) * k.idz2;
-    md = fmax(md, fabs(dv));
+    const float dv = (B[xp].x - B[xm].x) * k.idx2 + (B[yp].y - B[ym].y) * k.idy2 +
+                     (B[zp].z - B[zm].z) * k.idz2;
+    md = fmaxf(md, fabsf(dv));
   }
-  __shared__ double s[3][256];
-  s[0][threadIdx.x] = wb;
-  s[1][threadIdx.x] = ch;
-  s[2][threadIdx.x] = md;
+  // the warp's lanes, then the block's warps, in a fixed order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wb += __shfl_down_sync(0xffffffffu, wb, o);
+    ch += __shfl_down_sync(0xffffffffu, ch, o);
+    md = fmaxf(md, __shfl_down_sync(0xffffffffu, md, o));
+  }
+  __shared__ double s[3][8];
+  if (lane == 0) {
+    s[0][warp] = wb;
+    s[1][warp] = ch;
+    s[2][warp] = md;
+  }
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + o];
-      s[1][threadIdx.x] += s[1][threadIdx.x + o];
-      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + o]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[blockIdx.x * 4 + 0] = s[0][0];
-    part[blockIdx.x * 4 + 1] = s[1][0];
-    part[blockIdx.x * 4 + 2] = s[2][0];
-    part[blockIdx.x * 4 + 3] = 0.0;
+  if (threadIdx.x < 3) {
+    double r = s[threadIdx.x][0];
+    for (int w = 1; w < 8; ++w) r = threadIdx.x == 2 ? fmax(r, s[2][w]) : r + s[threadIdx.x][w];
+    part[blockIdx.x * 4 + threadIdx.x] = r;
+    if (threadIdx.x == 0) part[blockIdx.x * 4 + 3] = 0.0;
   }
 }
 
-// One block: fixed-order sums of the grid and particle partials.
+// Fixed-order sums of the grid and particle partials, spread over
+// kDiagBlocks blocks: each block sums a fixed slice of the partials and
+// writes its result; the block that finishes last (a counter, no waiting)
+// adds the block results in block order and rearms the counter.
 // out: W_K, Px, Py, Pz, charge, W_B, max_divB
-__global__ void diag_final_kernel(const double *gpart, int ngb, const double *ppart, int npb,
-                                  int nspecies, double *out) {
-  __shared__ double s[7][256];
+constexpr int kDiagThreads = 256;
+__global__ void __launch_bounds__(kDiagThreads)
+    diag_final_kernel(const double *gpart, int ngb, const double *ppart, int nppart,
+                      double vc, double *blk, unsigned *count, double *out) {
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < ngb; b += blockDim.x) {
+  const int nb = gridDim.x;
+  const int g0 = (int)((int64_t)ngb * blockIdx.x / nb), g1 = (int)((int64_t)ngb * (blockIdx.x + 1) / nb);
+  const int p0 = (int)((int64_t)nppart * blockIdx.x / nb),
+            p1 = (int)((int64_t)nppart * (blockIdx.x + 1) / nb);
+  for (int b = g0 + threadIdx.x; b < g1; b += blockDim.x) {
     v[5] += gpart[b * 4 + 0];
     v[4] += gpart[b * 4 + 1];
     v[6] = fmax(v[6], gpart[b * 4 + 2]);
   }
-  for (int b = threadIdx.x; b < npb * nspecies; b += blockDim.x) {
-    for (int m = 0; m < 4; ++m) v[m] += ppart[(size_t)b * 4 + m];
+  const double4 *pp = reinterpret_cast<const double4 *>(ppart);
+  for (int b = p0 + threadIdx.x; b < p1; b += blockDim.x) {
+    const double4 q = pp[b];
+    v[0] += q.x;
+    v[1] += q.y;
+    v[2] += q.z;
+    v[3] += q.w;
   }
-  for (int m = 0; m < 7; ++m) s[m][threadIdx.x] = v[m];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 6; ++m) v[m] += __shfl_down_sync(0xffffffffu, v[m], o);
+    v[6] = fmax(v[6], __shfl_down_sync(0xffffffffu, v[6], o));
+  }
+  __shared__ double s[7][kDiagThreads / 32];
+  __shared__ bool last;
+  if (lane == 0)
+    for (int m = 0; m < 7; ++m) s[m][warp] = v[m];
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      for (int m = 0; m < 6; ++m) s[m][threadIdx.x] += s[m][threadIdx.x + o];
-      s[6][threadIdx.x] = fmax(s[6][threadIdx.x], s[6][threadIdx.x + o]);
-    }
-    __syncthreads();
+  if (threadIdx.x < 7) {
+    double r = s[threadIdx.x][0];
+    for (int w = 1; w < kDiagThreads / 32; ++w)
+      r = threadIdx.x == 6 ? fmax(r, s[6][w]) : r + s[threadIdx.x][w];
+    blk[blockIdx.x * 8 + threadIdx.x] = r;
   }
-  if (threadIdx.x < 7) out[threadIdx.x] = s[threadIdx.x][0];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == (unsigned)(nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // every block's results into shared memory with one load per thread,
+  // then the sums in block order
+  __shared__ double sb[kDiagBlocks * 8];
+  const volatile double *vb = blk;
+  for (int e = threadIdx.x; e < nb * 8; e += blockDim.x) sb[e] = vb[e];
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double r = sb[threadIdx.x];
+    for (int b = 1; b < nb; ++b)
+      r = threadIdx.x == 6 ? fmax(r, sb[b * 8 + 6]) : r + sb[b * 8 + threadIdx.x];
+    // the grid sums are per unit volume until here
+    out[threadIdx.x] = (threadIdx.x == 4 || threadIdx.x == 5) ? r * vc : r;
+  }
+  if (threadIdx.x == 0) *count = 0u;
 }
 
 }  // namespace
@@ -1163,7 +1212,7 @@ __global__ void diag_final_kernel(const double *gpart, int ngb, const double *pp
 int grid_reduce_blocks(int device) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  return sms > 0 ? 2 * sms : 2;
+  return sms > 0 ? 8 * sms : 8;
 }
 
 static int elem_blocks(int n) {
@@ -1433,12 +1482,13 @@ cudaError_t launch_ohm_final(hv_ctx *c, const float4 *mom) {
 cudaError_t launch_diag(hv_ctx *c) {
   FieldConsts k = field_consts(c);
   c->launches += 2;
-  grid_diag_kernel<<<c->grid_blocks, 256, 0, c->stream>>>(c->g, k, (float)c->vc, c->B, c->B0ext,
-                                                          c->mprev, c->gridpart);
+  grid_diag_kernel<<<c->grid_blocks, 256, 0, c->stream>>>(c->g, k, c->B, c->B0ext, c->mprev,
+                                                          c->gridpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, 256, 0, c->stream>>>(c->gridpart, c->grid_blocks, c->pushpart,
-                                              c->push_blocks, c->nspecies, c->diag_dev);
+  diag_final_kernel<<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(
+      c->gridpart, c->grid_blocks, c->pushpart, c->push_blocks * c->nspecies, c->vc,
+      c->diag_blk, c->diag_count, c->diag_dev);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,8 @@ constexpr int kMaxSpecies = 8;
 // times v for J); the stencil of Eq. 17 is applied to these records when
 // the moments are folded onto the grid.
 constexpr int kMono = 20;
+// blocks of the diagnostics' final fixed-order sums
+constexpr int kDiagBlocks = 64;
 
 // Device error bits latched by kernels (atomicOr into the error word).
 constexpr int kErrCfl = 1;     // a particle moved more than one cell in a step
@@ -340,6 +342,8 @@ struct hv_ctx {
   double *pushpart;     // [kMaxSpecies][push_blocks][4]
   double *gridpart;     // [grid_blocks][4]
   double *diag_dev;     // [8]
+  double *diag_blk;     // [kDiagBlocks][8] block results of the final sums
+  unsigned *diag_count; // blocks of the final sums done (rearmed to 0)
   int *err;             // device error word
   int push_blocks, grid_blocks;
   hv::Species sp[hv::kMaxSpecies];
