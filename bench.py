@@ -491,9 +491,14 @@ def run_e2e(args, wl, world, dev, stream):
             hv.hv_reserve_ions(ctx, i, int(wl.reserve * c.shape[0]) + 1024)
     for s_idx, face, n_b, u_b, T_b, w_b in wl.inject:
         hv.hv_set_injection(ctx, s_idx, face, n_b, u_b, T_b, w_b)
-    for _ in range(steps):
+    # every step's diagnostics are read on the host, one step behind, so that
+    # the next step is already queued while the host waits for them
+    for i in range(steps):
         hv.hv_step(ctx, 1)
-        hv.hv_diag(ctx)
+        hv.hv_diag_async(ctx)
+        if i > 0:
+            hv.hv_diag_wait(ctx)
+    hv.hv_diag_wait(ctx)
     hv.hv_moments(ctx, n_host, J_host, None, None)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
@@ -505,7 +510,8 @@ def run_e2e(args, wl, world, dev, stream):
     d2h = 80 + (n_host.nbytes + J_host.nbytes) / steps
     return {"value": n_ions * steps / dt, "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "note": "load amortised over the steps; one hv_diag read per step"}
+            "note": "load amortised over the steps; every step's diagnostics read on the "
+                    "host (hv_diag_async / hv_diag_wait, one step behind)"}
 
 
 def cpu_baseline(wl):

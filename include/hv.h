@@ -265,6 +265,18 @@ hv_status hv_electron_pressure(hv_ctx *ctx, float *pe_out, int on_device);
  * diagnostic says so (the struct is still filled). */
 hv_status hv_diag(hv_ctx *ctx, hv_diag_t *out);
 
+/* hv_diag without the wait.  hv_diag_async enqueues the diagnostics of the
+ * state after the last step, with a copy of them and of the device error
+ * word to page-locked host memory that the context owns, and returns at
+ * once; up to 4 may be pending (HV_ESTATE when 4 are).  hv_diag_wait waits
+ * for the oldest pending one and fills *out as hv_diag does (out->step is
+ * the step it describes), with hv_diag's return codes; HV_ESTATE when none
+ * is pending.  A caller that enqueues step k + 1 before it waits for the
+ * diagnostics of step k reads every step's result while the GPU keeps
+ * working. */
+hv_status hv_diag_async(hv_ctx *ctx);
+hv_status hv_diag_wait(hv_ctx *ctx, hv_diag_t *out);
+
 /* Copy species `species` out in the library's current particle order (the
  * order changes when ions are sorted; see hv_query): cell [n], off3 [3][n], v3 [3][n]
  * (v^{n-1/2}), w [n].  Any pointer may be NULL.  n_out (may be NULL)

@@ -936,6 +936,62 @@ hv_status hv_diag(hv_ctx *c, hv_diag_t *out) {
   return HV_OK;
 }
 
+hv_status hv_diag_async(hv_ctx *c) {
+  if (!c) return fail(HV_EINVAL, "ctx is NULL");
+  if (c->dq_count == kDiagQueue) return fail(HV_ESTATE, "4 diagnostics pending: wait first");
+  if (!c->started) {
+    hv_status st = startup(c);
+    if (st != HV_OK) return st;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->dq_host) {
+    e = cudaMallocHost(&c->dq_host, sizeof(DiagSlot) * kDiagQueue);
+    for (int i = 0; i < kDiagQueue && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&c->dq_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "hv_diag_async: host slots");
+  }
+  DiagSlot &slot = c->dq_host[(c->dq_head + c->dq_count) % kDiagQueue];
+  e = launch_diag(c);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(slot.d, c->diag_dev, sizeof(double) * 7, cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&slot.word, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaEventRecord(c->dq_ev[(c->dq_head + c->dq_count) % kDiagQueue], c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_diag_async");
+  slot.step = c->step;
+  c->dq_count++;
+  return HV_OK;
+}
+
+hv_status hv_diag_wait(hv_ctx *c, hv_diag_t *out) {
+  if (!c || !out) return fail(HV_EINVAL, "ctx or out is NULL");
+  if (c->dq_count == 0) return fail(HV_ESTATE, "no diagnostics pending");
+  const int i = c->dq_head;
+  cudaError_t e = cudaEventSynchronize(c->dq_ev[i]);
+  if (e != cudaSuccess) return cuda_fail(e, "hv_diag_wait");
+  c->dq_head = (c->dq_head + 1) % kDiagQueue;
+  c->dq_count--;
+  const DiagSlot &slot = c->dq_host[i];
+  memset(out, 0, sizeof(*out));
+  out->step = slot.step;
+  out->t = slot.step * c->p.dt;
+  out->W_K = slot.d[0];
+  out->P[0] = slot.d[1];
+  out->P[1] = slot.d[2];
+  out->P[2] = slot.d[3];
+  out->charge = slot.d[4];
+  out->W_B = slot.d[5];
+  out->max_divB = slot.d[6];
+  out->err_word = slot.word;
+  const hv_status st = status_of_word(slot.word);
+  if (st != HV_OK) return st;
+  for (int k = 0; k < 7; ++k)
+    if (!std::isfinite(slot.d[k])) return fail(HV_ENAN, "non-finite diagnostic");
+  return HV_OK;
+}
+
 // hv_get_ions with open faces: the slots in use are read from the device and
 // the live ions among them (dead slots skipped) returned in order (host only).
 static hv_status get_ions_open(hv_ctx *c, Species &sp, int64_t *n_out, int32_t *cell, float *off3,
@@ -1286,6 +1342,11 @@ void hv_destroy(hv_ctx *c) {
     cudaStreamDestroy(c->side);
   }
   prof_destroy(c);
+  if (c->dq_host) {
+    for (int i = 0; i < kDiagQueue; ++i)
+      if (c->dq_ev[i]) cudaEventDestroy(c->dq_ev[i]);
+    cudaFreeHost(c->dq_host);
+  }
   for (int s = 0; s < c->nspecies; ++s) {
     for (int b = 0; b < 2; ++b) dev_free(c->sp[s].base[b], c->sp[s].bytes[b], c->stream);
     dev_free(std::min(c->sp[s].tile_off, c->sp[s].tile_off_next),

@@ -65,6 +65,14 @@ constexpr int kMaxSpecies = 8;
 constexpr int kMono = 20;
 // blocks of the diagnostics' final fixed-order sums
 constexpr int kDiagBlocks = 64;
+// diagnostics that may be pending at once (hv_diag_async)
+constexpr int kDiagQueue = 4;
+struct DiagSlot {
+  double d[8];   // W_K, Px, Py, Pz, charge, W_B, max_divB
+  int word;      // device error word
+  int pad;
+  int64_t step;  // the step the diagnostics describe
+};
 
 // Device error bits latched by kernels (atomicOr into the error word).
 constexpr int kErrCfl = 1;     // a particle moved more than one cell in a step
@@ -344,6 +352,11 @@ struct hv_ctx {
   double *diag_dev;     // [8]
   double *diag_blk;     // [kDiagBlocks][8] block results of the final sums
   unsigned *diag_count; // blocks of the final sums done (rearmed to 0)
+  // diagnostics enqueued by hv_diag_async, oldest first: results copied to
+  // page-locked host slots, an event per slot
+  hv::DiagSlot *dq_host;
+  cudaEvent_t dq_ev[hv::kDiagQueue];
+  int dq_head, dq_count;
   int *err;             // device error word
   int push_blocks, grid_blocks;
   hv::Species sp[hv::kMaxSpecies];

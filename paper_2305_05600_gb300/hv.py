@@ -82,7 +82,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
                            ctypes.c_void_p)
 
 EXPORTS = ["hv_set_allocator", "hv_init_grid", "hv_load_ions", "hv_step", "hv_moments",
-           "hv_diag", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
+           "hv_diag", "hv_diag_async", "hv_diag_wait", "hv_get_ions", "hv_query", "hv_profile", "hv_profile_read", "hv_destroy",
            "hv_sort_keys", "hv_sort_keys_noalloc", "hv_set_filter", "hv_filter_moments",
            "hv_filter_train_init", "hv_filter_grad", "hv_filter_train_step",
            "hv_filter_get_params", "hv_electron_pressure", "hv_get_tile_offsets",
@@ -111,6 +111,8 @@ def lib():
         L.hv_step.argtypes = [P, I32]
         L.hv_moments.argtypes = [P, P, P, P, P, ctypes.c_int]
         L.hv_diag.argtypes = [P, ctypes.POINTER(Diag)]
+        L.hv_diag_async.argtypes = [P]
+        L.hv_diag_wait.argtypes = [P, ctypes.POINTER(Diag)]
         L.hv_electron_pressure.argtypes = [P, P, ctypes.c_int]
         L.hv_get_ions.argtypes = [P, I32, ctypes.POINTER(I64), P, P, P, P, ctypes.c_int]
         L.hv_query.argtypes = [P, ctypes.POINTER(Info)]
@@ -315,6 +317,22 @@ def hv_electron_pressure(ctx: Ctx, pe_out=None, host: bool = True):
 def hv_diag(ctx: Ctx, check: bool = True) -> dict:
     d = Diag()
     rc = lib().hv_diag(ctx.handle, ctypes.byref(d))
+    if check:
+        _check(rc)
+    out = d.as_dict()
+    out["status"] = rc
+    return out
+
+
+def hv_diag_async(ctx: Ctx):
+    """Enqueue the diagnostics of the state after the last step (up to 4
+    pending); hv_diag_wait collects them oldest first."""
+    _check(lib().hv_diag_async(ctx.handle))
+
+
+def hv_diag_wait(ctx: Ctx, check: bool = True) -> dict:
+    d = Diag()
+    rc = lib().hv_diag_wait(ctx.handle, ctypes.byref(d))
     if check:
         _check(rc)
     out = d.as_dict()

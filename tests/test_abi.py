@@ -108,6 +108,8 @@ def test_context_calls_reject_null_on_host():
     L = hv.lib()
     assert L.hv_inject_error(None, 8) == hv.HV_EINVAL
     assert L.hv_get_tile_offsets(None, 0, None) == hv.HV_EINVAL
+    assert L.hv_diag_async(None) == hv.HV_EINVAL
+    assert L.hv_diag_wait(None, None) == hv.HV_EINVAL
 
 
 def test_noalloc_binding_rejects_host_tensors():

@@ -421,3 +421,43 @@ def test_alfven_config_200_steps(hvmod):
         assert abs(d[key] - od[key]) < 1e-3 * abs(od[key]), (key, d[key], od[key])
     assert d["max_divB"] < 1e-3
     ctx.close()
+
+
+def test_async_diagnostics(hvmod):
+    """hv_diag_async / hv_diag_wait give the values hv_diag gives for the
+    same state (the sums have a fixed order), pipelined one step behind;
+    at most 4 may be pending; the error word comes back through them."""
+    wl = I.harris(nx=40, nz=24, ppc=16, dx=0.25, seed=61, sort_every=2)
+    ctx = hvmod.load_workload(wl)
+    for _ in range(3):
+        hvmod.hv_step(ctx, 1)
+        ds = hvmod.hv_diag(ctx)
+        hvmod.hv_diag_async(ctx)
+        da = hvmod.hv_diag_wait(ctx)
+        for k in ("step", "t", "W_K", "W_B", "charge", "max_divB", "err_word"):
+            assert da[k] == ds[k], k
+        assert list(da["P"]) == list(ds["P"])
+    # pipelined: results arrive oldest first, each labelled with its step
+    steps = []
+    for i in range(4):
+        hvmod.hv_step(ctx, 1)
+        hvmod.hv_diag_async(ctx)
+        if i > 0:
+            steps.append(hvmod.hv_diag_wait(ctx)["step"])
+    steps.append(hvmod.hv_diag_wait(ctx)["step"])
+    assert steps == [4, 5, 6, 7]
+    # queue limits
+    for _ in range(4):
+        hvmod.hv_diag_async(ctx)
+    with pytest.raises(hvmod.HVError, match="HV_ESTATE"):
+        hvmod.hv_diag_async(ctx)
+    for _ in range(4):
+        hvmod.hv_diag_wait(ctx)
+    with pytest.raises(hvmod.HVError, match="HV_ESTATE"):
+        hvmod.hv_diag_wait(ctx)
+    # a latched error (injected on the host, no fault) is reported
+    hvmod.hv_inject_error(ctx, 1)
+    hvmod.hv_diag_async(ctx)
+    d = hvmod.hv_diag_wait(ctx, check=False)
+    assert d["status"] == hvmod.HV_ECFL and d["err_word"] == 1
+    ctx.close()
