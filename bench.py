@@ -223,8 +223,10 @@ def step_bytes(wl) -> dict:
     the field phase at the minimum of 124 B per cell (previous moments in
     and out, B in and out, E out, moments read by the field advance; the
     push's 40 B per cell counted once), and the sort amortised over its
-    interval (each ion's key read once, its other fields read and written
-    once: 4 + 2 x 28 B in 2D, 4 + 2 x 32 B in 3D)."""
+    interval (each ion's cell, offsets and velocities read once for its
+    predicted key, and its fields read and written once: 20 + 2 x 28 B in
+    2D, 28 + 2 x 32 B in 3D; with open faces the key is the cell alone,
+    4 B)."""
     p = wl.params
     dim2 = p["ny"] == 1
     ncell = p["nx"] * p["ny"] * p["nz"]
@@ -232,7 +234,8 @@ def step_bytes(wl) -> dict:
     push = push_bytes_per_launch(wl)
     field = ncell * (124 - 40)
     S = p["sort_every"]
-    sort = n * (4 + 2 * (28 if dim2 else 32)) / S if S > 0 else 0.0
+    key = 4 if p.get("open_faces", 0) else (20 if dim2 else 28)
+    sort = n * (key + 2 * (28 if dim2 else 32)) / S if S > 0 else 0.0
     return {"push": push, "field": float(field), "sort": sort, "total": push + field + sort}
 
 
