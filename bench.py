@@ -66,8 +66,8 @@ def parse():
 def make_workload(name, shape, seed_offset=0):
     from paper_2305_05600_gb300 import inputs as I
     # The windowed counting sort costs about 1.5 ms per call at 1024x512; the
-    # push is fastest at mid-interval, where the ions have reached the cells
-    # they were sorted by (predicted half an interval ahead).  Sorting every
+    # push is fastest mid-interval, where the ions have reached the cells
+    # they were sorted by (predicted 0.6875 intervals ahead).  Sorting every
     # 8 steps minimises the sum (measured on GB300 for 4, 6, 8).
     if name == "harris2d":
         return I.harris(shape=shape, seed=1000 + seed_offset, sort_every=8)

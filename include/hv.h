@@ -77,12 +77,13 @@ typedef struct {
   int32_t sort_every;   /* sort ions by cell every this many steps; 0 never.
                            The cell an ion is sorted by is its cell moved by
                            at most one cell along each axis toward where it
-                           is predicted to be half a sort interval later:
+                           is predicted to be 0.6875 sort intervals later:
                            along an axis of more than one cell, by +1 when
-                           off + v * (sort_every * dt / Delta) >= 1 and by
-                           -1 when it is < -1 (FP32, product and sum rounded
-                           separately; the stored v, u with relativistic
-                           particles), periodically.  Not with open faces. */
+                           off + v * (float)(1.375 * sort_every * dt / Delta)
+                           >= 1 and by -1 when it is < -1 (FP32, product and
+                           sum rounded separately; the stored v, u with
+                           relativistic particles), periodically.  Not with
+                           open faces. */
   int32_t field_smooth_passes; /* binomial passes applied to copies of E^n and
                            B^n that the push gathers (the self-consistent
                            field smoothing of Sec. 2.2); the field state is

@@ -394,11 +394,11 @@ def sort_stable(keys, nkeys):
 
 def sort_pred_coeffs(params):
     """The library's key-cell prediction coefficients per axis (FP32):
-    sort_every * dt / Delta, 0 on single-cell axes, with open faces and
-    without sorting (``include/hv.h``, sort_every)."""
+    1.375 * sort_every * dt / Delta, 0 on single-cell axes, with open faces
+    and without sorting (``include/hv.h``, sort_every)."""
     p = params
     on = p.get("sort_every", 0) > 0 and not p.get("open_faces", 0)
-    return tuple(np.float32(p["sort_every"] * p["dt"] / p[d]) if on and p[n] > 1
+    return tuple(np.float32(1.375 * p["sort_every"] * p["dt"] / p[d]) if on and p[n] > 1
                  else np.float32(0.0)
                  for n, d in (("nx", "dx"), ("ny", "dy"), ("nz", "dz")))
 

@@ -193,9 +193,9 @@ Geom make_geom(const hv_params *p) {
   for (int a = 0; a < 3; ++a) g.open[a] = (p->open_faces >> a) & 1;
   g.any_open = p->open_faces != 0;
   const bool pred = p->sort_every > 0 && !g.any_open;
-  g.pcx = pred && p->nx > 1 ? (float)(p->sort_every * p->dt / p->dx) : 0.f;
-  g.pcy = pred && p->ny > 1 ? (float)(p->sort_every * p->dt / p->dy) : 0.f;
-  g.pcz = pred && p->nz > 1 ? (float)(p->sort_every * p->dt / p->dz) : 0.f;
+  g.pcx = pred && p->nx > 1 ? (float)(kSortHorizon * p->sort_every * p->dt / p->dx) : 0.f;
+  g.pcy = pred && p->ny > 1 ? (float)(kSortHorizon * p->sort_every * p->dt / p->dy) : 0.f;
+  g.pcz = pred && p->nz > 1 ? (float)(kSortHorizon * p->sort_every * p->dt / p->dz) : 0.f;
   return g;
 }
 

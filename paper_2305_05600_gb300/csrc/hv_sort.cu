@@ -307,11 +307,12 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 // The step's sort: a stable counting sort of the ions by supercell key (tile,
 // then cell in the tile); ions with equal keys keep the order they had.  An
 // ion's key cell is its cell moved by at most one cell along an axis on
-// which its offset plus its velocity times sort_every * dt / Delta leaves
-// [-1, 1): the cell it is predicted to reach half a sort interval later
-// (pred_shift; none with open faces).  Ions leave their sorted cells in both
-// directions between two sorts instead of in one, which halves the deposit
-// runs the push has to break.  Two paths give the same permutation:
+// which its offset plus its velocity times kSortHorizon * sort_every * dt /
+// Delta leaves [-1, 1): the cell it is predicted to reach 0.6875 sort
+// intervals later (pred_shift; none with open faces).  Ions leave their
+// sorted cells in both directions between two sorts instead of in one,
+// which halves the deposit runs the push has to break.  Two paths give the
+// same permutation:
 //
 // General path (the first sort after loading, long sort intervals): the keys
 // go through the stable radix passes above, the ions are gathered by the

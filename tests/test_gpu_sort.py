@@ -3,9 +3,9 @@
 The library sorts every species by supercell key (tile index, then the cell
 inside the tile) every sort_every steps, keeping the order of ions with
 equal keys.  The key cell of an ion is its cell moved by at most one cell
-along each axis toward where it is predicted to be half a sort interval
-later (off + v * sort_every * dt / Delta outside [-1, 1), FP32;
-oracle.supercell_keys restates it).  Ions are identified by distinct weights, which the library
+along each axis toward where it is predicted to be 0.6875 sort intervals
+later (off + v * 1.375 * sort_every * dt / Delta outside [-1, 1), FP32;
+oracle.supercell_keys and oracle.sort_pred_coeffs restate it).  Ions are identified by distinct weights, which the library
 copies bit for bit, so the order hv_get_ions reports after a step is the
 sort's permutation applied to the order before it (the push moves ions
 in place).  Each sort is checked against oracle.sort_stable on the keys of

@@ -53,3 +53,13 @@ def test_predicted_key_cell_within_one_and_zero_pc_is_plain():
         q = off[a].astype(np.float64) + v[a].astype(np.float64) * 0.4
         assert (d[np.abs(q) < 0.999] == 0).all()
         assert (d[q > 1.001] == 1).all() and (d[q < -1.001] == -1).all()
+
+
+def test_prediction_coefficients():
+    # 1.375 * sort_every * dt / Delta in FP32 per axis with more than one
+    # cell; none without sorting or with open faces
+    p = dict(nx=8, ny=1, nz=4, dx=0.25, dy=1.0, dz=0.5, dt=0.02, sort_every=8)
+    pc = O.sort_pred_coeffs(p)
+    assert pc == (np.float32(0.88), np.float32(0.0), np.float32(0.44))
+    assert all(c == 0 for c in O.sort_pred_coeffs(dict(p, sort_every=0)))
+    assert all(c == 0 for c in O.sort_pred_coeffs(dict(p, open_faces=1)))
