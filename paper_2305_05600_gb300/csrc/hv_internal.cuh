@@ -289,7 +289,7 @@ struct PushConsts {
   float cx, cy, cz;     // dt / Delta per axis (0 for single-cell axes)
   float qvc;            // q / V_c
   float ic2;            // 1 / c^2 (relativistic push only)
-  float mass;           // m
+  double mass_d;        // m, applied to the FP64 energy and momentum sums
 };
 
 struct SortScratch;

@@ -621,12 +621,13 @@ __device__ __forceinline__ int push_ion(const PushArgs &a, const void *eb, int i
     vx = unx;
     vy = uny;
     vz = unz;
-    const float mw = a.k.mass * w;
+    // w |u|^2 (over gamma + 1) and w u; the species mass (and the 1/2 of
+    // the non-relativistic energy) is applied to the FP64 block sums
     const float uu = unx * unx + uny * uny + unz * unz;
-    rk[0] += REL ? mw * uu * __frcp_rn(gam + 1.f) : 0.5f * mw * uu;
-    rk[1] += mw * unx;
-    rk[2] += mw * uny;
-    rk[3] += mw * unz;
+    rk[0] = REL ? fmaf(w * uu, __frcp_rn(gam + 1.f), rk[0]) : fmaf(w, uu, rk[0]);
+    rk[1] = fmaf(w, unx, rk[1]);
+    rk[2] = fmaf(w, uny, rk[2]);
+    rk[3] = fmaf(w, unz, rk[3]);
   } else if (REL) {
     // start-up deposit of a relativistic particle: v = u / gamma
     const float ig = __frcp_rn(sqrtf(1.f + (vx * vx + vy * vy + vz * vz) * a.k.ic2));
@@ -873,7 +874,9 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
     if (threadIdx.x < 4) {
       double s = 0.0;
       for (int w = 0; w < nwarps; ++w) s += red[w][threadIdx.x];
-      a.part[(int64_t)blockIdx.x * 4 + threadIdx.x] = s;
+      const double m = a.k.mass_d;
+      a.part[(int64_t)blockIdx.x * 4 + threadIdx.x] =
+          s * (threadIdx.x == 0 && MODE < 2 ? 0.5 * m : m);
     }
   }
 }
@@ -927,7 +930,7 @@ cudaError_t launch_push(hv_ctx *c, int species, int mode) {
   a.k.cz = c->g.nz > 1 ? (float)(c->p.dt / c->p.dz) : 0.f;
   a.k.qvc = (float)(sp.q / c->vc);
   a.k.ic2 = c->p.relativistic ? (float)(1.0 / (c->p.c_light * c->p.c_light)) : 0.f;
-  a.k.mass = (float)sp.m;
+  a.k.mass_d = sp.m;
   a.part = c->pushpart + (size_t)species * c->push_blocks * 4;
   a.err = c->err;
   c->launches++;
