@@ -145,7 +145,10 @@ constexpr int kErrCapacity = 16;
 // interval; the push over an interval of 8 was fastest at 1.375 (measured
 // 1, 1.125, 1.25, 1.375, 1.5), where it spends alike on ions that have not
 // yet reached their key cell and on ions that have passed it.
-constexpr double kSortHorizon = 1.375;
+#ifndef HV_SORT_HORIZON
+#define HV_SORT_HORIZON 1.375
+#endif
+constexpr double kSortHorizon = HV_SORT_HORIZON;
 
 // Tile extents of the supercell order: 16x16 cells in the x-z layout,
 // 8x8x8 cells in 3D (cells per tile a power of two).
