@@ -32,6 +32,16 @@
 #ifndef HV_PUSH_MIN_BLOCKS
 #define HV_PUSH_MIN_BLOCKS 5
 #endif
+// 3D: threads per block and the resident blocks per SM the registers are
+// budgeted for (3 blocks of 128 threads fit by shared memory; 2 blocks of
+// 256 threads at 128 registers gave 16 warps per SM instead of 12 but the
+// same push time)
+#ifndef HV_PUSH_THREADS_3D
+#define HV_PUSH_THREADS_3D 128
+#endif
+#ifndef HV_PUSH_MIN_BLOCKS_3D
+#define HV_PUSH_MIN_BLOCKS_3D 2
+#endif
 #ifndef HV_PUSH_CHUNK
 #define HV_PUSH_CHUNK 8
 #endif
@@ -48,7 +58,10 @@ namespace hv {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = HV_PUSH_THREADS;
+template <int DIM>
+__host__ __device__ constexpr int threads_of() {
+  return DIM == 2 ? HV_PUSH_THREADS : HV_PUSH_THREADS_3D;
+}
 constexpr int kChunk = HV_PUSH_CHUNK;  // consecutive ions per lane per tile
 constexpr int kTile = 32 * kChunk;     // ions per warp tile
 constexpr int kGroup = HV_PUSH_GROUP;  // ions a lane moves with one vector access
@@ -394,7 +407,7 @@ struct WinCell {
 //   eb:    E, B of the window, 2 float4 per cell
 template <int DIM, int SHAPE>
 struct Layout {
-  static constexpr int NW = kThreads / 32;
+  static constexpr int NW = threads_of<DIM>() / 32;
   static constexpr int NA = DIM == 2 ? 7 : 8;  // cell, ox, [oy], oz, vx, vy, vz, w
   static constexpr size_t stage_bytes = (size_t)NA * kTile * 4;
   static constexpr size_t off_eb = align_up(stage_bytes * NW, 16);
@@ -711,7 +724,8 @@ struct Run {
 // staging tile is written back in place with bulk copies.
 template <int DIM, int SHAPE, int MODE>
 // (3D: the larger staging and window buffers allow two blocks per SM)
-__global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
+__global__ void __launch_bounds__(threads_of<DIM>(),
+                                  DIM == 2 ? HV_PUSH_MIN_BLOCKS : HV_PUSH_MIN_BLOCKS_3D)
     push_kernel(PushArgs a) {
   pdl_begin();
   constexpr bool PUSH = (MODE & 1) == 0;  // full step (not the start-up deposit)
@@ -725,6 +739,7 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? HV_PUSH_MIN_BLOCKS : 2)
   const Geom &g = a.g;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  constexpr int kThreads = threads_of<DIM>();
   constexpr int nwarps = kThreads / 32;
   float(&T)[NA][kTile] = *reinterpret_cast<float(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
   int(&TC)[NA][kTile] = *reinterpret_cast<int(*)[NA][kTile]>(smem_raw + L::stage_bytes * warp);
@@ -894,7 +909,7 @@ cudaError_t launch_t(const PushArgs &a, int blocks, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // an ordinary launch: the push may follow a wait on the side stream's
   // sort, which a programmatic launch must not overtake
-  push_kernel<DIM, SHAPE, MODE><<<blocks, kThreads, smem, s>>>(a);
+  push_kernel<DIM, SHAPE, MODE><<<blocks, threads_of<DIM>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 
