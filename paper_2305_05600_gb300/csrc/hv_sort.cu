@@ -551,16 +551,22 @@ __global__ void __launch_bounds__(256) wsort_prefix_kernel(Geom g, int32_t *wcnt
           }
           cand[p] = v;
         }
-    int run = 0;
+    // the windows that hold the cell, their counts all loaded before any
+    // prefix is stored (the loads overlap instead of waiting on each store)
+    int at[27], cn[27];
+    int m = 0;
     for (int q = 0; q < nc; ++q) {
       int x0, y0, z0;
       tile_origin<DIM>(g, cand[q], x0, y0, z0);
       const int s = win_slot<DIM>(g, x0, y0, z0, i, j, k);
       if (s < 0) continue;
-      int32_t *p = wcnt + (size_t)cand[q] * SW::NS + s;
-      const int c = *p;
-      *p = run;
-      run += c;
+      at[m++] = cand[q] * SW::NS + s;
+    }
+    for (int q = 0; q < m; ++q) cn[q] = wcnt[at[q]];
+    int run = 0;
+    for (int q = 0; q < m; ++q) {
+      wcnt[at[q]] = run;
+      run += cn[q];
     }
     cnt[key] = run;
   }
