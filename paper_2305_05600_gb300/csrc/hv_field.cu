@@ -854,18 +854,65 @@ __global__ void __launch_bounds__(st3d::kThreads, 2) stage3d_kernel(StageArgs a)
 // reaches 2 cells (J = curl B, then lap J) and each curl of E one more.
 // Every input is loaded once into shared memory; both stages then run from
 // there.
+//
+// Each thread takes two x-adjacent cells at a time: the pair's own and its
+// z-neighbours' operands are one 8-byte shared load for both cells, and only
+// the two outer x-neighbours are single loads.  For that every array starts
+// at an even x and has an even width; a region whose halo is odd grows by a
+// column on each side.  Those extra columns read one cell past the end of
+// their row (still inside the array) and hold values that no valid cell of
+// the next stage reads.
 // ----------------------------------------------------------------------------
 namespace sub2d {
 constexpr int SX = 32, SZ = 16, SH = 6;
-__host__ __device__ constexpr int W(int r) { return SX + 2 * r; }
-__host__ __device__ constexpr int N(int r) { return (SX + 2 * r) * (SZ + 2 * r); }
-constexpr int kB = 0;                          // B on R6 (3 planes)
-constexpr int kM = kB + 3 * N(6);              // on R5: p_e, 1/n_f, Jix, Jiy, Jiz
-constexpr int kJ = kM + 5 * N(5);              // J on R5 (stage 1) / R2 (stage 2)
-constexpr int kE = kJ + 3 * N(5);              // E on R4 (stage 1) / R1 (stage 2)
-constexpr int kS = kE + 3 * N(4);              // B* on R3
-constexpr int kFloats = kS + 3 * N(3);
-__device__ __forceinline__ int at(int r, int x, int z) { return (x + r) + (z + r) * W(r); }
+// tile-local array over x in [OX, OX + WW), z in [OZ, OZ + HH), row-major
+template <int OX, int WW, int OZ, int HH>
+struct Reg {
+  static_assert(OX % 2 == 0 && WW % 2 == 0, "cell pairs start at an even x");
+  static constexpr int ox = OX, w = WW, oz = OZ, h = HH, n = WW * HH, pairs = WW / 2 * HH;
+  __device__ static __forceinline__ int at(int x, int z) { return (x - OX) + (z - OZ) * WW; }
+};
+using RB = Reg<-6, SX + 12, -6, SZ + 12>;   // B
+using RM = Reg<-6, SX + 12, -5, SZ + 10>;   // p_e, 1/n_f, J_i
+using RJ1 = Reg<-6, SX + 12, -5, SZ + 10>;  // J = curl B, valid on x in [-5, SX + 5)
+using RE1 = Reg<-4, SX + 8, -4, SZ + 8>;    // E(B)
+using RS = Reg<-4, SX + 8, -3, SZ + 6>;     // B*, valid on x in [-3, SX + 3)
+using RJ2 = Reg<-2, SX + 4, -2, SZ + 4>;    // J = curl B*
+using RE2 = Reg<-2, SX + 4, -1, SZ + 2>;    // E(B*), valid on x in [-1, SX + 1)
+using R0 = Reg<0, SX, 0, SZ>;               // B_out
+constexpr int kB = 0;                       // B (3 planes)
+constexpr int kM = kB + 3 * RB::n;          // p_e, 1/n_f, Jix, Jiy, Jiz
+constexpr int kJ = kM + 5 * RM::n;          // J (stage 1, then stage 2)
+constexpr int kE = kJ + 3 * RJ1::n;         // E (stage 1, then stage 2)
+constexpr int kS = kE + 3 * RE1::n;         // B*
+constexpr int kFloats = kS + 3 * RS::n;
+static_assert(RJ2::n <= RJ1::n && RE2::n <= RE1::n, "stage 2 reuses the stage-1 arrays");
+static_assert(RB::n % 2 == 0 && RM::n % 2 == 0 && RJ1::n % 2 == 0 && RE1::n % 2 == 0 &&
+                  RS::n % 2 == 0 && RJ2::n % 2 == 0 && RE2::n % 2 == 0,
+              "every plane starts 8-byte aligned");
+__device__ __forceinline__ float2 ld2(const float *p) {
+  return *reinterpret_cast<const float2 *>(p);
+}
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+struct Pair3 {
+  float2 x, y, z;
+};
+// curl V at cells (x, z) and (x + 1, z) from V on region R (y derivatives
+// vanish in the x-z layout): J = curl B and the curl of E in Faraday's law
+template <class R>
+__device__ __forceinline__ Pair3 curl_pair(const FieldConsts &k, const float *V, int x, int z) {
+  const float *Vx = V, *Vy = V + R::n, *Vz = V + 2 * R::n;
+  const int b = R::at(x, z), w = R::w;
+  const float2 yu = ld2(Vy + b + w), yd = ld2(Vy + b - w), yc = ld2(Vy + b);
+  const float2 xu = ld2(Vx + b + w), xd = ld2(Vx + b - w), zc = ld2(Vz + b);
+  const float yl = Vy[b - 1], yr = Vy[b + 2], zl = Vz[b - 1], zr = Vz[b + 2];
+  Pair3 c;
+  c.x = make_float2(-(yu.x - yd.x) * k.idz2, -(yu.y - yd.y) * k.idz2);
+  c.y = make_float2((xu.x - xd.x) * k.idz2 - (zc.y - zl) * k.idx2,
+                    (xu.y - xd.y) * k.idz2 - (zr - zc.x) * k.idx2);
+  c.z = make_float2((yc.y - yl) * k.idx2, (yr - yc.x) * k.idx2);
+  return c;
+}
 }  // namespace sub2d
 
 struct SubArgs {
@@ -878,50 +925,53 @@ struct SubArgs {
   float h;
 };
 
-// E from Ohm's law at tile point (x, z), with B, J on their own regions and
-// p_e, 1/n_f and J_i per cell on R5 (computed once per cell at load).
-// With an external field (B = B0 + B1 split, Sec. 2.3) Bp holds B1 and
-// (b0x, b0y, b0z) is B0 at the point: J = curl B1, the cross products take
-// the total field.
-__device__ __forceinline__ void ohm2d(const float *sm, const FieldConsts &k, int x, int z,
-                                      const float *Bp, int rb, const float *Jp, int rj,
-                                      float b0x, float b0y, float b0z,
-                                      float &ex, float &ey, float &ez) {
-  using namespace sub2d;
-  const int nb = N(rb), nj = N(rj), nm = N(5);
-  const float *pe = sm + kM, *invn = pe + nm, *mjx = invn + nm, *mjy = mjx + nm, *mjz = mjy + nm;
-  const int im = at(5, x, z);
-  const float gpx = (pe[im + 1] - pe[im - 1]) * k.idx2;
-  const float gpz = (pe[im + W(5)] - pe[im - W(5)]) * k.idz2;
-  const int ij = at(rj, x, z), wj = W(rj);
-  const float *Jx = Jp, *Jy = Jp + nj, *Jz = Jp + 2 * nj;
-  const float jx = Jx[ij], jy = Jy[ij], jz = Jz[ij];
-  const float lx = (Jx[ij + 1] + Jx[ij - 1] - 2.f * jx) * k.ilx + (Jx[ij + wj] + Jx[ij - wj] - 2.f * jx) * k.ilz;
-  const float ly = (Jy[ij + 1] + Jy[ij - 1] - 2.f * jy) * k.ilx + (Jy[ij + wj] + Jy[ij - wj] - 2.f * jy) * k.ilz;
-  const float lz = (Jz[ij + 1] + Jz[ij - 1] - 2.f * jz) * k.ilx + (Jz[ij + wj] + Jz[ij - wj] - 2.f * jz) * k.ilz;
-  const int ib = at(rb, x, z);
-  const float bx = Bp[ib] + b0x, by = Bp[nb + ib] + b0y, bz = Bp[2 * nb + ib] + b0z;
-  const float ux = jx - mjx[im], uy = jy - mjy[im], uz = jz - mjz[im];
-  const float inv = invn[im];
+// E from Ohm's law at one cell from its operands: the pressure gradient, J
+// and lap J, the total B, the ion current J_i and 1/n_f.
+__device__ __forceinline__ void ohm_cell(const FieldConsts &k, float gpx, float gpz, float jx,
+                                         float jy, float jz, float lx, float ly, float lz,
+                                         float bx, float by, float bz, float mx, float my,
+                                         float mz, float inv, float &ex, float &ey, float &ez) {
+  const float ux = jx - mx, uy = jy - my, uz = jz - mz;
   ex = ((uy * bz - uz * by) - gpx) * inv + k.eta * jx - k.eta_h * lx;
   ey = (uz * bx - ux * bz) * inv + k.eta * jy - k.eta_h * ly;
   ez = ((ux * by - uy * bx) - gpz) * inv + k.eta * jz - k.eta_h * lz;
 }
 
-// J = curl B (y derivatives vanish in the x-z layout) on region rj from B on rb.
-template <int rb, int rj>
-__device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, float *Jp) {
+// E from Ohm's law at cells (x, z), (x + 1, z), with B on region RBs, J on
+// RJs, and p_e, 1/n_f, J_i per cell (computed once per cell at load).  With
+// an external field (B = B0 + B1 split, Sec. 2.3) Bp holds B1 and b0, b1 are
+// B0 at the two cells: J = curl B1, the cross products take the total field.
+template <class RBs, class RJs>
+__device__ __forceinline__ void ohm_pair(const float *sm, const FieldConsts &k, int x, int z,
+                                         const float *Bp, const float *Jp, float4 b0, float4 b1,
+                                         sub2d::Pair3 &e) {
   using namespace sub2d;
-  const int nb = N(rb), nj = N(rj), wb = W(rb);
-  for (int t_ = (int)threadIdx.x; t_ < N(rj); t_ += blockDim.x) {
-      const int x = t_ % W(rj) - rj, z = t_ / W(rj) - rj;
-      const int b = at(rb, x, z);
-      const float *Bx = Bp, *By = Bp + nb, *Bz = Bp + 2 * nb;
-      const int j = at(rj, x, z);
-      Jp[j] = -(By[b + wb] - By[b - wb]) * k.idz2;
-      Jp[nj + j] = (Bx[b + wb] - Bx[b - wb]) * k.idz2 - (Bz[b + 1] - Bz[b - 1]) * k.idx2;
-      Jp[2 * nj + j] = (By[b + 1] - By[b - 1]) * k.idx2;
-    }
+  const float *pe = sm + kM, *invn = pe + RM::n, *mjx = invn + RM::n, *mjy = mjx + RM::n,
+              *mjz = mjy + RM::n;
+  const int im = RM::at(x, z);
+  const float2 pc = ld2(pe + im), pu = ld2(pe + im + RM::w), pd = ld2(pe + im - RM::w);
+  const float pl = pe[im - 1], pr = pe[im + 2];
+  const float2 nv = ld2(invn + im), m_x = ld2(mjx + im), m_y = ld2(mjy + im),
+               m_z = ld2(mjz + im);
+  const int ij = RJs::at(x, z), wj = RJs::w;
+  float2 jc[3], lp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float *J = Jp + c * RJs::n;
+    const float2 cc = ld2(J + ij), uu = ld2(J + ij + wj), dd = ld2(J + ij - wj);
+    const float l = J[ij - 1], r = J[ij + 2];
+    jc[c] = cc;
+    lp[c] = make_float2((cc.y + l - 2.f * cc.x) * k.ilx + (uu.x + dd.x - 2.f * cc.x) * k.ilz,
+                        (r + cc.x - 2.f * cc.y) * k.ilx + (uu.y + dd.y - 2.f * cc.y) * k.ilz);
+  }
+  const int ib = RBs::at(x, z);
+  const float2 bx = ld2(Bp + ib), by = ld2(Bp + RBs::n + ib), bz = ld2(Bp + 2 * RBs::n + ib);
+  ohm_cell(k, (pc.y - pl) * k.idx2, (pu.x - pd.x) * k.idz2, jc[0].x, jc[1].x, jc[2].x, lp[0].x,
+           lp[1].x, lp[2].x, bx.x + b0.x, by.x + b0.y, bz.x + b0.z, m_x.x, m_y.x, m_z.x, nv.x,
+           e.x.x, e.y.x, e.z.x);
+  ohm_cell(k, (pr - pc.x) * k.idx2, (pu.y - pd.y) * k.idz2, jc[0].y, jc[1].y, jc[2].y, lp[0].y,
+           lp[1].y, lp[2].y, bx.y + b1.x, by.y + b1.y, bz.y + b1.z, m_x.y, m_y.y, m_z.y, nv.y,
+           e.x.y, e.y.y, e.z.y);
 }
 
 // threads per block of the fused subcycle kernel
@@ -930,10 +980,18 @@ __device__ __forceinline__ void curl2d(const FieldConsts &k, const float *Bp, fl
 #endif
 constexpr int kSubThreads = HV_SUB_THREADS;
 
+// f(x, z) for every cell pair (x, z), (x + 1, z) of region R, pairs spread
+// over the block's threads in row-major order
+template <class R, class F>
+__device__ __forceinline__ void for_pairs(F f) {
+  for (int t = (int)threadIdx.x; t < R::pairs; t += kSubThreads)
+    f(R::ox + 2 * (t % (R::w / 2)), R::oz + t / (R::w / 2));
+}
+
 __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
   pdl_begin();
   using namespace sub2d;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const Geom &g = a.g;
   const FieldConsts &k = a.k;
   const int ntx = (g.nx + SX - 1) / SX;
@@ -944,102 +1002,127 @@ __global__ void __launch_bounds__(kSubThreads) substep2d_kernel(SubArgs a) {
     const int kk = wrap_near(z0 + z, g.nz, SZ + SH);
     return ii + g.nx * kk;
   };
-  // load B on R6 and the moments on R5: every thread issues all its loads
-  // before it stores any, so the L2 latencies overlap
+  // load B on RB and the moments on RM, two cells per pair: every thread
+  // issues all its loads before it stores any, so the L2 latencies overlap
   {
-    constexpr int LB = (N(6) + kSubThreads - 1) / kSubThreads;
-    constexpr int LM = (N(5) + kSubThreads - 1) / kSubThreads;
-    float4 bv[LB], mv[LM];
+    constexpr int LB = (RB::pairs + kSubThreads - 1) / kSubThreads;
+    constexpr int LM = (RM::pairs + kSubThreads - 1) / kSubThreads;
+    float4 bv[2 * LB], mv[2 * LM];
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
-      const int t_ = (int)threadIdx.x + u * kSubThreads;
-      if (t_ < N(6)) bv[u] = a.B[gidx(t_ % W(6) - 6, t_ / W(6) - 6)];
-    }
-#pragma unroll
-    for (int u = 0; u < LM; ++u) {
-      const int t_ = (int)threadIdx.x + u * kSubThreads;
-      if (t_ < N(5)) mv[u] = a.mom[gidx(t_ % W(5) - 5, t_ / W(5) - 5)];
-    }
-#pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int t_ = (int)threadIdx.x + u * kSubThreads;
-      if (t_ < N(6)) {
-        const int i = at(6, t_ % W(6) - 6, t_ / W(6) - 6);
-        Bp[i] = bv[u].x;
-        Bp[N(6) + i] = bv[u].y;
-        Bp[2 * N(6) + i] = bv[u].z;
+      const int t = (int)threadIdx.x + u * kSubThreads;
+      if (t < RB::pairs) {
+        const int x = RB::ox + 2 * (t % (RB::w / 2)), z = RB::oz + t / (RB::w / 2);
+        bv[2 * u] = a.B[gidx(x, z)];
+        bv[2 * u + 1] = a.B[gidx(x + 1, z)];
       }
     }
 #pragma unroll
     for (int u = 0; u < LM; ++u) {
-      const int t_ = (int)threadIdx.x + u * kSubThreads;
-      if (t_ < N(5)) {
+      const int t = (int)threadIdx.x + u * kSubThreads;
+      if (t < RM::pairs) {
+        const int x = RM::ox + 2 * (t % (RM::w / 2)), z = RM::oz + t / (RM::w / 2);
+        mv[2 * u] = a.mom[gidx(x, z)];
+        mv[2 * u + 1] = a.mom[gidx(x + 1, z)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = (int)threadIdx.x + u * kSubThreads;
+      if (t < RB::pairs) {
+        const int i = 2 * t;  // the pair's index in row-major order
+        const float4 c0 = bv[2 * u], c1 = bv[2 * u + 1];
+        st2(Bp + i, make_float2(c0.x, c1.x));
+        st2(Bp + RB::n + i, make_float2(c0.y, c1.y));
+        st2(Bp + 2 * RB::n + i, make_float2(c0.z, c1.z));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LM; ++u) {
+      const int t = (int)threadIdx.x + u * kSubThreads;
+      if (t < RM::pairs) {
+        const int i = 2 * t;
+        const float4 c0 = mv[2 * u], c1 = mv[2 * u + 1];
         // p_e and 1/n_f once per cell (the floor enters both, Sec. 2.1)
-        const float f = fmaxf(mv[u].x, k.n_floor);
-        Mp[t_] = k.isothermal ? k.Te * f : k.Te * powf(f, k.gamma_e);
-        Mp[N(5) + t_] = __frcp_rn(f);
-        Mp[2 * N(5) + t_] = mv[u].y;
-        Mp[3 * N(5) + t_] = mv[u].z;
-        Mp[4 * N(5) + t_] = mv[u].w;
+        const float f0 = fmaxf(c0.x, k.n_floor), f1 = fmaxf(c1.x, k.n_floor);
+        st2(Mp + i, k.isothermal ? make_float2(k.Te * f0, k.Te * f1)
+                                 : make_float2(k.Te * powf(f0, k.gamma_e),
+                                               k.Te * powf(f1, k.gamma_e)));
+        st2(Mp + RM::n + i, make_float2(__frcp_rn(f0), __frcp_rn(f1)));
+        st2(Mp + 2 * RM::n + i, make_float2(c0.y, c1.y));
+        st2(Mp + 3 * RM::n + i, make_float2(c0.z, c1.z));
+        st2(Mp + 4 * RM::n + i, make_float2(c0.w, c1.w));
       }
     }
   }
   __syncthreads();
-  // stage 1: J(B) on R5, E on R4, B* on R3
-  curl2d<6, 5>(k, Bp, Jp);
+  // stage 1: J(B), E(B), B* = B - (h/2) curl E
+  for_pairs<RJ1>([&](int x, int z) {
+    const Pair3 c = curl_pair<RB>(k, Bp, x, z);
+    const int j = RJ1::at(x, z);
+    st2(Jp + j, c.x);
+    st2(Jp + RJ1::n + j, c.y);
+    st2(Jp + 2 * RJ1::n + j, c.z);
+  });
   __syncthreads();
-  for (int t_ = (int)threadIdx.x; t_ < N(4); t_ += blockDim.x) {
-      const int x = t_ % W(4) - 4, z = t_ / W(4) - 4;
-      float ex, ey, ez;
-      float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (a.B0) b0 = __ldg(a.B0 + gidx(x, z));
-      ohm2d(sm, k, x, z, Bp, 6, Jp, 5, b0.x, b0.y, b0.z, ex, ey, ez);
-      const int i = at(4, x, z);
-      Ep[i] = ex;
-      Ep[N(4) + i] = ey;
-      Ep[2 * N(4) + i] = ez;
+  for_pairs<RE1>([&](int x, int z) {
+    float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+    if (a.B0) {
+      b0 = __ldg(a.B0 + gidx(x, z));
+      b1 = __ldg(a.B0 + gidx(x + 1, z));
     }
+    Pair3 e;
+    ohm_pair<RB, RJ1>(sm, k, x, z, Bp, Jp, b0, b1, e);
+    const int i = RE1::at(x, z);
+    st2(Ep + i, e.x);
+    st2(Ep + RE1::n + i, e.y);
+    st2(Ep + 2 * RE1::n + i, e.z);
+  });
   __syncthreads();
   const float c1 = 0.5f * a.h;
-  for (int t_ = (int)threadIdx.x; t_ < N(3); t_ += blockDim.x) {
-      const int x = t_ % W(3) - 3, z = t_ / W(3) - 3;
-      const int e = at(4, x, z), w = W(4), b = at(6, x, z), s = at(3, x, z);
-      const float *Ex = Ep, *Ey = Ep + N(4), *Ez = Ep + 2 * N(4);
-      const float cx = -(Ey[e + w] - Ey[e - w]) * k.idz2;
-      const float cy = (Ex[e + w] - Ex[e - w]) * k.idz2 - (Ez[e + 1] - Ez[e - 1]) * k.idx2;
-      const float cz = (Ey[e + 1] - Ey[e - 1]) * k.idx2;
-      Sp[s] = Bp[b] - c1 * cx;
-      Sp[N(3) + s] = Bp[N(6) + b] - c1 * cy;
-      Sp[2 * N(3) + s] = Bp[2 * N(6) + b] - c1 * cz;
-    }
+  for_pairs<RS>([&](int x, int z) {
+    const Pair3 c = curl_pair<RE1>(k, Ep, x, z);
+    const int b = RB::at(x, z), s = RS::at(x, z);
+    const float2 bx = ld2(Bp + b), by = ld2(Bp + RB::n + b), bz = ld2(Bp + 2 * RB::n + b);
+    st2(Sp + s, make_float2(bx.x - c1 * c.x.x, bx.y - c1 * c.x.y));
+    st2(Sp + RS::n + s, make_float2(by.x - c1 * c.y.x, by.y - c1 * c.y.y));
+    st2(Sp + 2 * RS::n + s, make_float2(bz.x - c1 * c.z.x, bz.y - c1 * c.z.y));
+  });
   __syncthreads();
-  // stage 2: J(B*) on R2, E on R1, B_out on the tile
-  curl2d<3, 2>(k, Sp, Jp);
+  // stage 2: J(B*), E(B*), B_out = B - h curl E
+  for_pairs<RJ2>([&](int x, int z) {
+    const Pair3 c = curl_pair<RS>(k, Sp, x, z);
+    const int j = RJ2::at(x, z);
+    st2(Jp + j, c.x);
+    st2(Jp + RJ2::n + j, c.y);
+    st2(Jp + 2 * RJ2::n + j, c.z);
+  });
   __syncthreads();
-  for (int t_ = (int)threadIdx.x; t_ < N(1); t_ += blockDim.x) {
-      const int x = t_ % W(1) - 1, z = t_ / W(1) - 1;
-      float ex, ey, ez;
-      float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (a.B0) b0 = __ldg(a.B0 + gidx(x, z));
-      ohm2d(sm, k, x, z, Sp, 3, Jp, 2, b0.x, b0.y, b0.z, ex, ey, ez);
-      const int i = at(1, x, z);
-      Ep[i] = ex;
-      Ep[N(1) + i] = ey;
-      Ep[2 * N(1) + i] = ez;
+  for_pairs<RE2>([&](int x, int z) {
+    float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+    if (a.B0) {
+      b0 = __ldg(a.B0 + gidx(x, z));
+      b1 = __ldg(a.B0 + gidx(x + 1, z));
     }
+    Pair3 e;
+    ohm_pair<RS, RJ2>(sm, k, x, z, Sp, Jp, b0, b1, e);
+    const int i = RE2::at(x, z);
+    st2(Ep + i, e.x);
+    st2(Ep + RE2::n + i, e.y);
+    st2(Ep + 2 * RE2::n + i, e.z);
+  });
   __syncthreads();
-  for (int t_ = (int)threadIdx.x; t_ < SX * SZ; t_ += blockDim.x) {
-      const int x = t_ % SX, z = t_ / SX;
-      const int gx = x0 + x, gz = z0 + z;
-      if (gx >= g.nx || gz >= g.nz) continue;
-      const int e = at(1, x, z), w = W(1), b = at(6, x, z);
-      const float *Ex = Ep, *Ey = Ep + N(1), *Ez = Ep + 2 * N(1);
-      const float cx = -(Ey[e + w] - Ey[e - w]) * k.idz2;
-      const float cy = (Ex[e + w] - Ex[e - w]) * k.idz2 - (Ez[e + 1] - Ez[e - 1]) * k.idx2;
-      const float cz = (Ey[e + 1] - Ey[e - 1]) * k.idx2;
-      a.Bout[gx + g.nx * gz] = make_float4(Bp[b] - a.h * cx, Bp[N(6) + b] - a.h * cy,
-                                           Bp[2 * N(6) + b] - a.h * cz, 0.f);
-    }
+  for_pairs<R0>([&](int x, int z) {
+    const int gx = x0 + x, gz = z0 + z;
+    if (gz >= g.nz || gx >= g.nx) return;
+    const Pair3 c = curl_pair<RE2>(k, Ep, x, z);
+    const int b = RB::at(x, z);
+    const float2 bx = ld2(Bp + b), by = ld2(Bp + RB::n + b), bz = ld2(Bp + 2 * RB::n + b);
+    float4 *out = a.Bout + gx + g.nx * gz;
+    out[0] = make_float4(bx.x - a.h * c.x.x, by.x - a.h * c.y.x, bz.x - a.h * c.z.x, 0.f);
+    if (gx + 1 < g.nx)
+      out[1] = make_float4(bx.y - a.h * c.x.y, by.y - a.h * c.y.y, bz.y - a.h * c.z.y, 0.f);
+  });
 }
 
 FieldConsts field_consts(const hv_ctx *c) {
