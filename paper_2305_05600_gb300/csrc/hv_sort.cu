@@ -15,7 +15,10 @@
 //   scan      exclusive scan of the table in digit-major order
 //   downsweep stable per-tile ranks (warp match + per-warp counters) and
 //             scatter to table offset + rank.
-// A final gather applies the permutation to the particle arrays.
+// The particles are then gathered by the permutation, or (after an earlier
+// sort) the last pass writes every original index's sorted position instead
+// and a final pass reads the particle arrays in order and stores every
+// particle at its position.
 #include <algorithm>
 
 #include "hv_internal.cuh"
@@ -39,6 +42,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScanChunk = 4096;
 
+// radix passes: a lane loads all of its 16 items before it counts or ranks
+// any (off: item by item)
+#ifndef HV_RADIX_PREFETCH
+#define HV_RADIX_PREFETCH 1
+#endif
+
 // Items of a tile are split into one contiguous run of 512 per warp; round r
 // of warp w covers tile items w*512 + r*32 + lane, so lane order within a
 // round and round order within a warp follow input order.
@@ -54,12 +63,26 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const int32_t *keys, 
   hist[threadIdx.x] = 0;
   __syncthreads();
   const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+#if HV_RADIX_PREFETCH
+  // every key of the lane loaded before the first count
+  int key[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t idx = item_index(tile0, warp, r, lane);
+    key[r] = idx < n ? keys[idx] : 0;
+  }
+#pragma unroll
+#endif
   for (int r = 0; r < kItems; ++r) {
     const int64_t idx = item_index(tile0, warp, r, lane);
     const bool valid = idx < n;
     const unsigned act = __ballot_sync(kFull, valid);
     if (!valid) continue;
+#if HV_RADIX_PREFETCH
+    const int d = (int)(((uint32_t)key[r] >> shift) & 255u);
+#else
     const int d = (int)(((uint32_t)keys[idx] >> shift) & 255u);
+#endif
     const unsigned peers = __match_any_sync(act, d);
     if (lane == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
   }
@@ -151,12 +174,15 @@ __global__ void __launch_bounds__(kThreads) chunk_scan_kernel(int32_t *a, int64_
   }
 }
 
+// vals_out receives the values in sorted order, or with `inverse` the
+// sorted position of every value at index value (the inverse permutation
+// when the values are the original indices).
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys_in,
                                                               const int32_t *vals_in, int64_t n,
                                                               int shift, int64_t ntiles,
                                                               const int32_t *table,
                                                               int32_t *keys_out,
-                                                              int32_t *vals_out) {
+                                                              int32_t *vals_out, bool inverse) {
   __shared__ int wcount[kWarps][256];
   __shared__ int gbase[256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -165,12 +191,24 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys
   __syncthreads();
   const int64_t tile0 = (int64_t)blockIdx.x * kTile;
   int key[kItems], val[kItems], rank[kItems];
+#if HV_RADIX_PREFETCH
+  // every key and value of the lane loaded before the first rank
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t idx = item_index(tile0, warp, r, lane);
     const bool valid = idx < n;
     key[r] = valid ? keys_in[idx] : 0;
     val[r] = valid ? (vals_in ? vals_in[idx] : (int)idx) : 0;
+  }
+#endif
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t idx = item_index(tile0, warp, r, lane);
+    const bool valid = idx < n;
+#if !HV_RADIX_PREFETCH
+    key[r] = valid ? keys_in[idx] : 0;
+    val[r] = valid ? (vals_in ? vals_in[idx] : (int)idx) : 0;
+#endif
     rank[r] = -1;
     const unsigned act = __ballot_sync(kFull, valid);
     if (valid) {
@@ -200,7 +238,8 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys
     const int d = (int)(((uint32_t)key[r] >> shift) & 255u);
     const int64_t dst = (int64_t)gbase[d] + wcount[warp][d] + rank[r];
     keys_out[dst] = key[r];
-    vals_out[dst] = val[r];
+    if (inverse) vals_out[val[r]] = (int32_t)dst;
+    else vals_out[dst] = val[r];
   }
 }
 
@@ -270,11 +309,12 @@ bool scratch_reserve(SortScratch *&s, int64_t n, cudaStream_t st) {
   return true;
 }
 
-// Radix passes over keys[n]; returns the buffers holding the permutation and
+// Radix passes over keys[n]; returns the buffers holding the permutation
+// (with `inverse`, the sorted position of every input index instead) and
 // the sorted keys.
 cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratch *s,
                        cudaStream_t st, int32_t **perm_out, int64_t *launches,
-                       int32_t **keys_out = nullptr) {
+                       int32_t **keys_out = nullptr, bool inverse = false) {
   const int bits = key_bits(nkeys);
   const int passes = (bits + 7) / 8;
   const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -290,7 +330,8 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
     scan_bsum_kernel<<<1, kThreads, 0, st>>>(s->bsum, nb);
     chunk_scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(s->table, tl, s->bsum);
     downsweep_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, vin, n, shift, ntiles, s->table,
-                                                             s->k[out], s->v[out]);
+                                                             s->k[out], s->v[out],
+                                                             inverse && p == passes - 1);
     *launches += 5;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -316,8 +357,8 @@ cudaError_t radix_perm(const int32_t *keys, int64_t n, int64_t nkeys, SortScratc
 //
 // General path (the first sort after loading, long sort intervals): the keys
 // go through the stable radix passes above, the ions are gathered by the
-// resulting permutation and the tile ranges are found by binary search in
-// the sorted keys.
+// permutation (the first sort) or stored at their sorted positions (later
+// sorts), and the tile ranges are found by binary search in the sorted keys.
 //
 // Windowed path: between two sorts an ion moves at most one cell per axis
 // per step (a larger move is a CFL error and the ion is held), and a key
@@ -694,6 +735,7 @@ __global__ void live_count_kernel(const int *tile_off, int ntiles, int *n_used) 
   *n_used = tile_off[ntiles];
 }
 
+// Ion perm[i] to position i (stores in order, reads scattered).
 __global__ void gather_kernel(Soa in, Soa out, const int32_t *perm, int64_t n) {
   const bool has_y = in.oy != nullptr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -708,6 +750,26 @@ __global__ void gather_kernel(Soa in, Soa out, const int32_t *perm, int64_t n) {
     out.vz[i] = in.vz[s];
     out.w[i] = in.w[s];
   }
+}
+
+// Ion i (read in order) to its sorted position dst[i]: the reads are
+// coalesced and only the stores scatter, which do not hold a thread up.
+__global__ void __launch_bounds__(256) place_kernel(Soa in, Soa out, const int32_t *dst, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool has_y = in.oy != nullptr;
+  const int64_t d = dst[i];
+  const int c = in.cell[i];
+  const float ox = in.ox[i], oy = has_y ? in.oy[i] : 0.f, oz = in.oz[i];
+  const float vx = in.vx[i], vy = in.vy[i], vz = in.vz[i], w = in.w[i];
+  out.cell[d] = c;
+  out.ox[d] = ox;
+  if (has_y) out.oy[d] = oy;
+  out.oz[d] = oz;
+  out.vx[d] = vx;
+  out.vy[d] = vy;
+  out.vz[d] = vz;
+  out.w[d] = w;
 }
 
 // tile_off[t] = first index whose sorted key is >= t << tlog (binary search)
@@ -812,13 +874,21 @@ hv_status sort_general(hv_ctx *c, Species &sp, cudaStream_t st) {
   // the keys live in v[1]: the first radix pass reads them and writes
   // k[0], v[0]; later passes overwrite them only after that
   ion_keys_kernel<<<eb, 256, 0, st>>>(g, src, sp.n, s->v[1]);
-  int32_t *perm = nullptr, *skeys = nullptr;
+  // ions in the order they were loaded in are gathered (scattered reads,
+  // stores in order); ions sorted before move little, and placing them
+  // (reads in order, stores mostly in runs) is faster
+  const bool place = c->since_sort >= 0;
+  int32_t *idx = nullptr, *skeys = nullptr;
   int64_t launches = 1;
-  cudaError_t e = radix_perm(s->v[1], sp.n, nkeys + (g.any_open ? 1 : 0), s, st, &perm,
-                             &launches, &skeys);
+  cudaError_t e = radix_perm(s->v[1], sp.n, nkeys + (g.any_open ? 1 : 0), s, st, &idx,
+                             &launches, &skeys, /*inverse=*/place);
   if (e == cudaSuccess) {
-    gather_kernel<<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(src, sp.buf[sp.cur ^ 1], perm,
-                                                                  sp.n);
+    if (place)
+      place_kernel<<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(src, sp.buf[sp.cur ^ 1], idx,
+                                                                   sp.n);
+    else
+      gather_kernel<<<(unsigned)((sp.n + 255) / 256), 256, 0, st>>>(src, sp.buf[sp.cur ^ 1], idx,
+                                                                    sp.n);
     tile_bounds_kernel<<<(g.ntiles + 256) / 256, 256, 0, st>>>(skeys, sp.n, g.tlog, g.ntiles,
                                                               sp.tile_off_next);
     launches += 2;
