@@ -47,6 +47,12 @@ constexpr int kScanChunk = 4096;
 #ifndef HV_RADIX_PREFETCH
 #define HV_RADIX_PREFETCH 1
 #endif
+// downsweep: a tile's items are ordered by digit in shared memory before
+// they are stored, so that the stores of one digit are contiguous (off:
+// every item stored from its lane)
+#ifndef HV_RADIX_STAGE
+#define HV_RADIX_STAGE 1
+#endif
 
 // Items of a tile are split into one contiguous run of 512 per warp; round r
 // of warp w covers tile items w*512 + r*32 + lane, so lane order within a
@@ -222,15 +228,51 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys
     __syncwarp();
   }
   __syncthreads();
-  // exclusive scan over warps for each digit
-  {
-    int run = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      const int t = wcount[w][threadIdx.x];
-      wcount[w][threadIdx.x] = run;
-      run += t;
-    }
+  // exclusive scan over warps for each digit (thread = digit)
+  int total = 0;
+  for (int w = 0; w < kWarps; ++w) {
+    const int t = wcount[w][threadIdx.x];
+    wcount[w][threadIdx.x] = total;
+    total += t;
   }
+#if HV_RADIX_STAGE
+  __shared__ int skey[kTile], sval[kTile];
+  __shared__ int dstart[256], wsum[kWarps];
+  // the tile's first position of every digit: exclusive scan of the digit
+  // totals
+  int incl = total;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  dstart[threadIdx.x] = before + incl - total;
+  __syncthreads();
+  // every item to its position in the tile ordered by digit (stable: warp,
+  // round, lane order), then stored from there in that order
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    if (rank[r] < 0) continue;
+    const int d = (int)(((uint32_t)key[r] >> shift) & 255u);
+    const int loc = dstart[d] + wcount[warp][d] + rank[r];
+    skey[loc] = key[r];
+    sval[loc] = val[r];
+  }
+  __syncthreads();
+  const int nv = (int)min((int64_t)kTile, n - tile0);
+  for (int j = threadIdx.x; j < nv; j += kThreads) {
+    const int k = skey[j];
+    const int d = (int)(((uint32_t)k >> shift) & 255u);
+    const int64_t dst = (int64_t)gbase[d] + (j - dstart[d]);
+    keys_out[dst] = k;
+    if (inverse) vals_out[sval[j]] = (int32_t)dst;
+    else vals_out[dst] = sval[j];
+  }
+#else
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
@@ -241,6 +283,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const int32_t *keys
     if (inverse) vals_out[val[r]] = (int32_t)dst;
     else vals_out[dst] = val[r];
   }
+#endif
 }
 
 // Count keys (warp-aggregated atomics) and flag out-of-range keys.  The loop
