@@ -53,6 +53,11 @@ constexpr int kScanChunk = 4096;
 #ifndef HV_RADIX_STAGE
 #define HV_RADIX_STAGE 1
 #endif
+// general sort of ions sorted before: place them at their sorted positions
+// (off: gather them by the permutation, as the first sort does)
+#ifndef HV_GENERAL_PLACE
+#define HV_GENERAL_PLACE 1
+#endif
 
 // Items of a tile are split into one contiguous run of 512 per warp; round r
 // of warp w covers tile items w*512 + r*32 + lane, so lane order within a
@@ -920,7 +925,7 @@ hv_status sort_general(hv_ctx *c, Species &sp, cudaStream_t st) {
   // ions in the order they were loaded in are gathered (scattered reads,
   // stores in order); ions sorted before move little, and placing them
   // (reads in order, stores mostly in runs) is faster
-  const bool place = c->since_sort >= 0;
+  const bool place = HV_GENERAL_PLACE && c->since_sort >= 0;
   int32_t *idx = nullptr, *skeys = nullptr;
   int64_t launches = 1;
   cudaError_t e = radix_perm(s->v[1], sp.n, nkeys + (g.any_open ? 1 : 0), s, st, &idx,
