@@ -90,8 +90,8 @@ def test_allocator_hooks_must_come_in_pairs():
 
 def test_error_word_maps_to_status_without_a_gpu():
     """The device error word -> status mapping every synchronising call
-    uses (SURVEY's failure-detection codes), checked on the host: each bit
-    alone and the precedence when several are set."""
+    uses (the failure-detection codes of include/hv.h), checked on the
+    host: each bit alone and the precedence when several are set."""
     st = hv.hv_error_status
     assert st(0) == hv.HV_OK
     assert st(1) == hv.HV_ECFL
