@@ -316,13 +316,55 @@ hv_status latched(hv_ctx *c, int *word) {
 
 __global__ void inject_error_kernel(int *err, int bits) { atomicOr(err, bits); }
 
+// Side stream and events for sorts issued ahead of their step, created on
+// first use.
+hv_status side_stream(hv_ctx *c) {
+  if (c->side) return HV_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fold, cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    e = cudaEventCreateWithFlags(&c->ev_rec[b], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "side stream");
+  return HV_OK;
+}
+
+// QS moment records (x-z layout) are double-buffered: a push deposits into
+// one buffer while the other waits for its next push.  The buffer the fold
+// just read is cleared on the side stream, beside the field advance, and
+// the push that deposits into it next waits for the clear.
+hv_status clear_records_async(hv_ctx *c) {
+  if (!uses_records(c)) return HV_OK;
+  hv_status st = side_stream(c);
+  if (st != HV_OK) return st;
+  const int b = c->accpar ^ 1;  // read by the fold just issued (the fold flips accpar)
+  cudaError_t e = cudaEventRecord(c->ev_fold, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fold, 0);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->accm[b], 0, sizeof(float) * kMono * (size_t)c->g.npad, c->side);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_rec[b], c->side);
+  if (e != cudaSuccess) return cuda_fail(e, "record clear");
+  c->rec_pending[b] = 1;
+  return HV_OK;
+}
+
+void wait_records(hv_ctx *c) {
+  if (!c->rec_pending[c->accpar]) return;
+  cudaStreamWaitEvent(c->stream, c->ev_rec[c->accpar], 0);
+  c->rec_pending[c->accpar] = 0;
+}
+
 hv_status startup(hv_ctx *c) {
+  wait_records(c);
   for (int s = 0; s < c->nspecies; ++s) {
     cudaError_t e = launch_push(c, s, 1);
     if (e != cudaSuccess) return cuda_fail(e, "start-up deposit");
   }
   cudaError_t e = launch_moments(c, 1);
   if (e != cudaSuccess) return cuda_fail(e, "start-up moments");
+  hv_status rs = clear_records_async(c);
+  if (rs != HV_OK) return rs;
   if (c->p.pe_eq) {
     e = launch_pe_init(c);
     if (e != cudaSuccess) return cuda_fail(e, "start-up electron pressure");
@@ -718,17 +760,6 @@ hv_status hv_set_injection(hv_ctx *c, int32_t species, int32_t face, double n, c
   return HV_OK;
 }
 
-// Side stream and events for sorts issued ahead of their step, created on
-// first use.
-static hv_status side_stream(hv_ctx *c) {
-  if (c->side) return HV_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(e, "side stream");
-  return HV_OK;
-}
-
 hv_status hv_step(hv_ctx *c, int32_t nsteps) {
   if (!c) return fail(HV_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(HV_EINVAL, "nsteps must be >= 0");
@@ -763,6 +794,7 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
       ev.launches[0] = c->launches - l0;
       l0 = c->launches;
     }
+    wait_records(c);
     for (int sp = 0; sp < c->nspecies; ++sp) {
       cudaError_t e = launch_push(c, sp, 0);
       if (e != cudaSuccess) return cuda_fail(e, "push");
@@ -808,6 +840,10 @@ hv_status hv_step(hv_ctx *c, int32_t nsteps) {
     }
     cudaError_t e = launch_moments(c, 0);
     if (e != cudaSuccess) return cuda_fail(e, "moments");
+    {
+      hv_status rs = clear_records_async(c);
+      if (rs != HV_OK) return rs;
+    }
     if (ps) {
       cudaEventRecord(ev.e[3], c->stream);
       ev.launches[2] = c->launches - l0;
@@ -1339,6 +1375,9 @@ void hv_destroy(hv_ctx *c) {
     cudaStreamSynchronize(c->side);
     cudaEventDestroy(c->ev_push);
     cudaEventDestroy(c->ev_sort);
+    cudaEventDestroy(c->ev_fold);
+    cudaEventDestroy(c->ev_rec[0]);
+    cudaEventDestroy(c->ev_rec[1]);
     cudaStreamDestroy(c->side);
   }
   prof_destroy(c);

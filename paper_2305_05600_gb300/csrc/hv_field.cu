@@ -42,7 +42,6 @@ struct MomArgs {
   Geom g;
   float4 *acc;            // per-target accumulator (read and zeroed)
   const float *rec;       // moment records of this step (read)
-  float *rec_clear;       // moment records of the next step (zeroed)
   const float4 *prev_in;  // n^{n-1/2}, J^{n-1/2}
   float4 *raw_out;        // folded deposit (when smoothing follows)
   float4 *prev_out;       // n^{n+1/2}, J^{n+1/2}
@@ -114,8 +113,8 @@ __global__ void __launch_bounds__(256) fold_kernel(MomArgs a) {
 // (4 S0 - Sxx - Szz)/6 (the two y neighbours of the single y cell folded in),
 // its x+-1 neighbours (S0 +- 2 Sx + Sxx)/12 and its z+-1 neighbours
 // (S0 +- 2 Sz + Szz)/12.  A cell collects from every source voxel whose
-// stencil reaches one of its images.  The other record buffer (read by the
-// previous fold) is zeroed for the next deposit.
+// stencil reaches one of its images.  (The buffer read here is cleared
+// for its next deposit by the host, beside the field advance.)
 __global__ void __launch_bounds__(256) fold_records_kernel(MomArgs a) {
   pdl_begin();
   const Geom &g = a.g;
@@ -154,9 +153,6 @@ __global__ void __launch_bounds__(256) fold_records_kernel(MomArgs a) {
             m[ch] += w;
           }
         }
-        float4 *z4 = reinterpret_cast<float4 *>(a.rec_clear + (size_t)T * kMono);
-#pragma unroll
-        for (int q = 0; q < kMono / 4; ++q) z4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     finish_moment(a, c, make_float4(m[0], m[1], m[2], m[3]));
   }
@@ -1337,7 +1333,6 @@ cudaError_t launch_moments(hv_ctx *c, int init) {
   a.g = c->g;
   a.acc = c->acc;
   a.rec = c->accm[c->accpar];
-  a.rec_clear = c->accm[c->accpar ^ 1];
   a.prev_in = c->mprev;
   a.prev_out = c->mprev;
   a.ext_out = c->mext;

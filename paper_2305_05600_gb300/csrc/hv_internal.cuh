@@ -324,6 +324,9 @@ struct hv_ctx {
   cudaStream_t side;    // a sort issued ahead of its step runs here, beside
                         // the previous step's field advance
   cudaEvent_t ev_push, ev_sort;
+  cudaEvent_t ev_fold, ev_rec[2];  // QS records: a fold issued; buffer b cleared
+  int rec_pending[2];   // a clear of record buffer b is issued on `side`
+                        // and the next push into b has not waited for it
   int presorted;        // the current step's sort was issued on `side`
   int since_sort;       // pushes since the last sort (-1: the ions are in
                         // load order, not sorted yet)
