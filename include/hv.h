@@ -245,7 +245,11 @@ hv_status hv_load_ions(hv_ctx *ctx, int32_t species, double q, double m, int64_t
  * waiting.  The first call also performs the start-up: moments of the
  * loaded ions at x^0 with v^{-1/2} become n^{-1/2}, J^{-1/2}, and
  * E^0 = Ohm(B^0, n^{-1/2}, J^{-1/2}).  Returns errors of argument checks and
- * launches only; device errors appear at the next synchronising call. */
+ * launches only; device errors appear at the next synchronising call.
+ * Besides the context stream the library uses its own side stream for a
+ * sort issued ahead of its step and for clearing a deposit buffer; the
+ * context stream waits for that work before anything reads its results,
+ * and hv_destroy waits for it too. */
 hv_status hv_step(hv_ctx *ctx, int32_t nsteps);
 
 /* Copy the current grids out (any pointer may be NULL): n_out [nz][ny][nx]
