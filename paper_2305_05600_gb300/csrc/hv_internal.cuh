@@ -154,7 +154,10 @@ constexpr double kSortHorizon = HV_SORT_HORIZON;
 // 8x8x8 cells in 3D (cells per tile a power of two).
 constexpr int kTile2X = 16, kTile2Z = 16, kTile3 = 8;
 // push blocks per supercell tile
-constexpr int kPushSplit = 4;
+#ifndef HV_PUSH_SPLIT
+#define HV_PUSH_SPLIT 2
+#endif
+constexpr int kPushSplit = HV_PUSH_SPLIT;
 
 // Supercell sort key of interior cell (i, j, k): tile index, then the cell
 // inside the tile, both x fastest.
