@@ -251,15 +251,18 @@ def measured_peak():
 
 def traffic_record(workload: str):
     """DRAM bytes per push launch from the committed ncu summary, valid only
-    while the push kernel source is unchanged (hash recorded with it)."""
-    src = os.path.join(ROOT, "paper_2305_05600_gb300", "csrc", "hv_push.cu")
+    while the push kernel's source and compile-time settings are unchanged
+    (a hash of both recorded with it)."""
+    csrc = os.path.join(ROOT, "paper_2305_05600_gb300", "csrc")
     rec = os.path.join(ROOT, "profiles", "push_traffic.json")
     try:
         with open(rec) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        blob = b"".join(open(os.path.join(csrc, name), "rb").read()
+                        for name in ("hv_push.cu", "hv_internal.cuh"))
+        h = hashlib.sha256(blob).hexdigest()[:16]
         ent = d.get(workload)
-        if ent and ent.get("hv_push_sha") == h:
+        if ent and ent.get("source_sha") == h:
             return float(ent["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass
